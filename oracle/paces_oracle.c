@@ -1,0 +1,784 @@
+/*
+ * paces_oracle.c -- plain FP64 CPU oracle of the co-evolving-subspace time step.
+ *
+ * TEST INFRASTRUCTURE ONLY: loaded by the tests, the package smoke check and the
+ * benchmark's CPU-baseline leg; never by the product path.  No code, table or
+ * helper is shared with the CUDA library.
+ *
+ * What it computes (paces paper, arXiv 2603.07341):
+ *   model      H = sum_s eps_s|s><s| + sum_{a!=b} J_ab|a><b|
+ *                + sum_j omega_j n_j + sum_s g_s|s><s|(a_s^dag + a_s)      (Eq. holstein)
+ *              with a hard phonon cap n_j <= K_j (App. parameters: d_pho - 1).
+ *   neighbours N_M = {n : <n|H|m> != 0, m in M}; H_eff = ball of radius m in the
+ *              graph H induces on basis states (Eqs. def_neighbor, def_neighbor_k, H_eff).
+ *   one step   truncate by weight, regrow H_eff, rescue re-admitted amplitudes
+ *              (Sec. "Truncation & post-adaptation detruncation"), build P H P
+ *              (Sec. "Generating the effective Hamiltonian"), propagate with the
+ *              Taylor series of exp(-i P H P dt) (App. C.1), record observables.
+ *
+ * Readings taken where the paper is silent (listed in the design notes):
+ *   - truncation keeps a row iff re^2 + im^2 >= theta^2, evaluated in FP64 with
+ *     no contraction (this file is compiled with -ffp-contract=off);
+ *   - no truncation before the first propagation after set_state;
+ *   - Taylor stops at the first n >= 2 with ||phi_n||^2 <= tol^2 ||r||^2;
+ *   - move order (which fixes row order): hops to t = 0..N-1 ascending, then
+ *     a_s^dag, then a_s; new states are appended in first-occurrence order.
+ *
+ * Representation: a basis state is the int tuple (s, n_0, ..., n_{N-1}); rows
+ * of H_eff are stored in order in a growable array with a linear-probing index.
+ */
+#include "paces_oracle.h"
+
+#include <complex.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef double complex cplx;
+
+/* ------------------------------------------------------------------ rowset */
+
+typedef struct {
+    int len;            /* ints per tuple = N + 1           */
+    int nrows, cap;     /* rows stored, rows allocated      */
+    int* t;             /* nrows * len                      */
+    int* idx;           /* hash index: slot -> row, -1 empty */
+    long nslots;        /* power of two                     */
+} rowset;
+
+static unsigned long long tuple_hash(const int* t, int len)
+{
+    /* FNV-1a over the integer values */
+    unsigned long long h = 1469598103934665603ULL;
+    for (int i = 0; i < len; ++i) {
+        h ^= (unsigned long long)(unsigned int)t[i];
+        h *= 1099511628211ULL;
+    }
+    return h ^ (h >> 29);
+}
+
+static int rs_init(rowset* r, int len)
+{
+    r->len = len;
+    r->nrows = 0;
+    r->cap = 64;
+    r->t = (int*)malloc(sizeof(int) * (size_t)r->cap * (size_t)len);
+    r->nslots = 128;
+    r->idx = (int*)malloc(sizeof(int) * (size_t)r->nslots);
+    if (!r->t || !r->idx) return OR_NOMEM;
+    for (long i = 0; i < r->nslots; ++i) r->idx[i] = -1;
+    return OR_OK;
+}
+
+static void rs_free(rowset* r)
+{
+    free(r->t);
+    free(r->idx);
+    r->t = NULL;
+    r->idx = NULL;
+    r->nrows = r->cap = 0;
+}
+
+static const int* rs_row(const rowset* r, int i) { return r->t + (size_t)i * (size_t)r->len; }
+
+static int rs_find(const rowset* r, const int* tup)
+{
+    long mask = r->nslots - 1;
+    long pos = (long)(tuple_hash(tup, r->len) & (unsigned long long)mask);
+    for (;;) {
+        int row = r->idx[pos];
+        if (row < 0) return -1;
+        if (memcmp(rs_row(r, row), tup, sizeof(int) * (size_t)r->len) == 0) return row;
+        pos = (pos + 1) & mask;
+    }
+}
+
+static void rs_place(rowset* r, int row)
+{
+    long mask = r->nslots - 1;
+    long pos = (long)(tuple_hash(rs_row(r, row), r->len) & (unsigned long long)mask);
+    while (r->idx[pos] >= 0) pos = (pos + 1) & mask;
+    r->idx[pos] = row;
+}
+
+/* append a tuple known to be absent; returns its row or -1 on allocation failure */
+static int rs_add(rowset* r, const int* tup)
+{
+    if (r->nrows == r->cap) {
+        int ncap = r->cap * 2;
+        int* nt = (int*)realloc(r->t, sizeof(int) * (size_t)ncap * (size_t)r->len);
+        if (!nt) return -1;
+        r->t = nt;
+        r->cap = ncap;
+    }
+    memcpy(r->t + (size_t)r->nrows * (size_t)r->len, tup, sizeof(int) * (size_t)r->len);
+    int row = r->nrows++;
+    if (2L * r->nrows > r->nslots) {
+        long ns = r->nslots * 2;
+        int* ni = (int*)malloc(sizeof(int) * (size_t)ns);
+        if (!ni) return -1;
+        free(r->idx);
+        r->idx = ni;
+        r->nslots = ns;
+        for (long i = 0; i < ns; ++i) r->idx[i] = -1;
+        for (int i = 0; i < r->nrows; ++i) rs_place(r, i);
+    } else {
+        rs_place(r, row);
+    }
+    return row;
+}
+
+/* ------------------------------------------------------------------ oracle */
+
+typedef struct {         /* one recorded step, for the adjoint */
+    int nrows;
+    int* tuples;         /* rows of H_eff of that step          */
+    int* from;           /* rescue map: new row -> previous row or -1 */
+    int nprev;
+    cplx* cprime;        /* amplitudes entering the propagator  */
+    int nterms;
+    double dt;
+} step_rec;
+
+struct oracle {
+    int N, len;
+    double* Jm;          /* N*N hopping matrix J_ab              */
+    double* Mm;          /* N*N hopping pattern dJ_ab/dJ          */
+    double *eps, *omega, *g;
+    int* cap;
+    int m, m_init;
+    double tol;
+    int nmax, fixed_terms;
+
+    rowset rows;         /* current H_eff                         */
+    cplx* c;             /* amplitudes on rows                    */
+    int ccap;
+    int fresh;           /* set_state done, first step not yet    */
+    int* lvl;            /* BFS level offsets                     */
+    int nlvl, lvlcap;
+    unsigned char* keep; /* last truncation mask                  */
+    int nkeep;
+
+    /* P H P of the current rows */
+    int hp_rows;
+    int* hp_off;
+    int* hp_col;
+    double* hp_val;
+    double* hp_dJ;       /* dH/dJ per entry                       */
+    double* hp_dg;       /* dH/dg per entry                       */
+    double* diag;
+    long hp_nnz;
+
+    rowset init;         /* psi(0) */
+    cplx* c0;
+
+    double st[OR_NST];
+    double time;
+
+    int recording;
+    step_rec* rec;
+    int nrec, reccap;
+    int* last_from;      /* rescue map of the last step           */
+};
+
+static double hop_pattern(int lattice_kind, int coupling_kind, const int* dims, int N,
+                          int a, int b)
+{
+    /* pattern M_ab such that J_ab = J * M_ab */
+    if (a == b) return 0.0;
+    if (lattice_kind == 0) {          /* ring: (j, j+1 mod N), pairs de-duplicated */
+        if (N < 2) return 0.0;
+        if ((a + 1) % N == b || (b + 1) % N == a) return 1.0;
+        return 0.0;
+    }
+    int d0 = 1, d1 = 1;
+    if (lattice_kind == 1) { d0 = N; d1 = 1; }
+    if (lattice_kind == 2) { d0 = dims[0]; d1 = dims[1]; }
+    if (lattice_kind == 3) { d0 = dims[0]; d1 = dims[1]; }
+    int ax = a % d0, ay = (a / d0) % d1, az = a / (d0 * d1);
+    int bx = b % d0, by = (b / d0) % d1, bz = b / (d0 * d1);
+    double dx = ax - bx, dy = ay - by, dz = az - bz;
+    double r2 = dx * dx + dy * dy + dz * dz;
+    if (coupling_kind == 0) return r2 == 1.0 ? 1.0 : 0.0;
+    return 1.0 / (r2 * sqrt(r2));
+}
+
+oracle_t* or_create(int n_sites, int lattice_kind, const int* dims, int coupling_kind,
+                    double J, const double* J_explicit, const double* eps,
+                    const double* omega, const double* g, const int* cap,
+                    int m, int m_init, double tol, int nmax, int fixed_terms)
+{
+    if (n_sites < 1 || lattice_kind < 0 || lattice_kind > 4 || coupling_kind < 0 ||
+        coupling_kind > 1 || m < 0 || !cap)
+        return NULL;
+    if (lattice_kind == 2 && (!dims || dims[0] * dims[1] != n_sites)) return NULL;
+    if (lattice_kind == 3 && (!dims || dims[0] * dims[1] * dims[2] != n_sites)) return NULL;
+    if (lattice_kind == 4 && !J_explicit) return NULL;
+    if (lattice_kind == 0 && coupling_kind != 0) return NULL;
+
+    oracle_t* o = (oracle_t*)calloc(1, sizeof(oracle_t));
+    if (!o) return NULL;
+    int N = n_sites;
+    o->N = N;
+    o->len = N + 1;
+    o->Jm = (double*)calloc((size_t)N * N, sizeof(double));
+    o->Mm = (double*)calloc((size_t)N * N, sizeof(double));
+    o->eps = (double*)calloc((size_t)N, sizeof(double));
+    o->omega = (double*)calloc((size_t)N, sizeof(double));
+    o->g = (double*)calloc((size_t)N, sizeof(double));
+    o->cap = (int*)calloc((size_t)N, sizeof(int));
+    for (int a = 0; a < N; ++a) {
+        for (int b = 0; b < N; ++b) {
+            double p;
+            if (lattice_kind == 4) p = (a == b) ? 0.0 : J_explicit[a * N + b];
+            else p = hop_pattern(lattice_kind, coupling_kind, dims, N, a, b);
+            o->Mm[a * N + b] = p;
+            o->Jm[a * N + b] = J * p;
+        }
+        o->eps[a] = eps ? eps[a] : 0.0;
+        o->omega[a] = omega ? omega[a] : 0.0;
+        o->g[a] = g ? g[a] : 0.0;
+        o->cap[a] = cap[a];
+        if (cap[a] < 0) { or_destroy(o); return NULL; }
+    }
+    o->m = m;
+    o->m_init = m_init;
+    o->tol = tol;
+    o->nmax = nmax;
+    o->fixed_terms = fixed_terms;
+    rs_init(&o->rows, o->len);
+    rs_init(&o->init, o->len);
+    o->lvlcap = 64;
+    o->lvl = (int*)malloc(sizeof(int) * (size_t)o->lvlcap);
+    return o;
+}
+
+static void free_recs(oracle_t* o)
+{
+    for (int i = 0; i < o->nrec; ++i) {
+        free(o->rec[i].tuples);
+        free(o->rec[i].from);
+        free(o->rec[i].cprime);
+    }
+    free(o->rec);
+    o->rec = NULL;
+    o->nrec = o->reccap = 0;
+}
+
+void or_destroy(oracle_t* o)
+{
+    if (!o) return;
+    free(o->Jm); free(o->Mm); free(o->eps); free(o->omega); free(o->g); free(o->cap);
+    rs_free(&o->rows);
+    rs_free(&o->init);
+    free(o->c); free(o->c0); free(o->lvl); free(o->keep);
+    free(o->hp_off); free(o->hp_col); free(o->hp_val); free(o->hp_dJ); free(o->hp_dg);
+    free(o->diag);
+    free(o->last_from);
+    free_recs(o);
+    free(o);
+}
+
+void or_get_hopping(const oracle_t* o, double* out)
+{
+    memcpy(out, o->Jm, sizeof(double) * (size_t)o->N * (size_t)o->N);
+}
+
+/* Moves of basis state tup in canonical order.  Writes child tuples and the
+ * matrix element <child|H|tup> (and its J and g derivatives); returns count. */
+static int moves(const oracle_t* o, const int* tup, int* child, double* val, double* dJ,
+                 double* dg)
+{
+    int N = o->N, len = o->len, s = tup[0], k = 0;
+    for (int t = 0; t < N; ++t) {
+        if (t == s || o->Jm[t * N + s] == 0.0) continue;
+        memcpy(child + k * len, tup, sizeof(int) * (size_t)len);
+        child[k * len] = t;
+        val[k] = o->Jm[t * N + s];
+        if (dJ) dJ[k] = o->Mm[t * N + s];
+        if (dg) dg[k] = 0.0;
+        ++k;
+    }
+    int ns = tup[1 + s];
+    if (o->g[s] != 0.0 && ns < o->cap[s]) {             /* a_s^dag */
+        memcpy(child + k * len, tup, sizeof(int) * (size_t)len);
+        child[k * len + 1 + s] = ns + 1;
+        val[k] = o->g[s] * sqrt((double)(ns + 1));
+        if (dJ) dJ[k] = 0.0;
+        if (dg) dg[k] = sqrt((double)(ns + 1));
+        ++k;
+    }
+    if (o->g[s] != 0.0 && ns > 0) {                      /* a_s */
+        memcpy(child + k * len, tup, sizeof(int) * (size_t)len);
+        child[k * len + 1 + s] = ns - 1;
+        val[k] = o->g[s] * sqrt((double)ns);
+        if (dJ) dJ[k] = 0.0;
+        if (dg) dg[k] = sqrt((double)ns);
+        ++k;
+    }
+    return k;
+}
+
+static int max_moves(const oracle_t* o) { return o->N + 2; }
+
+static double diag_of(const oracle_t* o, const int* tup)
+{
+    double d = o->eps[tup[0]];
+    for (int j = 0; j < o->N; ++j) d = d + o->omega[j] * (double)tup[1 + j];
+    return d;
+}
+
+static void lvl_push(oracle_t* o, int v)
+{
+    if (o->nlvl == o->lvlcap) {
+        o->lvlcap *= 2;
+        o->lvl = (int*)realloc(o->lvl, sizeof(int) * (size_t)o->lvlcap);
+    }
+    o->lvl[o->nlvl++] = v;
+}
+
+/* Grow rows by BFS levels: levels < 0 means until nothing new appears. */
+static int expand(oracle_t* o, int levels)
+{
+    int len = o->len, D = max_moves(o);
+    int* child = (int*)malloc(sizeof(int) * (size_t)D * (size_t)len);
+    double* val = (double*)malloc(sizeof(double) * (size_t)D);
+    int* parent = (int*)malloc(sizeof(int) * (size_t)len);
+    if (!child || !val || !parent) return OR_NOMEM;
+    o->nlvl = 0;
+    lvl_push(o, 0);
+    lvl_push(o, o->rows.nrows);
+    int lo = 0, hi = o->rows.nrows;
+    for (int l = 0; levels < 0 || l < levels; ++l) {
+        for (int p = lo; p < hi; ++p) {
+            memcpy(parent, rs_row(&o->rows, p), sizeof(int) * (size_t)len);
+            int k = moves(o, parent, child, val, NULL, NULL);
+            for (int i = 0; i < k; ++i)
+                if (rs_find(&o->rows, child + i * len) < 0)
+                    if (rs_add(&o->rows, child + i * len) < 0) return OR_NOMEM;
+        }
+        lo = hi;
+        hi = o->rows.nrows;
+        lvl_push(o, hi);
+        if (lo == hi) break;
+    }
+    free(child); free(val); free(parent);
+    return OR_OK;
+}
+
+static int ensure_c(oracle_t* o, int n)
+{
+    if (n <= o->ccap) return OR_OK;
+    int nc = o->ccap ? o->ccap : 64;
+    while (nc < n) nc *= 2;
+    cplx* c = (cplx*)realloc(o->c, sizeof(cplx) * (size_t)nc);
+    if (!c) return OR_NOMEM;
+    o->c = c;
+    o->ccap = nc;
+    return OR_OK;
+}
+
+static void observe(oracle_t* o);
+
+int or_set_state(oracle_t* o, int n, const int* site, const int* occ, const double* amps)
+{
+    if (!o || n <= 0 || !site || !occ || !amps) return OR_INVALID;
+    int N = o->N, len = o->len;
+    rs_free(&o->rows);
+    rs_free(&o->init);
+    rs_init(&o->rows, len);
+    rs_init(&o->init, len);
+    free(o->c0);
+    o->c0 = (cplx*)malloc(sizeof(cplx) * (size_t)n);
+    int* tup = (int*)malloc(sizeof(int) * (size_t)len);
+    if (ensure_c(o, n)) return OR_NOMEM;
+    for (int i = 0; i < n; ++i) {
+        if (site[i] < 0 || site[i] >= N) { free(tup); return OR_INVALID; }
+        tup[0] = site[i];
+        for (int j = 0; j < N; ++j) {
+            int v = occ[(size_t)i * N + j];
+            if (v < 0 || v > o->cap[j]) { free(tup); return OR_INVALID; }
+            tup[1 + j] = v;
+        }
+        if (rs_find(&o->rows, tup) >= 0) { free(tup); return OR_INVALID; }
+        rs_add(&o->rows, tup);
+        rs_add(&o->init, tup);
+        o->c[i] = amps[2 * i] + I * amps[2 * i + 1];
+        o->c0[i] = o->c[i];
+    }
+    free(tup);
+    int rc = expand(o, o->m_init);
+    if (rc) return rc;
+    if (ensure_c(o, o->rows.nrows)) return OR_NOMEM;
+    for (int i = n; i < o->rows.nrows; ++i) o->c[i] = 0.0;
+    o->fresh = 1;
+    o->time = 0.0;
+    free_recs(o);
+    memset(o->st, 0, sizeof(o->st));
+    observe(o);
+    o->st[OR_ST_ROWS] = o->rows.nrows;
+    o->st[OR_ST_KEPT] = n;
+    o->st[OR_ST_NORM_PHI0] = o->st[OR_ST_NORM];
+    o->st[OR_ST_NORM_BEFORE] = o->st[OR_ST_NORM];
+    return OR_OK;
+}
+
+long or_build_hamiltonian(oracle_t* o, int* cnt, int* cols, double* vals, double* diag)
+{
+    int q = o->rows.nrows, len = o->len, D = max_moves(o);
+    free(o->hp_off); free(o->hp_col); free(o->hp_val); free(o->hp_dJ); free(o->hp_dg);
+    free(o->diag);
+    o->hp_off = (int*)malloc(sizeof(int) * ((size_t)q + 1));
+    o->hp_col = (int*)malloc(sizeof(int) * ((size_t)q * D + 1));
+    o->hp_val = (double*)malloc(sizeof(double) * ((size_t)q * D + 1));
+    o->hp_dJ = (double*)malloc(sizeof(double) * ((size_t)q * D + 1));
+    o->hp_dg = (double*)malloc(sizeof(double) * ((size_t)q * D + 1));
+    o->diag = (double*)malloc(sizeof(double) * ((size_t)q + 1));
+    int* child = (int*)malloc(sizeof(int) * (size_t)D * (size_t)len);
+    double* val = (double*)malloc(sizeof(double) * (size_t)D);
+    double* dJ = (double*)malloc(sizeof(double) * (size_t)D);
+    double* dg = (double*)malloc(sizeof(double) * (size_t)D);
+    long nnz = 0;
+    for (int i = 0; i < q; ++i) {
+        const int* tup = rs_row(&o->rows, i);
+        o->hp_off[i] = (int)nnz;
+        o->diag[i] = diag_of(o, tup);
+        int k = moves(o, tup, child, val, dJ, dg);
+        for (int e = 0; e < k; ++e) {
+            int j = rs_find(&o->rows, child + e * len);
+            if (j < 0) continue;                  /* image outside H_eff */
+            o->hp_col[nnz] = j;
+            o->hp_val[nnz] = val[e];
+            o->hp_dJ[nnz] = dJ[e];
+            o->hp_dg[nnz] = dg[e];
+            ++nnz;
+        }
+    }
+    o->hp_off[q] = (int)nnz;
+    o->hp_rows = q;
+    o->hp_nnz = nnz;
+    free(child); free(val); free(dJ); free(dg);
+    if (cnt) for (int i = 0; i < q; ++i) cnt[i] = o->hp_off[i + 1] - o->hp_off[i];
+    if (cols) memcpy(cols, o->hp_col, sizeof(int) * (size_t)nnz);
+    if (vals) memcpy(vals, o->hp_val, sizeof(double) * (size_t)nnz);
+    if (diag) memcpy(diag, o->diag, sizeof(double) * (size_t)q);
+    return nnz;
+}
+
+/* y = P H P x */
+static void apply_h(const oracle_t* o, const cplx* x, cplx* y)
+{
+    for (int i = 0; i < o->hp_rows; ++i) {
+        cplx acc = o->diag[i] * x[i];
+        for (int e = o->hp_off[i]; e < o->hp_off[i + 1]; ++e) acc += o->hp_val[e] * x[o->hp_col[e]];
+        y[i] = acc;
+    }
+}
+
+static double norm2(const cplx* v, int n)
+{
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += creal(v[i]) * creal(v[i]) + cimag(v[i]) * cimag(v[i]);
+    return s;
+}
+
+/* r = sum_n (-i dt H)^n / n! c via phi_n = (-i dt / n) H phi_{n-1} (App. C.1) */
+static int taylor(oracle_t* o, double dt, cplx* c, int* nterms_out, double* energy)
+{
+    int q = o->hp_rows;
+    cplx* phi = (cplx*)malloc(sizeof(cplx) * ((size_t)q + 1));
+    cplx* y = (cplx*)malloc(sizeof(cplx) * ((size_t)q + 1));
+    cplx* r = (cplx*)malloc(sizeof(cplx) * ((size_t)q + 1));
+    if (!phi || !y || !r) return OR_NOMEM;
+    memcpy(phi, c, sizeof(cplx) * (size_t)q);
+    memcpy(r, c, sizeof(cplx) * (size_t)q);
+    int converged = 0, n = 0;
+    int nlimit = o->fixed_terms > 0 ? o->fixed_terms : o->nmax;
+    *energy = 0.0;
+    for (n = 1; n <= nlimit; ++n) {
+        apply_h(o, phi, y);
+        if (n == 1) {
+            double e = 0.0;
+            for (int i = 0; i < q; ++i) e += creal(conj(c[i]) * y[i]);
+            *energy = e;
+        }
+        cplx f = -I * dt / (double)n;
+        for (int i = 0; i < q; ++i) {
+            phi[i] = f * y[i];
+            r[i] += phi[i];
+        }
+        if (o->fixed_terms > 0) continue;
+        double a = norm2(phi, q), b = norm2(r, q);
+        if (n >= 2 && a <= o->tol * o->tol * b) { converged = 1; break; }
+    }
+    if (o->fixed_terms > 0) { converged = 1; n = o->fixed_terms; }
+    memcpy(c, r, sizeof(cplx) * (size_t)q);
+    free(phi); free(y); free(r);
+    *nterms_out = n;
+    return converged ? OR_OK : OR_NOCONVERGE;
+}
+
+static void observe(oracle_t* o)
+{
+    int q = o->rows.nrows;
+    o->st[OR_ST_NORM] = norm2(o->c, q);
+    cplx ov = 0.0;
+    for (int k = 0; k < o->init.nrows; ++k) {
+        int j = rs_find(&o->rows, rs_row(&o->init, k));
+        if (j >= 0) ov += conj(o->c0[k]) * o->c[j];
+    }
+    o->st[OR_ST_C_RE] = creal(ov);
+    o->st[OR_ST_C_IM] = cimag(ov);
+    o->st[OR_ST_TIME] = o->time;
+}
+
+void or_populations(const oracle_t* o, double* P, double* nbar)
+{
+    int N = o->N;
+    for (int j = 0; j < N; ++j) P[j] = nbar[j] = 0.0;
+    for (int i = 0; i < o->rows.nrows; ++i) {
+        const int* t = rs_row(&o->rows, i);
+        double w = creal(o->c[i]) * creal(o->c[i]) + cimag(o->c[i]) * cimag(o->c[i]);
+        P[t[0]] += w;
+        for (int j = 0; j < N; ++j) nbar[j] += w * (double)t[1 + j];
+    }
+}
+
+int or_step(oracle_t* o, double dt, double theta, const unsigned char* keep_override,
+            int keep_len)
+{
+    if (!o || (o->rows.nrows == 0 && !o->fresh)) return OR_STATE;
+    int len = o->len;
+    int q_old = o->rows.nrows;
+    double norm_before = norm2(o->c, q_old);
+    int kept = q_old;
+    free(o->last_from);
+    o->last_from = NULL;
+    if (!o->fresh) {
+        if (keep_override && keep_len != q_old) return OR_INVALID;
+        /* 1. truncation Q: keep rows whose weight reaches theta^2 */
+        free(o->keep);
+        o->keep = (unsigned char*)malloc((size_t)q_old + 1);
+        o->nkeep = q_old;
+        double th2 = theta * theta;
+        for (int i = 0; i < q_old; ++i) {
+            double re = creal(o->c[i]), im = cimag(o->c[i]);
+            double w = re * re + im * im;
+            o->keep[i] = keep_override ? (keep_override[i] != 0) : (w >= th2);
+        }
+        /* 2. M in row order, then regrow H_eff by m BFS levels */
+        rowset old = o->rows;
+        cplx* cold = o->c;
+        o->c = NULL;
+        o->ccap = 0;
+        rs_init(&o->rows, len);
+        kept = 0;
+        for (int i = 0; i < q_old; ++i)
+            if (o->keep[i]) { rs_add(&o->rows, rs_row(&old, i)); ++kept; }
+        int rc = expand(o, o->m);
+        if (rc) return rc;
+        /* 3. rescue: amplitudes of re-admitted states come back (detruncation) */
+        int q = o->rows.nrows;
+        if (ensure_c(o, q > 0 ? q : 1)) return OR_NOMEM;
+        o->last_from = (int*)malloc(sizeof(int) * ((size_t)q + 1));
+        for (int i = 0; i < q; ++i) {
+            int j = rs_find(&old, rs_row(&o->rows, i));
+            o->last_from[i] = j;
+            o->c[i] = (j >= 0) ? cold[j] : 0.0;
+        }
+        rs_free(&old);
+        free(cold);
+    }
+    /* 4. P H P, 5. propagation */
+    or_build_hamiltonian(o, NULL, NULL, NULL, NULL);
+    int q = o->rows.nrows;
+    if (o->recording) {
+        if (o->nrec == o->reccap) {
+            o->reccap = o->reccap ? 2 * o->reccap : 16;
+            o->rec = (step_rec*)realloc(o->rec, sizeof(step_rec) * (size_t)o->reccap);
+        }
+        step_rec* R = &o->rec[o->nrec++];
+        memset(R, 0, sizeof(*R));
+        R->nrows = q;
+        R->tuples = (int*)malloc(sizeof(int) * (size_t)q * len + 1);
+        memcpy(R->tuples, o->rows.t, sizeof(int) * (size_t)q * len);
+        R->from = (int*)malloc(sizeof(int) * ((size_t)q + 1));
+        for (int i = 0; i < q; ++i) R->from[i] = o->last_from ? o->last_from[i] : i;
+        R->nprev = q_old;
+        R->cprime = (cplx*)malloc(sizeof(cplx) * ((size_t)q + 1));
+        memcpy(R->cprime, o->c, sizeof(cplx) * (size_t)q);
+    }
+    double n0 = norm2(o->c, q);
+    int nterms = 0;
+    double energy = 0.0;
+    int rc = taylor(o, dt, o->c, &nterms, &energy);
+    if (o->recording) {
+        o->rec[o->nrec - 1].nterms = nterms;
+        o->rec[o->nrec - 1].dt = dt;
+    }
+    o->time += dt;
+    o->fresh = 0;
+    observe(o);
+    o->st[OR_ST_NORM_PHI0] = n0;
+    o->st[OR_ST_ENERGY] = energy;
+    o->st[OR_ST_ROWS] = q;
+    o->st[OR_ST_KEPT] = kept;
+    o->st[OR_ST_NNZ] = (double)(o->hp_nnz + q);
+    o->st[OR_ST_TERMS] = nterms;
+    o->st[OR_ST_NORM_BEFORE] = norm_before;
+    return rc;
+}
+
+int or_nrows(const oracle_t* o) { return o->rows.nrows; }
+
+void or_get_rows(const oracle_t* o, int* tuples, double* amps)
+{
+    int q = o->rows.nrows;
+    if (tuples) memcpy(tuples, o->rows.t, sizeof(int) * (size_t)q * (size_t)o->len);
+    if (amps)
+        for (int i = 0; i < q; ++i) {
+            amps[2 * i] = creal(o->c[i]);
+            amps[2 * i + 1] = cimag(o->c[i]);
+        }
+}
+
+int or_level_offsets(const oracle_t* o, int* off, int max)
+{
+    for (int i = 0; i < o->nlvl && i < max; ++i) off[i] = o->lvl[i];
+    return o->nlvl;
+}
+
+int or_last_keep(const oracle_t* o, unsigned char* keep, int max)
+{
+    for (int i = 0; i < o->nkeep && i < max; ++i) keep[i] = o->keep[i];
+    return o->nkeep;
+}
+
+void or_stats(const oracle_t* o, double* st) { memcpy(st, o->st, sizeof(o->st)); }
+
+/* ------------------------------------------------------------------ adjoint
+ *
+ * Gradient of a real loss L of the recorded trajectory with respect to
+ * theta = (J, g, omega, eps_0..eps_{N-1}), holding the recorded subspace
+ * sequence and term counts fixed.  Cotangents use dL = Re(mu^dag dc).
+ * For one step with phi_n = B_n phi_{n-1}, B_n = (-i dt/n) H, c = sum_n phi_n:
+ *   mu_N = gbar, mu_{n-1} = gbar + B_n^dag mu_n,
+ *   dL/dtheta_p += sum_n Re(mu_n^dag (-i dt/n) (dH/dtheta_p) phi_{n-1}),
+ * and the cotangent of the previous step's amplitudes is mu_0 scattered back
+ * through the rescue map.  H is linear in every parameter, so dH/dtheta_p has
+ * the sparsity of H with the derivative coefficients.
+ */
+int or_record(oracle_t* o, int on)
+{
+    free_recs(o);
+    o->recording = on;
+    return OR_OK;
+}
+
+/* rebuild rows/hamiltonian of a recorded step into the oracle (scratch use) */
+static int load_rec_rows(oracle_t* o, const step_rec* R)
+{
+    rs_free(&o->rows);
+    rs_init(&o->rows, o->len);
+    for (int i = 0; i < R->nrows; ++i)
+        if (rs_add(&o->rows, R->tuples + (size_t)i * o->len) < 0) return OR_NOMEM;
+    or_build_hamiltonian(o, NULL, NULL, NULL, NULL);
+    return OR_OK;
+}
+
+/* y = (dH/dtheta_p) x for p = 0 (J), 1 (g), 2 (omega), 3+s (eps_s) */
+static void apply_dh(const oracle_t* o, int p, const cplx* x, cplx* y)
+{
+    for (int i = 0; i < o->hp_rows; ++i) {
+        const int* t = rs_row(&o->rows, i);
+        cplx acc = 0.0;
+        if (p == 0 || p == 1) {
+            const double* d = (p == 0) ? o->hp_dJ : o->hp_dg;
+            for (int e = o->hp_off[i]; e < o->hp_off[i + 1]; ++e) acc += d[e] * x[o->hp_col[e]];
+        } else if (p == 2) {
+            double nsum = 0.0;
+            for (int j = 0; j < o->N; ++j) nsum += (double)t[1 + j];
+            acc = nsum * x[i];
+        } else {
+            acc = (t[0] == p - 3) ? x[i] : 0.0;
+        }
+        y[i] = acc;
+    }
+}
+
+int or_backward(oracle_t* o, int nsteps_rec, const double* dL_dc_final, const double* dL_dC,
+                double* grad)
+{
+    if (!o || nsteps_rec != o->nrec || nsteps_rec <= 0) return OR_INVALID;
+    int N = o->N, len = o->len, P = 3 + N;
+    for (int p = 0; p < P; ++p) grad[p] = 0.0;
+    /* park the live state; the recorded steps are reloaded one by one */
+    rowset live = o->rows;
+    cplx* live_c = o->c;
+    int live_ccap = o->ccap;
+    o->c = NULL;
+    o->ccap = 0;
+    rs_init(&o->rows, len);
+
+    const step_rec* last = &o->rec[nsteps_rec - 1];
+    cplx* gbar = (cplx*)calloc((size_t)last->nrows + 1, sizeof(cplx));
+    if (dL_dc_final)
+        for (int i = 0; i < last->nrows; ++i)
+            gbar[i] = dL_dc_final[2 * i] + I * dL_dc_final[2 * i + 1];
+
+    int rc = OR_OK;
+    for (int k = nsteps_rec - 1; k >= 0 && rc == OR_OK; --k) {
+        const step_rec* R = &o->rec[k];
+        int q = R->nrows, nt = R->nterms;
+        rc = load_rec_rows(o, R);
+        if (rc) break;
+        if (dL_dC) {   /* C(t_k) = sum_j conj(psi0_j) c(key_j)  =>  gbar_j += psi0_j w_k */
+            cplx w = dL_dC[2 * k] + I * dL_dC[2 * k + 1];
+            for (int j = 0; j < o->init.nrows; ++j) {
+                int i = rs_find(&o->rows, rs_row(&o->init, j));
+                if (i >= 0) gbar[i] += o->c0[j] * w;
+            }
+        }
+        /* forward terms of this step, recomputed */
+        size_t qs = (size_t)q + 1;
+        cplx* phis = (cplx*)malloc(sizeof(cplx) * (size_t)(nt + 1) * qs);
+        cplx* y = (cplx*)malloc(sizeof(cplx) * qs);
+        cplx* mu = (cplx*)malloc(sizeof(cplx) * qs);
+        if (!phis || !y || !mu) { rc = OR_NOMEM; break; }
+        memcpy(phis, R->cprime, sizeof(cplx) * (size_t)q);
+        for (int n = 1; n <= nt; ++n) {
+            apply_h(o, phis + (size_t)(n - 1) * qs, y);
+            cplx f = -I * R->dt / (double)n;
+            for (int i = 0; i < q; ++i) phis[(size_t)n * qs + i] = f * y[i];
+        }
+        /* reverse recurrence */
+        memcpy(mu, gbar, sizeof(cplx) * (size_t)q);
+        for (int n = nt; n >= 1; --n) {
+            cplx f = -I * R->dt / (double)n;
+            const cplx* phi_prev = phis + (size_t)(n - 1) * qs;
+            for (int p = 0; p < P; ++p) {
+                apply_dh(o, p, phi_prev, y);
+                cplx s = 0.0;
+                for (int i = 0; i < q; ++i) s += conj(mu[i]) * (f * y[i]);
+                grad[p] += creal(s);
+            }
+            apply_h(o, mu, y);                     /* B_n^dag mu = (i dt/n) H mu */
+            for (int i = 0; i < q; ++i) mu[i] = gbar[i] + conj(f) * y[i];
+        }
+        /* mu is now the cotangent of c'; scatter through the rescue map */
+        cplx* prev = (cplx*)calloc((size_t)R->nprev + 1, sizeof(cplx));
+        for (int i = 0; i < q; ++i)
+            if (R->from[i] >= 0) prev[R->from[i]] += mu[i];
+        free(gbar);
+        gbar = prev;
+        free(phis); free(y); free(mu);
+    }
+    free(gbar);
+    rs_free(&o->rows);
+    o->rows = live;
+    free(o->c);
+    o->c = live_c;
+    o->ccap = live_ccap;
+    or_build_hamiltonian(o, NULL, NULL, NULL, NULL);
+    return rc;
+}

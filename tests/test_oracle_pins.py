@@ -1,0 +1,373 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Every check compares the oracle with something other than itself: a dense
+Kronecker-product Hamiltonian exponentiated by eigendecomposition, textbook
+closed forms, the paper's printed worked examples (tests/golden), invariants,
+and finite differences.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle.oracle import Oracle, OracleError, absorption_spectrum
+from paper_2603_07341_gb300 import workloads as W
+from tests.dense_model import dense_holstein, dense_index, propagator, ring_hop
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def gold(name):
+    with open(os.path.join(GOLD, name)) as f:
+        return json.load(f)
+
+
+def oracle_for(cfg, **over):
+    kw = W.model_kwargs(cfg, **over)
+    extra = {k: over[k] for k in ("tol", "nmax", "fixed_terms") if k in over}
+    return Oracle(**kw, **extra)
+
+
+def state_vector(o, D, strides, dim):
+    t, a = o.rows()
+    v = np.zeros(dim, dtype=np.complex128)
+    v[dense_index(t, D, strides)] = a
+    return v
+
+
+# ---------------------------------------------------------------- whole step vs expm
+def test_ring4_full_space_matches_dense_expm():
+    """Config ring4 (full space 2500).  With theta = 0 every step keeps the whole
+    space, so the trajectory is exp(-iHt) psi0 to the series tolerance (Sec. 3.5:
+    the only error sources are Q, P_m and the series cutoff).  At the workload's
+    theta = 1e-8 the early steps truncate; the end state stays within 1e-6."""
+    cfg = W.CONFIGS["ring4"]
+    N = cfg["n_sites"]
+    H, D, strides = dense_holstein(ring_hop(N, cfg["J"]), [0.0] * N, [1.0] * N, [1.0] * N, [4] * N)
+    U = propagator(H)
+    for theta, tol in ((0.0, 1e-11), (cfg["theta"], 1e-6)):
+        o = oracle_for(cfg)
+        o.set_state(*W.start_state(cfg))
+        assert o.nrows() == 4 * 5 ** 4
+        psi0 = state_vector(o, D, strides, H.shape[0])
+        for k in range(1, cfg["nsteps"] + 1):
+            o.step(cfg["dt"], theta)
+            if theta == 0.0:
+                assert o.stats()["rows"] == 2500
+            if k % 50 == 0:
+                err = np.linalg.norm(state_vector(o, D, strides, H.shape[0]) - U(k * cfg["dt"], psi0))
+                assert err <= tol, (theta, k, err)
+
+
+def test_threshold_to_zero_converges():
+    """Starting from the full space (m_init = closure), the error against the exact
+    evolution falls steadily as the threshold goes to zero and reaches the series
+    tolerance (Sec. 4.2: fidelity grows with the kept set; Sec. 3.5 error sources)."""
+    cfg = W.CONFIGS["ring4"]
+    N = cfg["n_sites"]
+    H, D, strides = dense_holstein(ring_hop(N, 1.0), [0.0] * N, [1.0] * N, [1.0] * N, [4] * N)
+    U = propagator(H)
+    errs = []
+    thetas = (1e-2, 1e-3, 1e-4, 1e-5, 1e-6, 1e-8, 1e-10)
+    for th in thetas:
+        o = oracle_for(cfg)
+        o.set_state(*W.start_state(cfg))
+        psi0 = state_vector(o, D, strides, H.shape[0])
+        for _ in range(60):
+            o.step(0.05, th)
+        errs.append(np.linalg.norm(state_vector(o, D, strides, H.shape[0]) - U(3.0, psi0)))
+    assert all(errs[i + 1] < 0.5 * errs[i] for i in range(len(errs) - 1)), errs
+    assert errs[-1] < 1e-9
+
+
+@pytest.mark.parametrize("m", [1, 2])
+def test_restriction_error_order_and_bound(m):
+    """Eq. epsilon_Pm / App. F: one step restricted to the radius-m ball errs by
+    O(dt^{m+1}) and stays under sum_{l>m} (2^{l-m}-1)/l! (alpha dt)^l, alpha <= ||H||."""
+    N = 4
+    H, D, strides = dense_holstein(ring_hop(N, 1.0), [0.0] * N, [1.0] * N, [1.0] * N, [4] * N)
+    alpha = np.max(np.abs(np.linalg.eigvalsh(H)))
+    U = propagator(H)
+    errs = []
+    dts = (0.04, 0.02, 0.01)
+    for dt in dts:
+        o = Oracle(N, W.RING, J=1.0, omega=1.0, g=1.0, cap=4, m=m, m_init=m)
+        o.set_state([0], [[0] * N], [1.0])
+        psi0 = state_vector(o, D, strides, H.shape[0])
+        o.step(dt, 0.0)
+        err = np.linalg.norm(state_vector(o, D, strides, H.shape[0]) - U(dt, psi0))
+        bound = sum((2.0 ** (l - m) - 1.0) / math.factorial(l) * (alpha * dt) ** l
+                    for l in range(m + 1, 60))
+        assert err <= bound, (dt, err, bound)
+        errs.append(err)
+    for a, b in zip(errs, errs[1:]):
+        assert abs(math.log2(a / b) - (m + 1)) < 0.15, errs
+
+
+# ---------------------------------------------------------------- closed forms
+def test_two_site_rabi():
+    """N = 2, g = 0: P_1 = (4J^2/Omega^2) sin^2(Omega t / 2), Omega^2 = Delta^2 + 4J^2.
+    The ring of two sites has a single bond (pairs are de-duplicated)."""
+    for eps in ((0.0, 0.0), (0.3, -0.2)):
+        J = 1.0
+        o = Oracle(2, W.RING, J=J, eps=eps, omega=1.0, g=0.0, cap=1, m=2, m_init=-1)
+        o.set_state([0], [[0, 0]], [1.0])
+        assert o.hopping()[0, 1] == J
+        delta = eps[0] - eps[1]
+        Om = math.sqrt(delta ** 2 + 4 * J * J)
+        for k in range(1, 101):
+            o.step(0.05, 0.0)
+            t = 0.05 * k
+            P, nbar = o.populations()
+            assert abs(P[1] - 4 * J * J / Om ** 2 * math.sin(Om * t / 2) ** 2) < 1e-12
+            assert np.all(nbar == 0.0)
+        t_, _ = o.rows()
+        assert np.all(t_[:, 1:] == 0)       # g = 0: the phonon vacuum sector is kept
+
+
+def test_independent_boson_autocorrelation():
+    """N = 1, J = 0 (displaced oscillator, Fig. 2 of the paper with the textbook
+    solution): C(t) = exp[(g/w)^2 (e^{-iwt} - 1) + i g^2 t / w],
+    <n>(t) = 2 (g/w)^2 (1 - cos wt).  Cap K = 40 leaves a Poisson tail < 1e-20."""
+    g, w = 1.0, 1.0
+    o = Oracle(1, W.RING, J=0.0, omega=w, g=g, cap=40, m=2, m_init=-1)
+    o.set_state([0], [[0]], [1.0])
+    assert o.nrows() == 41
+    for k in range(1, 201):
+        o.step(0.05, 0.0)
+        t = 0.05 * k
+        st = o.stats()
+        c_exact = np.exp((g / w) ** 2 * (np.exp(-1j * w * t) - 1) + 1j * g * g * t / w)
+        assert abs(st["C_re"] + 1j * st["C_im"] - c_exact) < 1e-11
+        _, nbar = o.populations()
+        assert abs(nbar[0] - 2 * (g / w) ** 2 * (1 - math.cos(w * t))) < 1e-10
+
+
+def test_electronic_spectrum_g0_and_dipolar_pattern():
+    """g = 0: C(t) = sum_k |<k|mu>|^2 e^{-i E_k t} over the N x N exciton matrix
+    (the exact diagonalisation the paper uses for its g = 0 spectra).  Entries
+    of the all-pairs J0/r^3 pattern are checked against hand values."""
+    J0 = -1.0
+    o = Oracle(9, W.OPEN2D, dims=(3, 3, 1), coupling_kind=W.DIPOLAR, J=J0, omega=1.0, g=0.0,
+               cap=2, m=2, m_init=-1)
+    h = o.hopping()
+    assert h[0, 1] == J0 and h[0, 3] == J0                      # r = 1
+    assert abs(h[0, 4] - J0 / (2.0 * math.sqrt(2.0))) < 1e-16   # r = sqrt 2
+    assert abs(h[0, 2] - J0 / 8.0) < 1e-16                      # r = 2
+    assert abs(h[0, 8] - J0 / (8.0 * math.sqrt(8.0))) < 1e-16   # r = sqrt 8
+    assert np.allclose(h, h.T) and np.all(np.diag(h) == 0)
+    mu = np.full(9, 1 / 3.0)
+    o.set_state(np.arange(9), np.zeros((9, 9), dtype=np.int32), mu)
+    E, V = np.linalg.eigh(h)
+    w = np.abs(V.T @ mu) ** 2
+    for k in range(1, 81):
+        o.step(0.05, 0.0)
+        st = o.stats()
+        c_exact = np.sum(w * np.exp(-1j * E * 0.05 * k))
+        assert abs(st["C_re"] + 1j * st["C_im"] - c_exact) < 1e-12
+
+
+def test_dimer_bright_line_shift():
+    """App. G.1: without vibrations the dimer's bright state absorbs at the bare
+    transition shifted by exactly J: C(t) = e^{-iJt}."""
+    for J in (0.55, -0.55):
+        o = Oracle(2, W.RING, J=J, omega=1.0, g=0.0, cap=2, m=2, m_init=-1)
+        o.set_state([0, 1], [[0, 0], [0, 0]], [1 / math.sqrt(2)] * 2)
+        for k in range(1, 41):
+            o.step(0.05, 0.0)
+            st = o.stats()
+            assert abs(st["C_re"] + 1j * st["C_im"] - np.exp(-1j * J * 0.05 * k)) < 1e-13
+
+
+# ---------------------------------------------------------------- worked examples
+def test_tb_neighbour_sets_worked_example():
+    """Paper's TB example: |N0| = 2, |N1| = 3, |N2| = 4 and a 7-state ball of
+    radius 2, {n-3..n+3}; N1 of {n-1, n+1} is {n-2, n, n+2}."""
+    gd = gold("tb_neighbour_sets.json")
+    L, n = 21, 10
+    hop = np.zeros((L, L))
+    for a in range(L - 1):
+        hop[a, a + 1] = hop[a + 1, a] = 1.0
+    supp = np.zeros(L)
+    supp[[n - 1, n + 1]] = 1.0
+    sets = [set(np.nonzero(np.linalg.matrix_power(hop, k) @ supp)[0]) for k in range(3)]
+    assert [len(s) for s in sets] == [gd["N0"], gd["N1"], gd["N2"]]
+    for mi, expect in ((1, gd["N1_first_example"]), (2, gd["ball_m2_offsets"])):
+        o = Oracle(L, W.CHAIN, J=1.0, omega=1.0, g=0.0, cap=0, m=2, m_init=mi)
+        o.set_state([n - 1, n + 1], np.zeros((2, L), dtype=np.int32), [2 ** -0.5] * 2)
+        t, _ = o.rows()
+        ball = set(t[:, 0].tolist())
+        assert ball == set.union(*sets[: mi + 1])
+        if mi == 1:
+            assert set(t[2:, 0] - n) == set(expect)
+        else:
+            assert len(ball) == gd["ball_m2"] and sorted(b - n for b in ball) == expect
+        assert list(o.level_offsets()[: mi + 2]) == ([0, 2, 5] if mi == 1 else [0, 2, 5, 7])
+
+
+@pytest.mark.parametrize("L,d", [(3, 4), (4, 3), (2, 6)])
+def test_holstein_nonzero_count_formula(L, d):
+    """App. C: the full-space open Holstein chain has d^L[(5L-2) - 2L/d] stored
+    entries, counting every diagonal; the TB chain has 3L - 2."""
+    o = Oracle(L, W.CHAIN, J=1.0, omega=1.0, g=0.8, cap=d - 1, m=2, m_init=-1)
+    o.set_state([0], [[0] * L], [1.0])
+    assert o.nrows() == L * d ** L
+    cnt, cols, vals, diag = o.hamiltonian()
+    assert len(cols) + o.nrows() == d ** L * (5 * L - 2) - 2 * L * d ** (L - 1)
+    tb = Oracle(L, W.CHAIN, J=1.0, omega=1.0, g=0.0, cap=0, m=2, m_init=-1)
+    tb.set_state([0], [[0] * L], [1.0])
+    c2, cols2, _, _ = tb.hamiltonian()
+    assert tb.nrows() == L and len(cols2) + L == 3 * L - 2
+
+
+def test_paper_sparsity_numbers():
+    """App. C printed figures for L = 9, d_pho = 5: 587 MiB of 64-bit nonzeros and
+    2248 TiB dense, from the density formula."""
+    gd = gold("sparsity_appC.json")
+    L, d = gd["L"], gd["d_pho"]
+    dim = L * d ** L
+    density = ((5 * L - 2) - 2 * L / d) / (L * L * d ** L)
+    nnz = round(density * dim * dim)
+    assert nnz == gd["nonzero_count_from_density"]
+    assert round(nnz * 8 / 2 ** 20) == gd["nonzeros_MiB"]
+    assert math.floor(dim * dim * 8 / 2 ** 40) == gd["dense_TiB"]
+
+
+# ---------------------------------------------------------------- invariants
+def test_norm_and_energy_conservation_inside_steps():
+    """Sec. 3.5 / Fig. error_sources: the propagator is unitary to machine precision
+    inside H_eff (norm to 1e-13) and conserves c^dag H_P c; with the full space kept
+    the energy is constant across steps."""
+    cfg = W.CONFIGS["ring4"]
+    o = oracle_for(cfg, eps=np.array([0.1, -0.2, 0.3, 0.0]))
+    o.set_state(np.arange(4), np.zeros((4, 4), dtype=np.int32), [0.5] * 4)
+    E0 = None
+    for _ in range(40):
+        o.step(0.05, 0.0)
+        st = o.stats()
+        assert abs(st["norm"] - st["norm_phi0"]) < 1e-13
+        E0 = st["energy"] if E0 is None else E0
+        assert abs(st["energy"] - E0) < 1e-12 * max(1.0, abs(E0))
+    assert abs(E0) > 0.05
+
+
+def test_truncation_never_increases_norm():
+    cfg = W.CONFIGS["ring16"]
+    o = oracle_for(cfg, m_init=4)
+    o.set_state(*W.start_state(cfg))
+    for _ in range(15):
+        o.step(0.02, 1e-4)
+        st = o.stats()
+        assert st["norm_phi0"] <= st["norm_before"] + 1e-15
+        assert st["kept"] <= st["rows"]
+
+
+def test_sign_of_J_invariance_on_bipartite_ring():
+    """J -> -J leaves populations and phonon numbers unchanged for a localised
+    start on a bipartite lattice (App. H; gauge |s> -> (-1)^s |s>)."""
+    cfg = W.CONFIGS["ring4"]
+    res = []
+    for J in (1.0, -1.0):
+        o = oracle_for(cfg, J=J, m_init=3)
+        o.set_state(*W.start_state(cfg))
+        for _ in range(60):
+            o.step(0.05, 1e-6)
+        res.append(o.populations())
+    assert np.allclose(res[0][0], res[1][0], atol=1e-13, rtol=0)
+    assert np.allclose(res[0][1], res[1][1], atol=1e-13, rtol=0)
+
+
+def test_second_order_taylor_breaks_unitarity():
+    """App. C.2: cutting the series at N_series = m = 2 makes the norm grow."""
+    cfg = W.CONFIGS["ring4"]
+    good = oracle_for(cfg)
+    bad = oracle_for(cfg, fixed_terms=2)
+    for o in (good, bad):
+        o.set_state(*W.start_state(cfg))
+        for _ in range(100):
+            o.step(0.05, 1e-8)
+    assert abs(good.stats()["norm"] - 1.0) < 1e-12
+    assert bad.stats()["norm"] > 1.0 + 1e-4
+
+
+def test_taylor_nonconvergence_is_reported():
+    """App. I: a step too large for the series is an error, not a silent result."""
+    cfg = W.CONFIGS["ring4"]
+    o = oracle_for(cfg, nmax=6)
+    o.set_state(*W.start_state(cfg))
+    with pytest.raises(OracleError) as e:
+        o.step(0.5, 1e-8)
+    assert e.value.code == 4
+
+
+def test_invalid_inputs_rejected():
+    o = Oracle(3, W.RING, J=1.0, omega=1.0, g=1.0, cap=2, m=2, m_init=1)
+    for site, occ in (([3], [[0, 0, 0]]), ([0], [[0, 3, 0]]), ([0, 0], [[0, 0, 0]] * 2)):
+        with pytest.raises(OracleError):
+            o.set_state(site, occ, [1.0] * len(site))
+
+
+# ---------------------------------------------------------------- spectrum
+def test_spectrum_of_single_line_matches_geometric_sum():
+    """A(w) of C(t) = e^{-iEt}: the trapezoid sum is a geometric series with a
+    closed form; the damping is e^{-t/tau}, 1/tau = 0.0577 (App. E)."""
+    E, dt, K = 0.3, 0.05, 400
+    C_t = np.exp(-1j * E * dt * np.arange(K + 1))
+    grid = np.linspace(-2, 2, 41)
+    A = absorption_spectrum(C_t, dt, grid)
+    for w, a in zip(grid, A):
+        z = (1j * (w - E) - 0.0577) * dt
+        s = (1 - np.exp(z * (K + 1))) / (1 - np.exp(z)) - 0.5 * (1 + np.exp(z * K))
+        assert abs(a - (s * dt).real) < 1e-11
+
+
+# ---------------------------------------------------------------- gradients
+def _loss_run(params, keeps=None, record=False, nsteps=12, theta=2e-3):
+    J, g, w, eps = params
+    o = Oracle(3, W.RING, J=J, eps=eps, omega=w, g=g, cap=2, m=1, m_init=1)
+    o.set_state([0, 1], [[0, 0, 0], [0, 0, 0]], [0.8, 0.6j])
+    if record:
+        o.record(True)
+    Cs, masks = [], []
+    for k in range(nsteps):
+        kp = None if keeps is None or k == 0 else keeps[k]
+        o.step(0.1, theta, kp)
+        masks.append(o.last_keep() if k > 0 else None)
+        st = o.stats()
+        Cs.append(st["C_re"] + 1j * st["C_im"])
+    Cs = np.array(Cs)
+    target = 0.3 * np.exp(-0.5j * np.arange(nsteps))
+    P, _ = o.populations()
+    L = P[0] + np.sum(np.abs(Cs - target) ** 2)
+    return L, o, masks, Cs, target
+
+
+def test_adjoint_matches_finite_differences():
+    """Adjoint of the truncated Taylor map with the subspace sequence held fixed
+    agrees with central differences of the same replayed map (extension; the paper
+    has no gradient: parity pinned by finite differences)."""
+    eps = W.seeded_normal(3, 7) * 0.2
+    base = (0.4, 0.7, 1.1, eps)
+    L0, o, masks, Cs, target = _loss_run(base, record=True)
+    t, a = o.rows()
+    dL_dc = np.where(t[:, 0] == 0, 2.0 * a, 0.0)
+    grad = o.backward(len(Cs), dL_dc_final=dL_dc, dL_dC=2.0 * (Cs - target))
+    assert sum(m is not None and (~m).any() for m in masks) > 3   # truncation was active
+
+    def perturbed(p, h):
+        J, g, w, e = base
+        e = e.copy()
+        if p == 0: J += h
+        elif p == 1: g += h
+        elif p == 2: w += h
+        else: e[p - 3] += h
+        return (J, g, w, e)
+
+    for p in range(3 + 3):
+        h = 1e-5
+        lp = _loss_run(perturbed(p, h), keeps=masks)[0]
+        lm = _loss_run(perturbed(p, -h), keeps=masks)[0]
+        fd = (lp - lm) / (2 * h)
+        assert abs(grad[p] - fd) <= 1e-6 * max(1.0, abs(fd)), (p, grad[p], fd)
