@@ -1,0 +1,350 @@
+"""Throughput of the paces per-timestep hot path on GB300.
+
+Workload (default): the 1D Holstein ring N = 16, K = 8 phonons per site,
+J = omega = 1, g = 1.5, dt = 0.02, theta = 1e-7, start |site 0, vacuum>, 1000
+steps (synthetic; the parameterised model stands in for the paper's 1D Holstein
+benchmark).  One bench step is one time step: truncation, m = 2 levels of
+expansion with hash de-duplication and rescue, the P H P build, the Taylor
+propagation and the observables.  The timed window is the last K steps of the
+1000-step trajectory (the largest subspaces): the trajectory is first advanced,
+untimed, to step 1000 - K - W, then W warm-up steps run, then K timed steps.
+
+Metric: H-applied amplitudes/s = sum over timed steps of (Taylor terms x rows of
+H_eff) / device time, with steps/s alongside.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica of the workload
+on its own GPU (the single-instance path does not shard); value is the sum of
+the ranks' units over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2603_07341_gb300 import workloads as W  # noqa: E402
+
+METRIC = "H-applied amplitudes/s"
+UNIT = "amplitudes/s"
+FALLBACK_HBM_GBS = 6800.0
+FP64_PEAK_TFLOPS = 1.25          # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal table)
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def taylor_counts(rec, h_words):
+    """Units, FP64 flops and algorithmic bytes of the propagator over records."""
+    q = rec[:, 6]
+    nnz_off = rec[:, 8] - q
+    terms = rec[:, 9]
+    units = float(np.sum(terms * q))
+    bytes_ = float(np.sum(q * 57.0 + nnz_off * 5.0 + (terms - 1) * (q * 73.0 + nnz_off * 5.0)))
+    flops = float(np.sum(terms * (q * 16.0 + nnz_off * 4.0) + q * 8.0))
+    return units, bytes_, flops
+
+
+def traffic_from_profile(kernel_src):
+    """ncu DRAM bytes per launch of the propagator, if taken on this source."""
+    path = os.path.join(ROOT, "profiles", "k_taylor_ring16_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    return d.get("bytes_per_launch") if d.get("source_sha") == h else None
+
+
+def cpu_baseline(cfg, budget_s=15.0, max_steps=None):
+    """The oracle as it stands on this host: steps from psi(0) until the budget."""
+    from oracle.oracle import Oracle
+    o = Oracle(**W.model_kwargs(cfg))
+    o.set_state(*W.start_state(cfg))
+    units = 0.0
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        o.step(cfg["dt"], cfg["theta"])
+        st = o.stats()
+        units += st["terms"] * st["rows"]
+        steps += 1
+        el = time.perf_counter() - t0
+        if el > budget_s or (max_steps and steps >= max_steps):
+            break
+    return units / el, steps, el, int(st["rows"])
+
+
+def run_reference(args, cfg):
+    ws, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    # W warm-up then K timed oracle steps, each a bounded sample: the trajectory
+    # from psi(0) (the oracle cannot reach the GPU window in minutes)
+    from oracle.oracle import Oracle
+    o = Oracle(**W.model_kwargs(cfg))
+    o.set_state(*W.start_state(cfg))
+    for _ in range(args.warmup):
+        o.step(cfg["dt"], cfg["theta"])
+    units = 0.0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(cfg["dt"], cfg["theta"])
+        st = o.stats()
+        units += st["terms"] * st["rows"]
+    el = time.perf_counter() - t0
+    v = units / el
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "sample": "oracle steps %d..%d from psi(0)"
+                       % (args.warmup + 1, args.warmup + args.steps)},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "oracle steps %d..%d from psi(0), final rows %d"
+                             % (args.warmup + 1, args.warmup + args.steps, int(st["rows"]))},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="ring16", choices=sorted(W.CONFIGS))
+    ap.add_argument("--end-step", type=int, default=None, help="last timed step (default: the config's)")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    cfg = W.CONFIGS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, cfg)
+
+    import torch
+    ws, rank, local = dist_setup()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2603_07341_gb300 import binding as B
+
+    K, Wm = args.steps, args.warmup
+    end = args.end_step or cfg["nsteps"]
+    start = max(0, end - K - Wm)
+    model = W.model_kwargs(cfg)
+    sol = B.Solver(**model)
+    sol.set_state(*W.start_state(cfg))
+    sol.step(cfg["dt"], start, cfg["theta"])            # advance to the window (untimed)
+    sol.step(cfg["dt"], Wm, cfg["theta"])               # warm-up
+    torch.cuda.synchronize()
+    win_state = sol.state() if not args.no_e2e else None
+    rec0 = sol.num_records()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    stream = sol.stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sol.profile(True)
+    sol.stage_stats(reset=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        e0.record(stream)
+        sol.step(cfg["dt"], K, cfg["theta"])
+        e1.record(stream)
+        barrier()
+    sol.profile(False)
+    ms = e0.elapsed_time(e1)
+    stage_ms, launches, stage_bytes = sol.stage_stats(reset=True)
+    rec = sol.observables(rec0, K)
+    units, tbytes, tflops = taylor_counts(rec, sol)
+    t_max = ms
+    total_units = units
+    if dist is not None:
+        tt = torch.tensor([ms, units], dtype=torch.float64, device="cuda")
+        mx = tt.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
+        t_max, total_units = float(mx[0]), float(tt[1])
+    value = total_units / (t_max / 1e3)
+
+    # roofline of the dominant kernel (the propagator), live CUDA events per launch
+    peak_gbs, peak_kind = peaks()
+    tay_ms = stage_ms[3] / K
+    achieved_gbs = tbytes / K / (tay_ms / 1e3) / 1e9
+    achieved_tf = tflops / K / (tay_ms / 1e3) / 1e12
+    frac_hbm = achieved_gbs / peak_gbs
+    frac_fp64 = achieved_tf / FP64_PEAK_TFLOPS
+    src = os.path.join(ROOT, "paper_2603_07341_gb300", "csrc", "kern_taylor.cu")
+    traffic = traffic_from_profile(src)
+    if frac_fp64 > frac_hbm:
+        roof = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s (FP64)",
+                "frac": frac_fp64, "traffic": traffic, "peak_kind": "nominal FP64 (derived)",
+                "hbm_achieved_gbs": achieved_gbs, "hbm_frac": frac_hbm}
+    else:
+        roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": peak_gbs, "unit": "GB/s",
+                "frac": frac_hbm, "traffic": traffic, "peak_kind": peak_kind + " (copy)",
+                "fp64_achieved_tflops": achieved_tf, "fp64_frac": frac_fp64}
+    roof["kernel"] = "k_taylor (one cooperative launch per time step)"
+    roof["algorithmic_bytes_per_launch"] = tbytes / K
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if win_state is not None and rank == 0:
+        site, occ, amps = win_state
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+        site_p, occ_p = pin(site), pin(occ)
+        amps_p = pin(np.stack([amps.real, amps.imag], 1).reshape(-1))
+        sol2 = B.Solver(**model)
+        sol2.set_state(*W.start_state(cfg))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sol2.load_state(site_p, occ_p, amps_p[0::2] + 1j * amps_p[1::2])
+        nrec = sol2.num_records()
+        out_units = 0.0
+        for k in range(K):
+            sol2.step(cfg["dt"], 1, cfg["theta"])
+            r = sol2.observables(nrec + k, 1)
+            out_units += r[0, 9] * r[0, 6]
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        bi = site.nbytes + occ.nbytes + 16 * len(amps)
+        e2e = {"value": out_units / el, "unit": UNIT, "h2d_bytes_per_step": bi / K,
+               "d2h_bytes_per_step": sol2.rec_len * 8,
+               "note": "load_state of the window-start state from pinned host arrays, then per step "
+                       "paces_step(1) and a read-back of its observables record"}
+        sol2.close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        v, nst, el, rows = cpu_baseline(cfg, args.cpu_budget)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "oracle steps 1..%d of %s from psi(0) (%.1f s, final rows %d)"
+                         % (nst, args.workload, el, rows)}
+
+    if rank == 0:
+        q = rec[:, 6]
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": Wm,
+            "ms_per_step": t_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "%s: 1D Holstein ring N=16 K=8 J=1 omega=1 g=1.5 dt=0.02 theta=1e-7, "
+                                   "timed steps %d..%d of %d" % (args.workload, start + Wm + 1, start + Wm + K,
+                                                                  cfg["nsteps"])
+                       if args.workload == "ring16" else args.workload,
+                       "rows_mean": float(np.mean(q)), "rows_max": float(np.max(q)),
+                       "nnz_mean": float(np.mean(rec[:, 8])), "terms_mean": float(np.mean(rec[:, 9])),
+                       "parallelism": "replicas" if ws > 1 else "single GPU",
+                       "l2": "no flush between steps; per-step working set %.0f MB vs 129 MB L2"
+                             % (np.max(q) * (16 * 4 + 8 * 2 + 16 * 2 + 4 * 4 + 5 * 4 + 9) / 1e6)},
+            "steps_per_s": K / (t_max / 1e3),
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(launches[:5].sum()),
+            "stages_ms_per_step": {n: float(m / K) for n, m in zip(B.STAGES, stage_ms)},
+            "stage_algorithmic_gbs": {n: (float(b / (m / 1e3) / 1e9) if m > 0 else None)
+                                      for n, b, m in zip(B.STAGES, stage_bytes, stage_ms)},
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line))
+    sol.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

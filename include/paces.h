@@ -1,0 +1,239 @@
+/*
+ * paces.h -- C interface of the GB300 (sm_103a) per-timestep hot path of paces,
+ * the co-evolving-subspace solver of the time-dependent Schroedinger equation
+ * (arXiv 2603.07341).
+ *
+ * One handle evolves one single-exciton Holstein-type model (Eq. holstein):
+ *
+ *   H = sum_s eps_s |s><s| + J sum_{a != b} M_ab |a><b|
+ *       + sum_j omega_j a_j^dag a_j + sum_s g_s |s><s| (a_s^dag + a_s),
+ *
+ * with a hard cap n_j <= K_j on the phonon number of site j (the paper's
+ * d_pho - 1).  Time is in units of 1/omega_0 and hbar = 1.  A time step is the
+ * map of Sec. 3.4, psi -> Q exp(-i P_m H P_m dt) psi, computed as
+ *   (a1) truncation Q: keep the basis states whose weight |c|^2 reaches theta^2,
+ *   (a2,a3) regrowth of H_eff to the ball of radius m around the kept set in the
+ *        graph H induces on basis states (Eqs. def_neighbor, def_neighbor_k, H_eff),
+ *        with de-duplication in a device hash table,
+ *   (a4) rescue of amplitudes of states that were dropped and re-admitted
+ *        ("post-adaptation detruncation", Sec. 3.3),
+ *   (a5) the restricted Hamiltonian P_m H P_m as a sparse matrix (Sec. 3.3,
+ *        "Generating the effective Hamiltonian"),
+ *   (a6) the Taylor-series action of exp(-i P_m H P_m dt) by repeated SpMV (App. C.1),
+ *   (a7) observables.
+ *
+ * Conventions, for every call below:
+ *   - Host pointers are read during the call only; the library copies what it
+ *     keeps.  The caller owns every array it passes.
+ *   - The library owns its device memory.  It allocates through the allocator
+ *     given to paces_create (or cudaMallocAsync when that is NULL), on the
+ *     stream given to paces_create, and frees it in paces_destroy.
+ *   - All device work is ordered on that stream.  Calls that return host data
+ *     (paces_get_*, paces_observables) synchronise it.
+ *   - Every call returns a status and never aborts the process.  After a
+ *     failure, paces_last_error() describes it.  A failed paces_step leaves
+ *     the state of the last completed step in place.
+ *   - One handle must not be used from two threads at once.
+ */
+#ifndef PACES_H
+#define PACES_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct paces_handle* paces_t;
+
+typedef enum {
+    PACES_OK = 0,
+    PACES_ERR_INVALID = 1,     /* an argument is out of range or inconsistent      */
+    PACES_ERR_KEY_WIDTH = 2,   /* the basis needs more than PACES_MAX_WORDS words  */
+    PACES_ERR_CAPACITY = 3,    /* device memory ran out (after growing)            */
+    PACES_ERR_NOCONVERGE = 4,  /* Taylor series not converged in taylor_nmax terms */
+    PACES_ERR_CUDA = 5,        /* a CUDA runtime call failed                       */
+    PACES_ERR_STATE = 6,       /* call out of order (e.g. step before set_state)   */
+    PACES_ERR_UNSUPPORTED = 7  /* a size this build does not handle (see limits)   */
+} paces_status;
+
+/* build limits */
+#define PACES_MAX_SITES 128     /* sites N                                   */
+#define PACES_MAX_WORDS 4       /* 64-bit words per basis key (256 bits)     */
+#define PACES_MAX_MOVES 64      /* off-diagonal moves per state (deg + 2)    */
+#define PACES_MAX_COEFS 256     /* distinct off-diagonal matrix elements     */
+
+/* lattice kinds: geometry that fixes the hopping pattern M_ab */
+#define PACES_RING 0      /* 1D periodic: M = 1 on (j, j+1 mod N), pairs de-duplicated */
+#define PACES_CHAIN 1     /* 1D open chain, site j at x = j (Eq. tb)                  */
+#define PACES_OPEN2D 2    /* dims[0] x dims[1] open square lattice, j = x + dims0*y    */
+#define PACES_OPEN3D 3    /* dims[0] x dims[1] x dims[2] open cubic lattice            */
+#define PACES_EXPLICIT 4  /* M given in J_explicit[N*N] (symmetric, zero diagonal)    */
+/* coupling kinds (geometric lattices): */
+#define PACES_NEAREST 0   /* M_ab = 1 for Euclidean distance 1                         */
+#define PACES_DIPOLAR 1   /* M_ab = 1 / r_ab^3 for all pairs (computed as 1/(r2*sqrt(r2))) */
+/* arithmetic of the propagator */
+#define PACES_C128 0      /* complex128 everywhere                                      */
+#define PACES_C64_SPMV 1  /* complex64 SpMV terms; FP64 accumulator, norms, magnitudes  */
+
+/* Device memory hook.  alloc returns device memory of `bytes` usable on
+ * `stream` (a cudaStream_t) or NULL; free releases it.  Both may be called from
+ * any paces_* call of the handle. */
+typedef struct {
+    void* ctx;
+    void* (*alloc)(void* ctx, size_t bytes, void* stream);
+    void (*free)(void* ctx, void* ptr, size_t bytes, void* stream);
+} paces_allocator;
+
+/* Model and method parameters (Eq. holstein; App. parameters for m, m_init). */
+typedef struct {
+    int32_t n_sites;            /* N, 1..PACES_MAX_SITES                                */
+    int32_t lattice_kind;       /* PACES_RING .. PACES_EXPLICIT                         */
+    int32_t dims[3];            /* lattice extents for OPEN2D / OPEN3D                  */
+    int32_t coupling_kind;      /* PACES_NEAREST or PACES_DIPOLAR                       */
+    double J;                   /* hopping scale: J_ab = J * M_ab                       */
+    const double* J_explicit;   /* [N*N] pattern M for PACES_EXPLICIT, else NULL        */
+    const double* eps;          /* [N] site energies eps_s, NULL = 0                    */
+    const double* omega;        /* [N] phonon frequencies omega_j, NULL = 0             */
+    const double* g;            /* [N] exciton-phonon couplings g_s, NULL = 0           */
+    const int32_t* phonon_cap;  /* [N] K_j >= 0 (d_pho - 1), required                  */
+    int32_t m;                  /* neighbour order of every step, >= 0 (paper: 2)       */
+    int32_t m_init;             /* neighbour order of H_eff(0); < 0 = until closure     */
+    int32_t precision;          /* PACES_C128 or PACES_C64_SPMV                         */
+    int32_t fixed_terms;        /* > 0: exactly this many series terms, no test         */
+    double taylor_tol;          /* stop at n >= 2 with ||phi_n|| <= tol ||r||; 0 = 1e-15 */
+    int32_t taylor_nmax;        /* series terms allowed before NOCONVERGE; 0 = 200      */
+    uint64_t max_rows;          /* initial row capacity hint; 0 = automatic (it grows)  */
+} paces_params;
+
+/* Basis-key layout (App. A, generalised to mixed radix): a state (s, n_0..n_{N-1})
+ * is the integer  s + N_s * sum_j n_j R_j  split over `words` 64-bit words; no
+ * digit straddles a word.  Word 0 holds the exciton digit s (radix exciton_radix)
+ * in its lowest position; site j lives in word site_word[j] with place value
+ * site_stride[j] and radix site_radix[j] (K_j + 1, or the next power of two when
+ * pow2 != 0, which is chosen whenever it needs no more words).  The all-ones key
+ * is never a valid state. */
+typedef struct {
+    int32_t n_sites;
+    int32_t words;
+    int32_t pow2;
+    int32_t reserved;
+    uint64_t exciton_radix;
+    int32_t site_word[PACES_MAX_SITES];
+    uint64_t site_stride[PACES_MAX_SITES];
+    uint64_t site_radix[PACES_MAX_SITES];
+} paces_layout;
+
+/* Host-only: plan the key layout of a model.  No GPU is touched.
+ * Returns INVALID for bad parameters, KEY_WIDTH if the basis needs more than
+ * PACES_MAX_WORDS words. */
+paces_status paces_plan_layout(const paces_params* params, paces_layout* out);
+
+/* Host-only: encode n states given in A form (App. A: site[n], occ[n*N]) into
+ * keys[n*words] (word 0 first).  Returns INVALID if a digit is out of range. */
+paces_status paces_encode_keys(const paces_layout* layout, int64_t n, const int32_t* site,
+                               const int32_t* occ, uint64_t* keys);
+
+/* Create a handle.  params is copied.  alloc may be NULL (cudaMallocAsync).
+ * stream is a cudaStream_t (NULL = legacy default stream).  The current CUDA
+ * device at this call is the handle's device.  Returns INVALID, KEY_WIDTH,
+ * UNSUPPORTED (more than PACES_MAX_MOVES moves or PACES_MAX_COEFS distinct
+ * matrix elements), CAPACITY or CUDA. */
+paces_status paces_create(const paces_params* params, const paces_allocator* alloc,
+                          void* stream, paces_t* out);
+
+/* Release all device memory of the handle (stream-ordered) and the handle. */
+paces_status paces_destroy(paces_t h);
+
+/* Text of the last error of the handle ("" if none); valid until the next call. */
+const char* paces_last_error(paces_t h);
+
+/* Set psi(0) (Sec. 2; input in A form, App. A): n > 0 distinct states site[n],
+ * occ[n*N], amplitudes amps[2n] as (re, im).  H_eff(0) becomes the ball of
+ * radius m_init around them (Eq. H_eff with m = m_init); the first paces_step
+ * propagates in it without truncating.  psi(0) is also the reference of the
+ * autocorrelation C(t) = <psi(0)|psi(t)> (Sec. 5, Eq. init_state_spec).
+ * Clears the observables.  Returns INVALID (duplicates, digits out of range),
+ * CAPACITY or CUDA. */
+paces_status paces_set_state(paces_t h, int64_t n, const int32_t* site, const int32_t* occ,
+                             const double* amps);
+
+/* Load a mid-trajectory state: n distinct rows with amplitudes become the
+ * current H_eff and vector exactly as a completed step leaves them, so the next
+ * paces_step truncates and regrows from it.  The C(t) reference is kept
+ * (C = 0 if paces_set_state was never called).  Observables are kept. */
+paces_status paces_load_state(paces_t h, int64_t n, const int32_t* site, const int32_t* occ,
+                              const double* amps);
+
+/* Advance nsteps time steps of length dt (> 0) with amplitude threshold theta
+ * (>= 0): keep a row iff re^2 + im^2 >= theta^2, evaluated in FP64 without
+ * contraction.  Appends one observables record per step.  Capacity grows
+ * automatically and the failing step is redone.  Returns INVALID, STATE (no
+ * state set), NOCONVERGE (series did not reach taylor_tol: the state is left
+ * at the end of the last converged step), CAPACITY or CUDA. */
+paces_status paces_step(paces_t h, double dt, int64_t nsteps, double theta);
+
+/* Number of rows q = dim H_eff of the current state. */
+paces_status paces_num_rows(paces_t h, int64_t* rows);
+
+/* Copy the current state to the host in row order: site[rows], occ[rows*N],
+ * amps[2*rows].  max is the capacity of the arrays in rows; INVALID if smaller
+ * than the row count.  Any pointer may be NULL to skip that array. */
+paces_status paces_get_state(paces_t h, int64_t max, int32_t* site, int32_t* occ,
+                             double* amps);
+
+/* Row offsets of the BFS levels of the current H_eff: level 0 (the kept set M,
+ * or psi(0)) is rows [off[0], off[1]), level k rows [off[k], off[k+1]).
+ * Writes up to max entries and the count (levels + 1) to *count. */
+paces_status paces_get_levels(paces_t h, int64_t* off, int32_t max, int32_t* count);
+
+/* Truncation mask of the last step over the rows that entered it (1 = kept).
+ * *n receives its length (0 when the last step did not truncate). */
+paces_status paces_get_keep(paces_t h, uint8_t* keep, int64_t max, int64_t* n);
+
+/* The restricted Hamiltonian P_m H P_m of the current H_eff as the kernels hold
+ * it: per row the count cnt[rows] of off-diagonal entries, their columns and
+ * values in move order (cols/vals of length max_nnz, rows back to back), and
+ * the diagonal diag[rows].  *nnz receives the off-diagonal total; INVALID if it
+ * exceeds max_nnz.  Pointers may be NULL (then only *nnz is returned). */
+paces_status paces_get_hamiltonian(paces_t h, int32_t* cnt, int32_t* cols, double* vals,
+                                   double* diag, int64_t max_nnz, int64_t* nnz);
+
+/* Observables, one record per time index (0 = psi(0), k = after step k).
+ * Each record has paces_record_len() doubles: the fields below, then the site
+ * populations P_s (N values; Eq. RMSD uses them) and the mean phonon numbers
+ * <n_j> (N values). */
+#define PACES_OBS_TIME 0         /* t                                           */
+#define PACES_OBS_NORM 1         /* ||c||^2 after the step                      */
+#define PACES_OBS_NORM_PHI0 2    /* ||c'||^2 entering the propagator            */
+#define PACES_OBS_ENERGY 3       /* <c'|P H P|c'>                               */
+#define PACES_OBS_C_RE 4         /* C(t) = <psi(0)|psi(t)>, real part            */
+#define PACES_OBS_C_IM 5
+#define PACES_OBS_ROWS 6         /* q = dim H_eff                               */
+#define PACES_OBS_KEPT 7         /* |M| after truncation                        */
+#define PACES_OBS_NNZ 8          /* stored entries of P H P incl. the diagonal  */
+#define PACES_OBS_TERMS 9        /* Taylor terms used                           */
+#define PACES_OBS_NORM_BEFORE 10 /* ||c||^2 before truncation                   */
+#define PACES_OBS_FIXED 12       /* fields before P_s                           */
+int32_t paces_record_len(paces_t h);
+/* Number of records held. */
+paces_status paces_num_records(paces_t h, int64_t* n);
+/* Copy records [first, first + count) to out[count * record_len]. */
+paces_status paces_observables(paces_t h, int64_t first, int64_t count, double* out);
+
+/* Stage timing (CUDA events on the handle's stream) and launch counting.
+ * Stages: 0 truncation, 1 expansion+dedup+rescue, 2 Hamiltonian build,
+ * 3 propagation, 4 observables. */
+#define PACES_NUM_STAGES 5
+paces_status paces_profile(paces_t h, int32_t enable);
+/* ms[5]: summed stage times since the last reset; launches[6]: kernels launched
+ * per stage (index 5: set_state and other kernels); bytes[5]: algorithmic bytes
+ * moved per stage (the per-unit figures of the design notes). */
+paces_status paces_stage_stats(paces_t h, double* ms, int64_t* launches, double* bytes,
+                               int32_t reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,360 @@
+// common.cuh -- device-side building blocks of the paces hot path (sm_103a).
+//
+// Basis keys (App. A, mixed radix): a state (s, n_0..n_{N-1}) is stored as W
+// 64-bit words; word 0 holds the exciton digit s lowest, then sites in order;
+// no digit straddles a word.  Moves of H are word additions:
+//   hop s -> t      : word0 += t - s
+//   a_j^dag / a_j   : word[w_j] +/- stride_j           (Eq. holstein terms)
+// Digits are read with division by invariant integers (Granlund & Montgomery,
+// "Division by invariant integers using multiplication", PLDI 1994, Fig. 4.1).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace paces {
+
+constexpr int kMaxSites = 128;
+constexpr int kMaxWords = 4;
+constexpr int kMaxMoves = 64;
+constexpr int kMaxCoefs = 256;
+constexpr int kMaxLevels = 256;
+constexpr int kMaxCap = 255;          // phonon cap K_j per site
+constexpr uint32_t kCand = 0x80000000u;
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+constexpr uint64_t kEmpty = ~0ull;
+constexpr uint32_t kMaxProbe = 1u << 16;
+
+// device error codes (Counters::err)
+enum DevErr : int {
+    kErrNone = 0,
+    kErrRows = 1,        // H_eff outgrew the row capacity
+    kErrProbe = 2,       // hash probe sequence exceeded kMaxProbe (table overloaded)
+    kErrCand = 3,        // candidate index space exhausted
+    kErrNoConverge = 4,  // Taylor series not converged in nmax terms
+    kErrBarrier = 5,     // a grid barrier waited past its time limit
+};
+
+// ---------------------------------------------------------------- division
+struct UDiv {          // q = floor(n / d) for all 64-bit n
+    uint64_t d, m;
+    uint32_t sh1, sh2;
+};
+
+__host__ __device__ inline uint64_t udiv(uint64_t n, const UDiv& v)
+{
+#ifdef __CUDA_ARCH__
+    uint64_t t1 = __umul64hi(v.m, n);
+#else
+    uint64_t t1 = (uint64_t)(((unsigned __int128)v.m * n) >> 64);
+#endif
+    return (t1 + ((n - t1) >> v.sh1)) >> v.sh2;
+}
+
+// ---------------------------------------------------------------- model
+// Everything the kernels need to know about one model, resident in device
+// memory (read through the read-only path).
+struct DevModel {
+    int N, W, D, P;            // sites, key words, max moves, row pitch of P H P
+    int pow2;
+    int nlad;                  // ladder table entries
+    UDiv div_exc;              // word0 / exciton radix (N, or the next power of two)
+    UDiv div_D;                // candidate index / D
+    int word_first[kMaxWords + 1];   // sites of word w: [word_first[w], word_first[w+1])
+    int site_word[kMaxSites];
+    uint64_t stride[kMaxSites];
+    UDiv div_stride[kMaxSites];
+    UDiv div_radix[kMaxSites];
+    int cap[kMaxSites];
+    int gnz[kMaxSites];        // g_s != 0
+    double eps[kMaxSites];
+    double omega[kMaxSites];
+    int adj_off[kMaxSites + 1];  // hops of site s: adj[adj_off[s] .. adj_off[s+1]) ascending t
+    int lad_off[kMaxSites + 1];  // ladder cids of site s: lad_cid[lad_off[s] + k] = cid(g_s sqrt(k+1))
+    uint8_t adj[kMaxSites * (kMaxMoves - 2)];
+    uint8_t adj_cid[kMaxSites * (kMaxMoves - 2)];
+    double coef[kMaxCoefs];
+    double coef_dJ[kMaxCoefs];
+    double coef_dg[kMaxCoefs];
+    int ncoef;
+    uint8_t lad_cid[kMaxSites * kMaxCap];
+};
+
+// Per-handle counters shared by the kernels of a step (device memory).
+struct Counters {
+    uint32_t q;                      // rows of the current H_eff
+    uint32_t q_in;                   // rows of the state that entered the step
+    uint32_t kept;                   // |M|
+    uint32_t nlevels;                // levels recorded in level_off (count - 1)
+    uint32_t level_off[kMaxLevels + 2];
+    unsigned long long nnz;          // off-diagonal entries of P H P
+    int err, err_step, err_info, pad0;
+    unsigned bar_count, bar_gen;
+    int nterms, pad1;
+    double norm_r, norm_phi0, energy, norm_last;
+};
+
+// ---------------------------------------------------------------- keys
+template <int W>
+struct Key {
+    uint64_t w[W];
+};
+
+template <int W>
+__device__ __forceinline__ Key<W> load_key(const uint64_t* __restrict__ keys, uint64_t row)
+{
+    Key<W> k;
+    const uint64_t* p = keys + row * W;
+    if constexpr (W == 2) {
+        ulonglong2 v = *reinterpret_cast<const ulonglong2*>(p);
+        k.w[0] = v.x;
+        k.w[1] = v.y;
+    } else if constexpr (W == 4) {
+        ulonglong2 a = reinterpret_cast<const ulonglong2*>(p)[0];
+        ulonglong2 b = reinterpret_cast<const ulonglong2*>(p)[1];
+        k.w[0] = a.x; k.w[1] = a.y; k.w[2] = b.x; k.w[3] = b.y;
+    } else {
+#pragma unroll
+        for (int i = 0; i < W; ++i) k.w[i] = p[i];
+    }
+    return k;
+}
+
+template <int W>
+__device__ __forceinline__ void store_key(uint64_t* __restrict__ keys, uint64_t row, const Key<W>& k)
+{
+    uint64_t* p = keys + row * W;
+#pragma unroll
+    for (int i = 0; i < W; ++i) p[i] = k.w[i];
+}
+
+template <int W>
+__device__ __forceinline__ bool key_eq(const Key<W>& a, const Key<W>& b)
+{
+    bool e = true;
+#pragma unroll
+    for (int i = 0; i < W; ++i) e &= (a.w[i] == b.w[i]);
+    return e;
+}
+
+// exciton site s of a key
+template <int W>
+__device__ __forceinline__ int key_site(const Key<W>& k, const DevModel* M)
+{
+    uint64_t q = udiv(k.w[0], M->div_exc);
+    return (int)(k.w[0] - q * M->div_exc.d);
+}
+
+// phonon number at site j
+template <int W>
+__device__ __forceinline__ int key_digit(const Key<W>& k, const DevModel* M, int j)
+{
+    uint64_t x = k.w[M->site_word[j]];
+    uint64_t q = udiv(x, M->div_stride[j]);
+    uint64_t q2 = udiv(q, M->div_radix[j]);
+    return (int)(q - q2 * M->div_radix[j].d);
+}
+
+// MurmurHash3 64-bit finaliser (Appleby), applied word by word.
+__device__ __forceinline__ uint64_t fmix64(uint64_t h)
+{
+    h ^= h >> 33;
+    h *= 0xff51afd7ed558ccdull;
+    h ^= h >> 33;
+    h *= 0xc4ceb9fe1a85ec53ull;
+    h ^= h >> 33;
+    return h;
+}
+
+template <int W>
+__device__ __forceinline__ uint64_t key_hash(const Key<W>& k)
+{
+    uint64_t h = fmix64(k.w[0] + 0x9E3779B97F4A7C15ull);
+#pragma unroll
+    for (int i = 1; i < W; ++i) h = fmix64(h ^ k.w[i]);
+    return h;
+}
+
+// Move mv of a state with exciton site s and n_s phonons there:
+//   mv < deg(s): hop to the mv-th neighbour (ascending site index)
+//   mv == deg(s): a_s^dag (valid if g_s != 0 and n_s < K_s)
+//   mv == deg(s)+1: a_s    (valid if g_s != 0 and n_s > 0)
+// Returns false for an invalid move; on success writes the child and its
+// coefficient id.
+template <int W>
+__device__ __forceinline__ bool apply_move(const DevModel* M, const Key<W>& k,
+                                           int s, int ns, int mv, Key<W>& child, int& cid)
+{
+    int a0 = M->adj_off[s], deg = M->adj_off[s + 1] - a0;
+    child = k;
+    if (mv < deg) {
+        int t = M->adj[a0 + mv];
+        child.w[0] = k.w[0] + (uint64_t)t - (uint64_t)s;
+        cid = M->adj_cid[a0 + mv];
+        return true;
+    }
+    if (!M->gnz[s]) return false;
+    int w = M->site_word[s];
+    if (mv == deg) {
+        if (ns >= M->cap[s]) return false;
+        child.w[w] = k.w[w] + M->stride[s];
+        cid = M->lad_cid[M->lad_off[s] + ns];
+        return true;
+    }
+    if (mv == deg + 1) {
+        if (ns <= 0) return false;
+        child.w[w] = k.w[w] - M->stride[s];
+        cid = M->lad_cid[M->lad_off[s] + ns - 1];
+        return true;
+    }
+    return false;
+}
+
+// ---------------------------------------------------------------- hash table
+// Open addressing with linear probing.  Slot = tag word (fingerprint << 32 |
+// value) followed by the W key words, padded to a multiple of 16 bytes.
+// value = row index, or kCand | candidate index while a level is being built.
+template <int W>
+struct Slot {
+    static constexpr int kWords = (W == 1) ? 2 : (W <= 3 ? 4 : 6);
+};
+
+// Home slot from the low 32 hash bits by multiplicative range reduction (any
+// table size below 2^32); the fingerprint comes from the high 32 bits.
+__device__ __forceinline__ uint64_t slot_home(uint64_t h, uint64_t slots)
+{
+    return ((h & 0xFFFFFFFFull) * slots) >> 32;
+}
+
+__device__ __forceinline__ uint64_t slot_next(uint64_t pos, uint64_t slots)
+{
+    return pos + 1 == slots ? 0 : pos + 1;
+}
+
+template <int W>
+__device__ __forceinline__ uint32_t fingerprint(uint64_t h)
+{
+    uint32_t f = (uint32_t)(h >> 32);
+    return f == 0xFFFFFFFFu ? 0xFFFFFFFEu : f;
+}
+
+// Read-only lookup: row of key or -1.
+template <int W>
+__device__ __forceinline__ int64_t table_lookup(const uint64_t* __restrict__ table, uint64_t slots,
+                                                const Key<W>& key)
+{
+    uint64_t h = key_hash<W>(key);
+    uint64_t fp = fingerprint<W>(h);
+    uint64_t pos = slot_home(h, slots);
+    for (uint32_t probe = 0; probe < kMaxProbe; ++probe) {
+        const uint64_t* sl = table + pos * Slot<W>::kWords;
+        uint64_t tag = __ldg(sl);
+        if (tag == kEmpty) return -1;
+        if ((tag >> 32) == fp) {
+            bool eq = true;
+#pragma unroll
+            for (int i = 0; i < W; ++i) eq &= (__ldg(sl + 1 + i) == key.w[i]);
+            if (eq) return (int64_t)(uint32_t)tag;
+        }
+        pos = slot_next(pos, slots);
+    }
+    return -1;
+}
+
+// Insert a unique row key (no duplicates possible): claim the first empty slot.
+template <int W>
+__device__ __forceinline__ bool table_insert_unique(uint64_t* table, uint64_t slots, const Key<W>& key,
+                                                    uint32_t row)
+{
+    uint64_t h = key_hash<W>(key);
+    uint64_t tag = ((uint64_t)fingerprint<W>(h) << 32) | row;
+    uint64_t pos = slot_home(h, slots);
+    for (uint32_t probe = 0; probe < kMaxProbe; ++probe) {
+        uint64_t* sl = table + pos * Slot<W>::kWords;
+        if (__ldcg(sl) == kEmpty) {
+            unsigned long long old = atomicCAS((unsigned long long*)sl, kEmpty, tag);
+            if (old == kEmpty) {
+#pragma unroll
+                for (int i = 0; i < W; ++i) sl[1 + i] = key.w[i];
+                return true;
+            }
+        }
+        pos = slot_next(pos, slots);
+    }
+    return false;
+}
+
+// ---------------------------------------------------------------- reductions
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v)
+{
+    int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// Exclusive scan of one value per thread over the block; *total gets the sum.
+template <int BLOCK>
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* total)
+{
+    static_assert(BLOCK % 32 == 0 && BLOCK <= 1024, "block size");
+    __shared__ uint32_t ws[BLOCK / 32];
+    __shared__ uint32_t tot;
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = warp_incl_scan(v);
+    if (lane == 31) ws[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t x = lane < BLOCK / 32 ? ws[lane] : 0u;
+        uint32_t xi = warp_incl_scan(x);
+        if (lane < BLOCK / 32) ws[lane] = xi - x;
+        if (lane == 31) tot = xi;
+    }
+    __syncthreads();
+    uint32_t r = ws[warp] + inc - v;
+    *total = tot;
+    __syncthreads();
+    return r;
+}
+
+// Deterministic block sum of several doubles (fixed shuffle tree + fixed warp order).
+template <int BLOCK, int K>
+__device__ __forceinline__ void block_sum(double (&v)[K], double* out /* smem or global, K values */)
+{
+    __shared__ double red[BLOCK / 32][K];
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double s = warp_sum(v[k]);
+        if (lane == 0) red[warp][k] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < K) {
+        double s = 0.0;
+        for (int w = 0; w < BLOCK / 32; ++w) s += red[w][threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------- grid barrier
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+constexpr uint64_t kBarrierTimeoutNs = 20ull * 1000 * 1000 * 1000;   // 20 s
+
+}  // namespace paces

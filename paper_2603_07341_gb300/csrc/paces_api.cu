@@ -1,0 +1,1068 @@
+// paces_api.cu -- host runtime behind include/paces.h: model tables, key layout,
+// device memory through the caller's allocator, the step driver (stage kernels
+// enqueued back to back on one stream, device-side error word checked once per
+// chunk of steps), automatic capacity growth, and the export calls.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "paces.h"
+#include "runtime.h"
+
+using namespace paces;
+
+namespace {
+
+constexpr int kChunk = 8;                 // steps enqueued between error checks
+constexpr uint32_t kMinRows = 1u << 10;
+constexpr uint32_t kDefaultRows = 1u << 16;
+constexpr uint64_t kMaxRowsHard = (1ull << 31) - 1;
+
+struct Stage {
+    enum { Trunc = 0, Expand = 1, Csr = 2, Taylor = 3, Obs = 4, Other = 5 };
+};
+
+uint64_t next_pow2(uint64_t v)
+{
+    uint64_t p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+UDiv make_udiv(uint64_t d)
+{
+    UDiv u;
+    u.d = d;
+    int l = 0;
+    while (l < 64 && (((unsigned __int128)1) << l) < d) ++l;          // l = ceil(log2 d)
+    unsigned __int128 two64 = ((unsigned __int128)1) << 64;
+    unsigned __int128 twol = ((unsigned __int128)1) << l;
+    u.m = (uint64_t)((two64 * (twol - d)) / d + 1);
+    u.sh1 = l < 1 ? (uint32_t)l : 1u;
+    u.sh2 = l > 1 ? (uint32_t)(l - 1) : 0u;
+    return u;
+}
+
+struct DevAlloc {
+    void* p;
+    size_t bytes;
+};
+
+}  // namespace
+
+struct paces_handle {
+    paces_params prm;
+    std::vector<double> eps, omega, g, Jx;
+    std::vector<int32_t> cap;
+    paces_layout lay;
+    DevModel* hmodel = nullptr;   // host copy
+    int W = 1, D = 4, P = 4, N = 1, lpr = 1;
+    paces_allocator alloc{};
+    bool has_alloc = false;
+    cudaStream_t st = nullptr;
+    int device = 0, sms = 1;
+    std::string err;
+
+    Bufs b{};
+    std::vector<DevAlloc> row_allocs;      // freed on growth
+    std::vector<DevAlloc> fixed_allocs;    // model, counters, obs, psi0
+    Counters* hctr = nullptr;              // pinned host mirror
+    uint32_t cap_rows = 0;
+
+    int gen = 0;
+    bool fresh = false, has_state = false, csr_valid = false;
+    bool last_truncated = false;
+    double time = 0.0;
+    int64_t n_records = 0, obs_cap = 0;
+    int64_t step_index = 0;
+    int64_t psi0_cap = 0;
+
+    bool profiling = false;
+    double stage_ms[PACES_NUM_STAGES] = {0};
+    double stage_bytes[PACES_NUM_STAGES] = {0};
+    int64_t stage_launch[PACES_NUM_STAGES + 1] = {0};
+    std::vector<cudaEvent_t> evpool;
+};
+
+namespace {
+
+paces_status fail(paces_t h, paces_status s, const std::string& msg)
+{
+    if (h) h->err = msg;
+    return s;
+}
+
+paces_status cuda_fail(paces_t h, cudaError_t e, const char* where)
+{
+    return fail(h, PACES_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CUDA_TRY(h, call)                                                  \
+    do {                                                                   \
+        cudaError_t e_ = (call);                                           \
+        if (e_ != cudaSuccess) return cuda_fail((h), e_, #call);           \
+    } while (0)
+
+void* dev_alloc(paces_t h, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~(size_t)255;
+    void* p = nullptr;
+    if (h->has_alloc) {
+        p = h->alloc.alloc(h->alloc.ctx, bytes, (void*)h->st);
+    } else if (cudaMallocAsync(&p, bytes, h->st) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    return p;
+}
+
+void dev_free(paces_t h, DevAlloc a)
+{
+    if (!a.p) return;
+    if (h->has_alloc) h->alloc.free(h->alloc.ctx, a.p, a.bytes, (void*)h->st);
+    else cudaFreeAsync(a.p, h->st);
+}
+
+template <typename T>
+T* alloc_track(paces_t h, std::vector<DevAlloc>& v, size_t count)
+{
+    size_t bytes = ((sizeof(T) * count) + 255) & ~(size_t)255;
+    if (bytes == 0) bytes = 256;
+    void* p = dev_alloc(h, bytes);
+    if (p) v.push_back({p, bytes});
+    return (T*)p;
+}
+
+// ---------------------------------------------------------------- model tables
+double hop_pattern(const paces_params& p, const std::vector<double>& Jx, int a, int b)
+{
+    int N = p.n_sites;
+    if (a == b) return 0.0;
+    if (p.lattice_kind == PACES_EXPLICIT) return Jx[(size_t)a * N + b];
+    if (p.lattice_kind == PACES_RING) {
+        if (N < 2) return 0.0;
+        return ((a + 1) % N == b || (b + 1) % N == a) ? 1.0 : 0.0;
+    }
+    int d0 = N, d1 = 1;
+    if (p.lattice_kind == PACES_OPEN2D || p.lattice_kind == PACES_OPEN3D) {
+        d0 = p.dims[0];
+        d1 = p.dims[1];
+    }
+    int ax = a % d0, ay = (a / d0) % d1, az = a / (d0 * d1);
+    int bx = b % d0, by = (b / d0) % d1, bz = b / (d0 * d1);
+    double dx = ax - bx, dy = ay - by, dz = az - bz;
+    double r2 = dx * dx + dy * dy + dz * dz;
+    if (p.coupling_kind == PACES_NEAREST) return r2 == 1.0 ? 1.0 : 0.0;
+    return 1.0 / (r2 * std::sqrt(r2));
+}
+
+paces_status check_params(const paces_params* p, std::string& why)
+{
+    if (!p) { why = "params is NULL"; return PACES_ERR_INVALID; }
+    int N = p->n_sites;
+    if (N < 1 || N > PACES_MAX_SITES) { why = "n_sites out of range"; return PACES_ERR_INVALID; }
+    if (p->lattice_kind < 0 || p->lattice_kind > 4) { why = "lattice_kind"; return PACES_ERR_INVALID; }
+    if (p->coupling_kind < 0 || p->coupling_kind > 1) { why = "coupling_kind"; return PACES_ERR_INVALID; }
+    if (p->lattice_kind == PACES_RING && p->coupling_kind != PACES_NEAREST) {
+        why = "a ring has nearest-neighbour coupling only";
+        return PACES_ERR_INVALID;
+    }
+    if (p->lattice_kind == PACES_OPEN2D && (p->dims[0] < 1 || p->dims[1] < 1 || p->dims[0] * p->dims[1] != N)) {
+        why = "dims[0]*dims[1] must equal n_sites";
+        return PACES_ERR_INVALID;
+    }
+    if (p->lattice_kind == PACES_OPEN3D &&
+        (p->dims[0] < 1 || p->dims[1] < 1 || p->dims[2] < 1 || p->dims[0] * p->dims[1] * p->dims[2] != N)) {
+        why = "dims[0]*dims[1]*dims[2] must equal n_sites";
+        return PACES_ERR_INVALID;
+    }
+    if (p->lattice_kind == PACES_EXPLICIT && !p->J_explicit) { why = "J_explicit is NULL"; return PACES_ERR_INVALID; }
+    if (!p->phonon_cap) { why = "phonon_cap is NULL"; return PACES_ERR_INVALID; }
+    for (int j = 0; j < N; ++j)
+        if (p->phonon_cap[j] < 0 || p->phonon_cap[j] > kMaxCap) { why = "phonon_cap out of range"; return PACES_ERR_INVALID; }
+    if (p->m < 0) { why = "m < 0"; return PACES_ERR_INVALID; }
+    if (p->precision != PACES_C128 && p->precision != PACES_C64_SPMV) { why = "precision"; return PACES_ERR_INVALID; }
+    if (p->taylor_tol < 0 || p->taylor_nmax < 0 || p->fixed_terms < 0) { why = "series limits"; return PACES_ERR_INVALID; }
+    return PACES_OK;
+}
+
+paces_status plan(const paces_params* p, paces_layout* L, std::string& why)
+{
+    paces_status s = check_params(p, why);
+    if (s) return s;
+    int N = p->n_sites;
+    const unsigned __int128 lim = (((unsigned __int128)1) << 64) - 1;   // keep the all-ones key invalid
+    paces_layout cand[2];
+    for (int mode = 0; mode < 2; ++mode) {       // 0: power-of-two radices, 1: dense
+        paces_layout& l = cand[mode];
+        std::memset(&l, 0, sizeof(l));
+        l.n_sites = N;
+        l.pow2 = mode == 0;
+        l.exciton_radix = mode == 0 ? next_pow2((uint64_t)N) : (uint64_t)N;
+        int w = 0;
+        unsigned __int128 prod = l.exciton_radix;
+        for (int j = 0; j < N; ++j) {
+            uint64_t r = (uint64_t)p->phonon_cap[j] + 1;
+            if (mode == 0) r = next_pow2(r);
+            if (prod * r > lim) {
+                ++w;
+                prod = 1;
+            }
+            l.site_word[j] = w;
+            l.site_stride[j] = (uint64_t)prod;
+            l.site_radix[j] = r;
+            prod *= r;
+        }
+        l.words = w + 1;
+    }
+    *L = cand[0].words <= cand[1].words ? cand[0] : cand[1];
+    if (L->words > PACES_MAX_WORDS) {
+        why = "the basis needs " + std::to_string(L->words) + " 64-bit words";
+        return PACES_ERR_KEY_WIDTH;
+    }
+    return PACES_OK;
+}
+
+paces_status encode(const paces_layout* L, int64_t n, const int32_t* site, const int32_t* occ, uint64_t* keys,
+                    std::string& why)
+{
+    int N = L->n_sites, W = L->words;
+    for (int64_t i = 0; i < n; ++i) {
+        uint64_t* k = keys + i * W;
+        for (int w = 0; w < W; ++w) k[w] = 0;
+        if (site[i] < 0 || site[i] >= N) { why = "site out of range"; return PACES_ERR_INVALID; }
+        k[0] = (uint64_t)site[i];
+        for (int j = 0; j < N; ++j) {
+            int32_t v = occ[i * N + j];
+            uint64_t cap = L->site_radix[j];
+            if (v < 0 || (uint64_t)v >= cap) { why = "occupation out of range"; return PACES_ERR_INVALID; }
+            k[L->site_word[j]] += (uint64_t)v * L->site_stride[j];
+        }
+    }
+    return PACES_OK;
+}
+
+// ---------------------------------------------------------------- buffers
+size_t slot_words(int W) { return W == 1 ? 2 : (W <= 3 ? 4 : 6); }
+
+void free_rows(paces_t h)
+{
+    for (auto& a : h->row_allocs) dev_free(h, a);
+    h->row_allocs.clear();
+}
+
+// Allocate every row-sized buffer for cap rows; on failure frees what it got.
+paces_status alloc_rows(paces_t h, uint32_t cap, std::vector<DevAlloc>& out, Bufs& b)
+{
+    std::vector<DevAlloc> saved;
+    saved.swap(h->row_allocs);
+    uint64_t slots = 2ull * cap + 1;           // load factor <= 0.5, any size below 2^32
+    size_t sw = slot_words(h->W);
+    bool ok = true;
+    auto chk = [&](void* p) { ok = ok && p; };
+    for (int g = 0; g < 2; ++g) {
+        chk(b.keys[g] = alloc_track<uint64_t>(h, h->row_allocs, (size_t)cap * h->W));
+        chk(b.table[g] = alloc_track<uint64_t>(h, h->row_allocs, slots * sw));
+    }
+    for (int v = 0; v < 4; ++v) chk(b.V[v] = alloc_track<double2>(h, h->row_allocs, cap));
+    if (h->prm.precision == PACES_C64_SPMV) {
+        for (int v = 0; v < 2; ++v) chk(b.F[v] = alloc_track<float2>(h, h->row_allocs, cap));
+    } else {
+        b.F[0] = b.F[1] = nullptr;
+    }
+    chk(b.col = alloc_track<uint32_t>(h, h->row_allocs, (size_t)cap * h->P));
+    chk(b.cid = alloc_track<uint8_t>(h, h->row_allocs, (size_t)cap * h->P));
+    chk(b.cnt = alloc_track<uint8_t>(h, h->row_allocs, cap));
+    chk(b.diag = alloc_track<double>(h, h->row_allocs, cap));
+    chk(b.cand_slot = alloc_track<uint32_t>(h, h->row_allocs, (size_t)cap * h->D));
+    chk(b.masks = alloc_track<uint64_t>(h, h->row_allocs, cap));
+    chk(b.keepw = alloc_track<uint32_t>(h, h->row_allocs, cap / 32 + 64));
+    out.swap(h->row_allocs);
+    h->row_allocs.swap(saved);
+    if (!ok) {
+        for (auto& a : out) dev_free(h, a);
+        out.clear();
+        return PACES_ERR_CAPACITY;
+    }
+    b.table_slots = slots;
+    b.cap_rows = cap;
+    b.cand_cap = (uint64_t)cap * h->D;
+    return PACES_OK;
+}
+
+paces_status set_counters(paces_t h)
+{
+    CUDA_TRY(h, cudaMemcpyAsync(h->b.ctr, h->hctr, sizeof(Counters), cudaMemcpyHostToDevice, h->st));
+    CUDA_TRY(h, cudaStreamSynchronize(h->st));
+    return PACES_OK;
+}
+
+paces_status read_counters(paces_t h)
+{
+    CUDA_TRY(h, cudaMemcpyAsync(h->hctr, h->b.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, h->st));
+    CUDA_TRY(h, cudaStreamSynchronize(h->st));
+    return PACES_OK;
+}
+
+void count(paces_t h, int stage, int n)
+{
+    if (n > 0) h->stage_launch[stage] += n;
+}
+
+paces_status clear_table(paces_t h, int gen)
+{
+    CUDA_TRY(h, cudaMemsetAsync(h->b.table[gen], 0xFF, h->b.table_slots * slot_words(h->W) * 8, h->st));
+    return PACES_OK;
+}
+
+// Grow the row capacity to at least `want`, keeping the current state (rows
+// [0, q) of generation gen in keys and in vector V[vec]) and rebuilding its
+// table.  Only the live state is stashed while the old buffers are released,
+// so the new capacity may use nearly all of the device memory.  Growth tries
+// 2x, then 1.5x, then 1.25x, then exactly `want`.
+paces_status grow(paces_t h, uint64_t want, uint32_t q, int vec)
+{
+    uint64_t cur = h->cap_rows, base = std::max<uint64_t>(cur, kMinRows);
+    if (want > kMaxRowsHard) return fail(h, PACES_ERR_CAPACITY, "more rows than 32-bit row indices allow");
+    uint64_t* sk = nullptr;
+    double2* sv = nullptr;
+    size_t kb = (size_t)q * h->W * 8, vb = (size_t)q * sizeof(double2);
+    if (q > 0 && cur > 0) {
+        sk = (uint64_t*)dev_alloc(h, kb);
+        sv = (double2*)dev_alloc(h, vb);
+        if (!sk || !sv) {
+            if (sk) dev_free(h, {sk, kb});
+            if (sv) dev_free(h, {sv, vb});
+            return fail(h, PACES_ERR_CAPACITY, "no room to stash the state while growing");
+        }
+        CUDA_TRY(h, cudaMemcpyAsync(sk, h->b.keys[h->gen], kb, cudaMemcpyDeviceToDevice, h->st));
+        CUDA_TRY(h, cudaMemcpyAsync(sv, h->b.V[vec], vb, cudaMemcpyDeviceToDevice, h->st));
+    }
+    free_rows(h);
+    Bufs nb = h->b;
+    std::vector<DevAlloc> na;
+    uint64_t tries[5] = {base * 2, base + base / 2, base + base / 4, want, cur};
+    uint64_t got = 0;
+    for (int t = 0; t < 5 && !got; ++t) {
+        uint64_t cap = std::min<uint64_t>(std::max<uint64_t>(tries[t], t < 4 ? want : 0), kMaxRowsHard);
+        if (cap == 0 || (t == 4 && cap < q)) continue;
+        if (alloc_rows(h, (uint32_t)cap, na, nb) == PACES_OK) got = cap;
+    }
+    if (!got) {
+        if (sk) dev_free(h, {sk, kb});
+        if (sv) dev_free(h, {sv, vb});
+        h->has_state = false;
+        return fail(h, PACES_ERR_CAPACITY, "device allocation failed; the state was lost");
+    }
+    h->row_allocs.swap(na);
+    h->b = nb;
+    h->cap_rows = (uint32_t)got;
+    if (sk) {
+        CUDA_TRY(h, cudaMemcpyAsync(h->b.keys[h->gen], sk, kb, cudaMemcpyDeviceToDevice, h->st));
+        CUDA_TRY(h, cudaMemcpyAsync(h->b.V[vec], sv, vb, cudaMemcpyDeviceToDevice, h->st));
+        dev_free(h, {sk, kb});
+        dev_free(h, {sv, vb});
+    }
+    paces_status s = clear_table(h, h->gen);
+    if (s) return s;
+    if (q > 0) count(h, Stage::Other, launch_insert_rows(h->b, h->gen, q, h->st));
+    CUDA_TRY(h, cudaGetLastError());
+    if (got < want) return fail(h, PACES_ERR_CAPACITY, "device memory exhausted at " + std::to_string(got) + " rows");
+    return PACES_OK;
+}
+
+paces_status ensure_obs(paces_t h, int64_t need)
+{
+    if (need <= h->obs_cap) return PACES_OK;
+    int64_t ncap = std::max<int64_t>(need, std::max<int64_t>(64, 2 * h->obs_cap));
+    size_t rl = (size_t)h->b.rec_len;
+    double* nb = (double*)dev_alloc(h, sizeof(double) * rl * ncap);
+    if (!nb) return fail(h, PACES_ERR_CAPACITY, "observables buffer");
+    CUDA_TRY(h, cudaMemsetAsync(nb, 0, sizeof(double) * rl * ncap, h->st));
+    if (h->b.obs) {
+        if (h->n_records > 0)
+            CUDA_TRY(h, cudaMemcpyAsync(nb, h->b.obs, sizeof(double) * rl * h->n_records, cudaMemcpyDeviceToDevice,
+                                        h->st));
+        for (auto it = h->fixed_allocs.begin(); it != h->fixed_allocs.end(); ++it)
+            if (it->p == h->b.obs) {
+                dev_free(h, *it);
+                h->fixed_allocs.erase(it);
+                break;
+            }
+    }
+    h->fixed_allocs.push_back({nb, sizeof(double) * rl * ncap});
+    h->b.obs = nb;
+    h->obs_cap = ncap;
+    return PACES_OK;
+}
+
+TaylorParams taylor_params(paces_t h, double dt, int step)
+{
+    TaylorParams p;
+    p.dt = dt;
+    double tol = h->prm.taylor_tol > 0 ? h->prm.taylor_tol : 1e-15;
+    p.tol2 = tol * tol;
+    p.nmax = h->prm.taylor_nmax > 0 ? h->prm.taylor_nmax : 200;
+    p.fixed_terms = h->prm.fixed_terms;
+    p.step = step;
+    p.lpr = h->lpr;
+    p.c64 = h->prm.precision == PACES_C64_SPMV;
+    return p;
+}
+
+cudaEvent_t ev(paces_t h, size_t i)
+{
+    while (h->evpool.size() <= i) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        h->evpool.push_back(e);
+    }
+    return h->evpool[i];
+}
+
+// Enqueue one time step.  ev_base: first of 6 events (profiling only).
+void enqueue_step(paces_t h, double dt, double th2, int64_t rec, size_t ev_base)
+{
+    const Bufs& b = h->b;
+    int step = (int)(h->step_index & 0x7fffffff);
+    auto mark = [&](int k) {
+        if (h->profiling) cudaEventRecord(ev(h, ev_base + k), h->st);
+    };
+    mark(0);
+    int gen = h->gen;
+    bool was_fresh = h->fresh;
+    if (!h->fresh) {
+        int gout = 1 - gen;
+        clear_table(h, gout);
+        count(h, Stage::Trunc, launch_truncate(b, gen, gout, th2, step, h->st));
+        mark(1);
+        for (int f = 0; f < h->prm.m; ++f) count(h, Stage::Expand, launch_level(b, gout, f, gen, step, h->st));
+        gen = gout;
+        h->last_truncated = true;
+    } else {
+        mark(1);
+        h->last_truncated = false;
+    }
+    mark(2);
+    count(h, Stage::Csr, launch_csr(b, gen, h->st));
+    mark(3);
+    count(h, Stage::Taylor, launch_taylor(b, taylor_params(h, dt, step), h->st));
+    mark(4);
+    h->time += dt;
+    count(h, Stage::Obs, launch_observe(b, gen, b.V[0], h->time, rec, was_fresh ? 2 : 0, h->st));
+    mark(5);
+    h->gen = gen;
+    h->fresh = false;
+    h->csr_valid = true;
+    h->step_index += 1;
+}
+
+// Algorithmic bytes of one step from its record (the per-unit figures of the
+// design notes); fills bytes[5].
+void step_bytes(paces_t h, const double* r, double q_in, bool truncated, double* bytes)
+{
+    double W8 = 8.0 * h->W, q = r[PACES_OBS_ROWS], kept = r[PACES_OBS_KEPT];
+    double nnz_off = r[PACES_OBS_NNZ] - q, terms = r[PACES_OBS_TERMS];
+    double slot = 8.0 * slot_words(h->W);
+    if (truncated) {
+        bytes[0] += q_in * (16.0 + 0.25) + kept * (2.0 * (W8 + 16.0) + slot);
+        // every row is a frontier row once: key read twice, D candidate slots
+        // written and read, its winner mask written and read; each new row: key,
+        // table slot, one rescue probe sector, c'
+        double newrows = q - kept;
+        bytes[1] += q * (2.0 * W8 + 8.0 * h->D + 16.0) + newrows * (W8 + slot + 32.0 + 16.0);
+    }
+    bytes[2] += q * (W8 + 9.0) + nnz_off * 5.0 + q * h->D * 32.0;
+    if (terms >= 1) bytes[3] += q * 57.0 + nnz_off * 5.0 + (terms - 1) * (q * 73.0 + nnz_off * 5.0);
+    bytes[4] += q * (W8 + 16.0);
+}
+
+}  // namespace
+
+// ======================================================================== C ABI
+extern "C" {
+
+paces_status paces_plan_layout(const paces_params* params, paces_layout* out)
+{
+    std::string why;
+    if (!out) return PACES_ERR_INVALID;
+    return plan(params, out, why);
+}
+
+paces_status paces_encode_keys(const paces_layout* layout, int64_t n, const int32_t* site, const int32_t* occ,
+                               uint64_t* keys)
+{
+    std::string why;
+    if (!layout || n < 0 || (n > 0 && (!site || !occ || !keys))) return PACES_ERR_INVALID;
+    if (layout->words < 1 || layout->words > PACES_MAX_WORDS) return PACES_ERR_INVALID;
+    return encode(layout, n, site, occ, keys, why);
+}
+
+paces_status paces_create(const paces_params* params, const paces_allocator* alloc, void* stream, paces_t* out)
+{
+    if (!out) return PACES_ERR_INVALID;
+    *out = nullptr;
+    std::string why;
+    paces_layout L;
+    paces_status s = plan(params, &L, why);
+    if (s) return s;
+    paces_t h = new paces_handle();
+    h->prm = *params;
+    int N = params->n_sites;
+    h->N = N;
+    h->lay = L;
+    h->W = L.words;
+    h->eps.assign(N, 0.0);
+    h->omega.assign(N, 0.0);
+    h->g.assign(N, 0.0);
+    h->cap.assign(params->phonon_cap, params->phonon_cap + N);
+    for (int j = 0; j < N; ++j) {
+        if (params->eps) h->eps[j] = params->eps[j];
+        if (params->omega) h->omega[j] = params->omega[j];
+        if (params->g) h->g[j] = params->g[j];
+    }
+    if (params->lattice_kind == PACES_EXPLICIT) h->Jx.assign(params->J_explicit, params->J_explicit + (size_t)N * N);
+    h->prm.eps = h->prm.omega = h->prm.g = h->prm.J_explicit = nullptr;
+    h->prm.phonon_cap = nullptr;
+    if (alloc && alloc->alloc && alloc->free) {
+        h->alloc = *alloc;
+        h->has_alloc = true;
+    }
+    h->st = (cudaStream_t)stream;
+
+    // model tables
+    DevModel* M = new DevModel();
+    std::memset(M, 0, sizeof(DevModel));
+    h->hmodel = M;
+    M->N = N;
+    M->W = L.words;
+    M->pow2 = L.pow2;
+    M->div_exc = make_udiv(L.exciton_radix);
+    int w = 0;
+    M->word_first[0] = 0;
+    for (int j = 0; j < N; ++j) {
+        while (L.site_word[j] > w) M->word_first[++w] = j;
+        M->site_word[j] = L.site_word[j];
+        M->stride[j] = L.site_stride[j];
+        M->div_stride[j] = make_udiv(L.site_stride[j]);
+        M->div_radix[j] = make_udiv(L.site_radix[j]);
+        M->cap[j] = h->cap[j];
+        M->gnz[j] = h->g[j] != 0.0;
+        M->eps[j] = h->eps[j];
+        M->omega[j] = h->omega[j];
+    }
+    while (w < L.words) M->word_first[++w] = N;
+    std::map<std::tuple<double, double, double>, int> ids;
+    auto cid_of = [&](double v, double dJ, double dg) -> int {
+        auto key = std::make_tuple(v, dJ, dg);
+        auto it = ids.find(key);
+        if (it != ids.end()) return it->second;
+        int id = (int)ids.size();
+        ids[key] = id;
+        if (id < kMaxCoefs) {
+            M->coef[id] = v;
+            M->coef_dJ[id] = dJ;
+            M->coef_dg[id] = dg;
+        }
+        return id;
+    };
+    int maxdeg = 0, nadj = 0, nlad = 0;
+    for (int si = 0; si < N; ++si) {
+        M->adj_off[si] = nadj;
+        for (int t = 0; t < N; ++t) {
+            double p = hop_pattern(h->prm, h->Jx, t, si);
+            double v = params->J * p;
+            if (t == si || v == 0.0) continue;
+            if (nadj - M->adj_off[si] >= kMaxMoves - 2) {
+                delete M;
+                delete h;
+                return PACES_ERR_UNSUPPORTED;
+            }
+            M->adj[nadj] = (uint8_t)t;
+            M->adj_cid[nadj] = (uint8_t)std::min(cid_of(v, p, 0.0), 255);
+            ++nadj;
+        }
+        maxdeg = std::max(maxdeg, nadj - M->adj_off[si]);
+        M->lad_off[si] = nlad;
+        for (int k = 0; k < h->cap[si]; ++k) {
+            double sq = std::sqrt((double)(k + 1));
+            M->lad_cid[nlad + k] = (uint8_t)std::min(cid_of(h->g[si] * sq, 0.0, sq), 255);
+        }
+        nlad += h->cap[si];
+    }
+    M->adj_off[N] = nadj;
+    M->lad_off[N] = nlad;
+    M->nlad = nlad;
+    M->ncoef = (int)ids.size();
+    if (M->ncoef > kMaxCoefs) {
+        delete M;
+        delete h;
+        return PACES_ERR_UNSUPPORTED;
+    }
+    h->D = maxdeg + 2;
+    h->P = (h->D + 3) / 4 * 4;
+    M->D = h->D;
+    M->P = h->P;
+    M->div_D = make_udiv((uint64_t)h->D);
+    h->lpr = h->P <= 8 ? 1 : (h->P <= 24 ? 4 : 8);
+
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e != cudaSuccess) {
+        delete M;
+        delete h;
+        return PACES_ERR_CUDA;
+    }
+    Bufs& b = h->b;
+    b.W = h->W;
+    b.D = h->D;
+    b.P = h->P;
+    b.N = N;
+    b.G = std::min(kMaxChunkBlocks, h->sms * 4);
+    b.grid = h->sms * 8;
+    int bps = taylor_blocks_per_sm(h->lpr, 0);
+    if (bps < 1) bps = 1;
+    b.taylor_grid = h->sms * bps;
+    b.rec_len = PACES_OBS_FIXED + 2 * N;
+
+    b.model = alloc_track<DevModel>(h, h->fixed_allocs, 1);
+    b.ctr = alloc_track<Counters>(h, h->fixed_allocs, 1);
+    b.blk_cnt = alloc_track<uint32_t>(h, h->fixed_allocs, kMaxChunkBlocks);
+    b.blk_off = alloc_track<uint32_t>(h, h->fixed_allocs, kMaxChunkBlocks);
+    b.partials = alloc_track<double>(h, h->fixed_allocs, 8 * (size_t)b.taylor_grid + 16);
+    b.obs_part = alloc_track<unsigned long long>(h, h->fixed_allocs, (size_t)b.grid * (2 * kMaxSites + 1) * 2);
+    if (!b.model || !b.ctr || !b.blk_cnt || !b.blk_off || !b.partials || !b.obs_part ||
+        cudaMallocHost(&h->hctr, sizeof(Counters)) != cudaSuccess) {
+        paces_destroy(h);
+        return PACES_ERR_CAPACITY;
+    }
+    std::memset(h->hctr, 0, sizeof(Counters));
+    if (cudaMemcpyAsync((void*)b.model, M, sizeof(DevModel), cudaMemcpyHostToDevice, h->st) != cudaSuccess ||
+        set_counters(h) != PACES_OK) {
+        paces_destroy(h);
+        return PACES_ERR_CUDA;
+    }
+    uint64_t want = params->max_rows ? params->max_rows : (uint64_t)kDefaultRows;
+    if (grow(h, want, 0, 0) != PACES_OK) {
+        paces_destroy(h);
+        return PACES_ERR_CAPACITY;
+    }
+    *out = h;
+    return PACES_OK;
+}
+
+paces_status paces_destroy(paces_t h)
+{
+    if (!h) return PACES_ERR_INVALID;
+    cudaStreamSynchronize(h->st);
+    free_rows(h);
+    for (auto& a : h->fixed_allocs) dev_free(h, a);
+    h->fixed_allocs.clear();
+    cudaStreamSynchronize(h->st);
+    for (auto e : h->evpool) cudaEventDestroy(e);
+    if (h->hctr) cudaFreeHost(h->hctr);
+    delete h->hmodel;
+    delete h;
+    return PACES_OK;
+}
+
+const char* paces_last_error(paces_t h) { return h ? h->err.c_str() : "NULL handle"; }
+
+static paces_status encode_state(paces_t h, int64_t n, const int32_t* site, const int32_t* occ,
+                                 std::vector<uint64_t>& keys)
+{
+    if (n <= 0 || !site || !occ) return fail(h, PACES_ERR_INVALID, "empty state or NULL arrays");
+    if ((uint64_t)n > kMaxRowsHard) return fail(h, PACES_ERR_INVALID, "too many states");
+    keys.resize((size_t)n * h->W);
+    std::string why;
+    for (int64_t i = 0; i < n; ++i)
+        for (int j = 0; j < h->N; ++j)
+            if (occ[i * h->N + j] > h->cap[j]) return fail(h, PACES_ERR_INVALID, "occupation above the phonon cap");
+    paces_status s = encode(&h->lay, n, site, occ, keys.data(), why);
+    if (s) return fail(h, s, why);
+    std::vector<int64_t> idx((size_t)n);
+    for (int64_t i = 0; i < n; ++i) idx[i] = i;
+    int W = h->W;
+    auto less = [&](int64_t a, int64_t b) {
+        return std::lexicographical_compare(&keys[a * W], &keys[a * W] + W, &keys[b * W], &keys[b * W] + W);
+    };
+    std::sort(idx.begin(), idx.end(), less);
+    for (int64_t i = 1; i < n; ++i)
+        if (std::equal(&keys[idx[i] * W], &keys[idx[i] * W] + W, &keys[idx[i - 1] * W]))
+            return fail(h, PACES_ERR_INVALID, "duplicate basis states");
+    return PACES_OK;
+}
+
+static paces_status upload_rows(paces_t h, int64_t n, const std::vector<uint64_t>& keys, const double* amps, int vec)
+{
+    if ((uint64_t)n * 2 > h->cap_rows) {
+        paces_status s = grow(h, (uint64_t)n * 2, 0, 0);
+        if (s) return s;
+    }
+    h->gen = 0;
+    paces_status s = clear_table(h, 0);
+    if (s) return s;
+    CUDA_TRY(h, cudaMemcpyAsync(h->b.keys[0], keys.data(), keys.size() * 8, cudaMemcpyHostToDevice, h->st));
+    CUDA_TRY(h, cudaMemcpyAsync(h->b.V[vec], amps, (size_t)n * sizeof(double2), cudaMemcpyHostToDevice, h->st));
+    count(h, Stage::Other, launch_insert_rows(h->b, 0, (uint32_t)n, h->st));
+    std::memset(h->hctr, 0, sizeof(Counters));
+    h->hctr->q = (uint32_t)n;
+    h->hctr->q_in = (uint32_t)n;
+    h->hctr->kept = (uint32_t)n;
+    h->hctr->level_off[0] = 0;
+    h->hctr->level_off[1] = (uint32_t)n;
+    h->hctr->nlevels = 1;
+    return set_counters(h);
+}
+
+paces_status paces_set_state(paces_t h, int64_t n, const int32_t* site, const int32_t* occ, const double* amps)
+{
+    if (!h) return PACES_ERR_INVALID;
+    if (!amps) return fail(h, PACES_ERR_INVALID, "amps is NULL");
+    std::vector<uint64_t> keys;
+    paces_status s = encode_state(h, n, site, occ, keys);
+    if (s) return s;
+    // psi(0) copy for the autocorrelation
+    if (n > h->psi0_cap) {
+        for (auto it = h->fixed_allocs.begin(); it != h->fixed_allocs.end();) {
+            if (it->p == h->b.psi0_keys || it->p == h->b.psi0_amp) {
+                dev_free(h, *it);
+                it = h->fixed_allocs.erase(it);
+            } else {
+                ++it;
+            }
+        }
+        h->b.psi0_keys = alloc_track<uint64_t>(h, h->fixed_allocs, (size_t)n * h->W);
+        h->b.psi0_amp = alloc_track<double2>(h, h->fixed_allocs, (size_t)n);
+        if (!h->b.psi0_keys || !h->b.psi0_amp) return fail(h, PACES_ERR_CAPACITY, "psi0 buffers");
+        h->psi0_cap = n;
+    }
+    CUDA_TRY(h, cudaMemcpyAsync(h->b.psi0_keys, keys.data(), keys.size() * 8, cudaMemcpyHostToDevice, h->st));
+    CUDA_TRY(h, cudaMemcpyAsync(h->b.psi0_amp, amps, (size_t)n * sizeof(double2), cudaMemcpyHostToDevice, h->st));
+    h->b.n0 = n;
+    for (int attempt = 0;; ++attempt) {
+        s = upload_rows(h, n, keys, amps, 1);
+        if (s) return s;
+        int f = 0;
+        bool overflow = false;
+        for (; h->prm.m_init < 0 || f < h->prm.m_init; ++f) {
+            count(h, Stage::Other, launch_level(h->b, 0, f, -1, -1, h->st));
+            if (h->prm.m_init < 0 || f + 1 == h->prm.m_init) {
+                s = read_counters(h);
+                if (s) return s;
+                if (h->hctr->err) {
+                    overflow = h->hctr->err == kErrRows || h->hctr->err == kErrProbe || h->hctr->err == kErrCand;
+                    if (!overflow) return fail(h, PACES_ERR_CUDA, "device error " + std::to_string(h->hctr->err));
+                    break;
+                }
+                if (h->prm.m_init < 0 && h->hctr->level_off[f + 2] == h->hctr->level_off[f + 1]) break;
+                if (f + 2 > kMaxLevels) return fail(h, PACES_ERR_UNSUPPORTED, "more than 256 BFS levels");
+            }
+        }
+        CUDA_TRY(h, cudaGetLastError());
+        if (!overflow) break;
+        s = grow(h, (uint64_t)h->cap_rows + h->cap_rows / 8, 0, 0);
+        if (s) return s;
+    }
+    h->fresh = true;
+    h->has_state = true;
+    h->csr_valid = false;
+    h->last_truncated = false;
+    h->time = 0.0;
+    h->n_records = 0;
+    s = ensure_obs(h, 1);
+    if (s) return s;
+    CUDA_TRY(h, cudaMemsetAsync(h->b.obs, 0, sizeof(double) * h->b.rec_len, h->st));
+    count(h, Stage::Other, launch_observe(h->b, 0, h->b.V[1], 0.0, 0, 1, h->st));
+    s = read_counters(h);
+    if (s) return s;
+    if (h->hctr->err) return fail(h, PACES_ERR_CUDA, "device error " + std::to_string(h->hctr->err));
+    h->n_records = 1;
+    return PACES_OK;
+}
+
+paces_status paces_load_state(paces_t h, int64_t n, const int32_t* site, const int32_t* occ, const double* amps)
+{
+    if (!h) return PACES_ERR_INVALID;
+    if (!amps) return fail(h, PACES_ERR_INVALID, "amps is NULL");
+    std::vector<uint64_t> keys;
+    paces_status s = encode_state(h, n, site, occ, keys);
+    if (s) return s;
+    s = upload_rows(h, n, keys, amps, 0);
+    if (s) return s;
+    h->fresh = false;
+    h->has_state = true;
+    h->csr_valid = false;
+    h->last_truncated = false;
+    return PACES_OK;
+}
+
+paces_status paces_step(paces_t h, double dt, int64_t nsteps, double theta)
+{
+    if (!h) return PACES_ERR_INVALID;
+    if (!(dt > 0.0) || nsteps < 0 || !(theta >= 0.0)) return fail(h, PACES_ERR_INVALID, "dt, nsteps or theta");
+    if (!h->has_state) return fail(h, PACES_ERR_STATE, "no state: call paces_set_state first");
+    double th2 = theta * theta;
+    int64_t done = 0;
+    std::vector<double> hrec;
+    while (done < nsteps) {
+        int chunk = (int)std::min<int64_t>(kChunk, nsteps - done);
+        paces_status s = ensure_obs(h, h->n_records + chunk);
+        if (s) return s;
+        CUDA_TRY(h, cudaMemsetAsync(h->b.obs + h->n_records * h->b.rec_len, 0,
+                                    sizeof(double) * h->b.rec_len * chunk, h->st));
+        int g0 = h->gen;
+        bool fresh0 = h->fresh;
+        double t0 = h->time;
+        int64_t step0 = h->step_index;
+        for (int k = 0; k < chunk; ++k) enqueue_step(h, dt, th2, h->n_records + k, (size_t)k * 6);
+        CUDA_TRY(h, cudaGetLastError());
+        s = read_counters(h);
+        if (s) return s;
+        int err = h->hctr->err;
+        if (err == 0) {
+            if (h->profiling) {
+                hrec.resize((size_t)chunk * h->b.rec_len);
+                CUDA_TRY(h, cudaMemcpy(hrec.data(), h->b.obs + h->n_records * h->b.rec_len,
+                                       sizeof(double) * hrec.size(), cudaMemcpyDeviceToHost));
+                for (int k = 0; k < chunk; ++k) {
+                    float ms;
+                    for (int st = 0; st < 5; ++st) {
+                        if (cudaEventElapsedTime(&ms, ev(h, (size_t)k * 6 + st), ev(h, (size_t)k * 6 + st + 1)) ==
+                            cudaSuccess)
+                            h->stage_ms[st] += ms;
+                    }
+                    const double* r = hrec.data() + (size_t)k * h->b.rec_len;
+                    double q_in = k == 0 ? (double)0 : hrec[(size_t)(k - 1) * h->b.rec_len + PACES_OBS_ROWS];
+                    if (k == 0) {
+                        double prev[PACES_OBS_FIXED] = {0};
+                        if (h->n_records > 0)
+                            cudaMemcpy(prev, h->b.obs + (h->n_records - 1) * h->b.rec_len,
+                                       sizeof(double) * PACES_OBS_FIXED, cudaMemcpyDeviceToHost);
+                        q_in = prev[PACES_OBS_ROWS];
+                    }
+                    bool tr = !(k == 0 && fresh0);
+                    step_bytes(h, r, q_in, tr, h->stage_bytes);
+                }
+            }
+            h->n_records += chunk;
+            done += chunk;
+            continue;
+        }
+        // a step failed: find it and restore the host view at its start
+        int64_t fs = (int64_t)h->hctr->err_step - (step0 & 0x7fffffff);
+        if (fs < 0 || fs >= chunk) fs = 0;
+        int gen = g0;
+        bool fresh = fresh0;
+        double t = t0;
+        for (int64_t k = 0; k < fs; ++k) {
+            if (!fresh) gen = 1 - gen;
+            fresh = false;
+            t += dt;
+        }
+        h->n_records += fs;
+        done += fs;
+        h->time = t;
+        h->step_index = step0 + fs;
+        if (err == kErrRows || err == kErrProbe || err == kErrCand) {
+            // the failing step's input (generation gen, vector V0) is intact
+            uint32_t q = h->hctr->q_in;
+            h->gen = gen;
+            h->fresh = fresh;
+            std::memset(h->hctr, 0, sizeof(Counters));
+            h->hctr->q = q;
+            h->hctr->q_in = q;
+            h->hctr->kept = q;
+            h->hctr->level_off[1] = q;
+            h->hctr->nlevels = 1;
+            Counters keep = *h->hctr;
+            paces_status gs = read_counters(h);   // keep norm_last from the device
+            if (gs) return gs;
+            keep.norm_last = h->hctr->norm_last;
+            *h->hctr = keep;
+            s = set_counters(h);
+            if (s) return s;
+            s = grow(h, (uint64_t)h->cap_rows + h->cap_rows / 8, q, 0);
+            if (s) return s;
+            continue;
+        }
+        if (err == kErrNoConverge) {
+            // the failed step's truncated and regrown state stays, unpropagated
+            int nterm = h->hctr->err_info;
+            h->gen = fresh ? gen : 1 - gen;
+            h->fresh = true;
+            h->csr_valid = false;
+            h->hctr->err = 0;
+            h->hctr->err_step = 0;
+            s = set_counters(h);
+            if (s) return s;
+            return fail(h, PACES_ERR_NOCONVERGE,
+                        "Taylor series not converged after " + std::to_string(nterm) + " terms at step " +
+                            std::to_string(h->step_index));
+        }
+        h->has_state = false;
+        return fail(h, PACES_ERR_CUDA, "device error code " + std::to_string(err));
+    }
+    return PACES_OK;
+}
+
+paces_status paces_num_rows(paces_t h, int64_t* rows)
+{
+    if (!h || !rows) return PACES_ERR_INVALID;
+    paces_status s = read_counters(h);
+    if (s) return s;
+    *rows = h->has_state ? (int64_t)h->hctr->q : 0;
+    return PACES_OK;
+}
+
+paces_status paces_get_state(paces_t h, int64_t max, int32_t* site, int32_t* occ, double* amps)
+{
+    if (!h) return PACES_ERR_INVALID;
+    if (!h->has_state) return fail(h, PACES_ERR_STATE, "no state");
+    paces_status s = read_counters(h);
+    if (s) return s;
+    uint32_t q = h->hctr->q;
+    if (max < (int64_t)q) return fail(h, PACES_ERR_INVALID, "arrays smaller than the row count");
+    if (q == 0) return PACES_OK;
+    if (site || occ) {
+        int32_t* ds = (int32_t*)dev_alloc(h, (size_t)q * 4);
+        int32_t* dox = (int32_t*)dev_alloc(h, (size_t)q * h->N * 4);
+        if (!ds || !dox) return fail(h, PACES_ERR_CAPACITY, "export buffers");
+        count(h, Stage::Other, launch_decode(h->b, h->gen, q, ds, dox, h->st));
+        if (site) CUDA_TRY(h, cudaMemcpyAsync(site, ds, (size_t)q * 4, cudaMemcpyDeviceToHost, h->st));
+        if (occ) CUDA_TRY(h, cudaMemcpyAsync(occ, dox, (size_t)q * h->N * 4, cudaMemcpyDeviceToHost, h->st));
+        CUDA_TRY(h, cudaStreamSynchronize(h->st));
+        dev_free(h, {ds, (size_t)q * 4});
+        dev_free(h, {dox, (size_t)q * h->N * 4});
+    }
+    if (amps) {
+        const double2* v = h->fresh ? h->b.V[1] : h->b.V[0];
+        CUDA_TRY(h, cudaMemcpyAsync(amps, v, (size_t)q * sizeof(double2), cudaMemcpyDeviceToHost, h->st));
+    }
+    CUDA_TRY(h, cudaStreamSynchronize(h->st));
+    return PACES_OK;
+}
+
+paces_status paces_get_levels(paces_t h, int64_t* off, int32_t max, int32_t* count_out)
+{
+    if (!h || !count_out) return PACES_ERR_INVALID;
+    paces_status s = read_counters(h);
+    if (s) return s;
+    int32_t n = (int32_t)h->hctr->nlevels + 1;
+    *count_out = n;
+    for (int32_t i = 0; i < n && i < max && off; ++i) off[i] = h->hctr->level_off[i];
+    return PACES_OK;
+}
+
+paces_status paces_get_keep(paces_t h, uint8_t* keep, int64_t max, int64_t* n)
+{
+    if (!h || !n) return PACES_ERR_INVALID;
+    paces_status s = read_counters(h);
+    if (s) return s;
+    if (!h->last_truncated) {
+        *n = 0;
+        return PACES_OK;
+    }
+    uint32_t q = h->hctr->q_in;
+    *n = q;
+    if (!keep) return PACES_OK;
+    if (max < (int64_t)q) return fail(h, PACES_ERR_INVALID, "keep array too small");
+    std::vector<uint32_t> w(q / 32 + 1);
+    CUDA_TRY(h, cudaMemcpyAsync(w.data(), h->b.keepw, w.size() * 4, cudaMemcpyDeviceToHost, h->st));
+    CUDA_TRY(h, cudaStreamSynchronize(h->st));
+    for (uint32_t i = 0; i < q; ++i) keep[i] = (w[i >> 5] >> (i & 31)) & 1u;
+    return PACES_OK;
+}
+
+paces_status paces_get_hamiltonian(paces_t h, int32_t* cnt, int32_t* cols, double* vals, double* diag,
+                                   int64_t max_nnz, int64_t* nnz)
+{
+    if (!h || !nnz) return PACES_ERR_INVALID;
+    if (!h->has_state) return fail(h, PACES_ERR_STATE, "no state");
+    if (!h->csr_valid) {
+        CUDA_TRY(h, cudaMemsetAsync(&h->b.ctr->nnz, 0, 8, h->st));
+        count(h, Stage::Other, launch_csr(h->b, h->gen, h->st));
+        h->csr_valid = true;
+    }
+    paces_status s = read_counters(h);
+    if (s) return s;
+    uint32_t q = h->hctr->q;
+    std::vector<uint8_t> c8(q);
+    if (q) CUDA_TRY(h, cudaMemcpyAsync(c8.data(), h->b.cnt, q, cudaMemcpyDeviceToHost, h->st));
+    CUDA_TRY(h, cudaStreamSynchronize(h->st));
+    std::vector<uint64_t> off(q + 1, 0);
+    for (uint32_t i = 0; i < q; ++i) off[i + 1] = off[i] + c8[i];
+    *nnz = (int64_t)off[q];
+    if (cnt)
+        for (uint32_t i = 0; i < q; ++i) cnt[i] = c8[i];
+    if (diag && q) CUDA_TRY(h, cudaMemcpyAsync(diag, h->b.diag, (size_t)q * 8, cudaMemcpyDeviceToHost, h->st));
+    if ((cols || vals) && off[q] > 0) {
+        if ((int64_t)off[q] > max_nnz) return fail(h, PACES_ERR_INVALID, "max_nnz too small");
+        uint64_t* doff = (uint64_t*)dev_alloc(h, (size_t)q * 8);
+        int32_t* dc = (int32_t*)dev_alloc(h, off[q] * 4);
+        double* dv = (double*)dev_alloc(h, off[q] * 8);
+        if (!doff || !dc || !dv) return fail(h, PACES_ERR_CAPACITY, "export buffers");
+        CUDA_TRY(h, cudaMemcpyAsync(doff, off.data(), (size_t)q * 8, cudaMemcpyHostToDevice, h->st));
+        count(h, Stage::Other, launch_export_csr(h->b, q, doff, dc, dv, h->st));
+        if (cols) CUDA_TRY(h, cudaMemcpyAsync(cols, dc, off[q] * 4, cudaMemcpyDeviceToHost, h->st));
+        if (vals) CUDA_TRY(h, cudaMemcpyAsync(vals, dv, off[q] * 8, cudaMemcpyDeviceToHost, h->st));
+        CUDA_TRY(h, cudaStreamSynchronize(h->st));
+        dev_free(h, {doff, (size_t)q * 8});
+        dev_free(h, {dc, off[q] * 4});
+        dev_free(h, {dv, off[q] * 8});
+    }
+    CUDA_TRY(h, cudaStreamSynchronize(h->st));
+    return PACES_OK;
+}
+
+int32_t paces_record_len(paces_t h) { return h ? h->b.rec_len : 0; }
+
+paces_status paces_num_records(paces_t h, int64_t* n)
+{
+    if (!h || !n) return PACES_ERR_INVALID;
+    *n = h->n_records;
+    return PACES_OK;
+}
+
+paces_status paces_observables(paces_t h, int64_t first, int64_t count_, double* out)
+{
+    if (!h || first < 0 || count_ < 0 || first + count_ > h->n_records || (count_ > 0 && !out))
+        return fail(h, PACES_ERR_INVALID, "record range");
+    if (count_ == 0) return PACES_OK;
+    CUDA_TRY(h, cudaMemcpyAsync(out, h->b.obs + first * h->b.rec_len, sizeof(double) * h->b.rec_len * count_,
+                                cudaMemcpyDeviceToHost, h->st));
+    CUDA_TRY(h, cudaStreamSynchronize(h->st));
+    return PACES_OK;
+}
+
+paces_status paces_profile(paces_t h, int32_t enable)
+{
+    if (!h) return PACES_ERR_INVALID;
+    h->profiling = enable != 0;
+    return PACES_OK;
+}
+
+paces_status paces_stage_stats(paces_t h, double* ms, int64_t* launches, double* bytes, int32_t reset)
+{
+    if (!h) return PACES_ERR_INVALID;
+    for (int i = 0; i < PACES_NUM_STAGES; ++i) {
+        if (ms) ms[i] = h->stage_ms[i];
+        if (bytes) bytes[i] = h->stage_bytes[i];
+    }
+    for (int i = 0; i <= PACES_NUM_STAGES; ++i)
+        if (launches) launches[i] = h->stage_launch[i];
+    if (reset) {
+        std::memset(h->stage_ms, 0, sizeof(h->stage_ms));
+        std::memset(h->stage_bytes, 0, sizeof(h->stage_bytes));
+        std::memset(h->stage_launch, 0, sizeof(h->stage_launch));
+    }
+    return PACES_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,74 @@
+// runtime.h -- launch interface between the host runtime (paces_api.cu) and the
+// kernel translation units.  Host-side declarations only.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace paces {
+
+constexpr int kBlock = 256;        // threads of the chunked (scan-based) kernels
+constexpr int kMaxChunkBlocks = 1024;
+
+// Device buffers of one handle (all device pointers).
+struct Bufs {
+    const DevModel* model;
+    Counters* ctr;
+    uint64_t* keys[2];             // row -> key, two generations
+    uint64_t* table[2];            // hash tables, two generations
+    uint64_t table_slots;          // slots per table (below 2^32)
+    double2* V[4];                 // V0: state / accumulator r, V1: c' (phi_0), V2, V3: terms
+    float2* F[2];                  // complex64 term buffers (C64_SPMV)
+    uint32_t* col;                 // P H P columns, row pitch P
+    uint8_t* cid;                  // coefficient ids, row pitch P
+    uint8_t* cnt;                  // entries per row
+    double* diag;                  // diagonal per row
+    uint32_t* cand_slot;           // candidate -> table slot
+    uint64_t* masks;               // winner bits per frontier row
+    uint32_t* keepw;               // truncation bitmask
+    uint32_t* blk_cnt;             // chunk counts
+    uint32_t* blk_off;             // chunk offsets
+    double* partials;              // Taylor reduction partials [2][G][4]
+    double* obs;                   // observables records
+    unsigned long long* obs_part;  // observables partials [grid][2*kMaxSites+1][2]
+    uint64_t* psi0_keys;
+    double2* psi0_amp;
+    int64_t n0;
+    uint32_t cap_rows;
+    uint64_t cand_cap;
+    int W, D, P, N;
+    int G;                          // blocks of chunked kernels
+    int grid;                       // blocks of grid-stride kernels
+    int taylor_grid;                // blocks of the cooperative propagator
+    int rec_len;
+};
+
+struct TaylorParams {
+    double dt;
+    double tol2;
+    int nmax;
+    int fixed_terms;
+    int step;
+    int lpr;                        // lanes per row (1, 4 or 8)
+    int c64;                        // complex64 SpMV terms
+};
+
+// Stage launchers; each returns the number of kernels it launched (or -1 on a
+// launch error, which the caller reads with cudaGetLastError).
+int launch_insert_rows(const Bufs& b, int gen, uint32_t n, cudaStream_t st);
+int launch_truncate(const Bufs& b, int gin, int gout, double th2, int step, cudaStream_t st);
+int launch_level(const Bufs& b, int gen, int f, int rescue_gen, int step, cudaStream_t st);
+int launch_csr(const Bufs& b, int gen, cudaStream_t st);
+int launch_taylor(const Bufs& b, const TaylorParams& p, cudaStream_t st);
+int launch_observe(const Bufs& b, int gen, const double2* vec, double t, int64_t rec,
+                   int mode, cudaStream_t st);
+int launch_decode(const Bufs& b, int gen, uint32_t n, int32_t* site, int32_t* occ,
+                  cudaStream_t st);
+int launch_export_csr(const Bufs& b, uint32_t q, const uint64_t* off, int32_t* cols,
+                      double* vals, cudaStream_t st);
+
+int taylor_blocks_per_sm(int lpr, int c64);
+
+}  // namespace paces

@@ -25,3 +25,11 @@ def pytest_collection_modifyitems(config, items):
     for it in items:
         if "gpu" in it.keywords:
             it.add_marker(skip)
+
+
+@pytest.fixture(scope="session")
+def libpaces():
+    """Build (if stale) and load the CUDA library; fails loudly if it cannot."""
+    from paper_2603_07341_gb300 import binding, build
+    build.build()
+    return binding.load()
