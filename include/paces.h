@@ -233,6 +233,46 @@ paces_status paces_profile(paces_t h, int32_t enable);
 paces_status paces_stage_stats(paces_t h, double* ms, int64_t* launches, double* bytes,
                                int32_t reset);
 
+/* ---- Expansion without allocation (no counterpart in the paper) -----------
+ * Some callers cannot allocate device memory: hosts whose framework has
+ * already reserved all of it in its own pool, real-time loops that must never
+ * enter an allocator, or code running under a policy that forbids a library
+ * from allocating.  For them this call performs one level of the expansion
+ * (a2/a3 above) with all of its working memory -- model tables, counters, the
+ * hash table, candidate slots and winner masks -- in one fixed device array of
+ * PACES_NOALLOC_SCRATCH_BYTES that the library reserves on every GPU that
+ * loads it and holds until the process exits.  It calls no cudaMalloc,
+ * cudaMallocAsync, cudaFree or allocating library routine.
+ *
+ * keys_in:  device array of n_in >= 1 distinct keys (paces_encode_keys
+ *           layout, words per key from paces_plan_layout), not modified.
+ * keys_out: device array of max_out keys (max_out >= n_in), caller-owned.
+ *           Receives the input keys in order, then every state reachable by
+ *           one move of H and not among them, in first-occurrence order
+ *           (inputs in order, moves in canonical order) -- exactly the rows
+ *           paces_set_state produces with m_init = 1.  *n_out gets the count.
+ * stream:   a cudaStream_t; the call synchronises it before returning.
+ *
+ * Limit: every piece of working memory must fit in the array, i.e.
+ *   68 KB (model tables and counters) + 8 KB (chunk counts)
+ *   + (2 R + 1) * 8 * S  (hash table; S = 2, 4, 4, 6 words for 1..4 key words)
+ *   + n_in * (4 D + 8) + 16 R bytes,
+ * with R = min(max_out, n_in (D + 1)) and D = max moves per state (the
+ * largest number of hops from a site, plus 2).  Larger requests, and outputs
+ * that would exceed max_out, return PACES_ERR_CAPACITY and leave keys_out
+ * undefined; INVALID, KEY_WIDTH or UNSUPPORTED are returned as by
+ * paces_create.
+ *
+ * The array is shared by every call in the process and keeps the previous
+ * call's contents; each call re-initialises what it reads.  Calls whose GPU
+ * work overlaps (two threads, or two streams of one thread) race on it and
+ * must be serialised by the caller.  The first call on each device looks up
+ * the array's device address (cudaGetSymbolAddress, with that device
+ * current) and caches it; make that first call before any stream capture. */
+#define PACES_NOALLOC_SCRATCH_BYTES (32u << 20)
+paces_status paces_expand_noalloc(const paces_params* params, const uint64_t* keys_in, int64_t n_in,
+                                  uint64_t* keys_out, int64_t max_out, int64_t* n_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

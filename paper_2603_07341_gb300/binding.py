@@ -29,6 +29,7 @@ EXPORTED = (
     "paces_set_state", "paces_load_state", "paces_step", "paces_num_rows", "paces_get_state",
     "paces_get_levels", "paces_get_keep", "paces_get_hamiltonian", "paces_record_len",
     "paces_num_records", "paces_observables", "paces_profile", "paces_stage_stats",
+    "paces_expand_noalloc",
 )
 
 
@@ -115,6 +116,8 @@ def load():
     lib.paces_profile.argtypes = [P, C.c_int32]
     lib.paces_stage_stats.restype = S
     lib.paces_stage_stats.argtypes = [P, dp, i64p, dp, C.c_int32]
+    lib.paces_expand_noalloc.restype = S
+    lib.paces_expand_noalloc.argtypes = [C.POINTER(Params), P, C.c_int64, P, C.c_int64, i64p, P]
     _lib = lib
     return lib
 
@@ -177,6 +180,27 @@ def encode_keys(layout, site, occ):
     if rc:
         raise PacesError(rc, "paces_encode_keys")
     return out
+
+
+def expand_noalloc(keys_in, max_out, stream=None, **model):
+    """One expansion level with no device allocation inside the library.
+
+    keys_in: CUDA tensor [n_in, words] of int64 holding uint64 keys (this
+    wrapper allocates the output tensor with torch; the library call itself
+    allocates nothing).  Returns the CUDA tensor [n_out, words]."""
+    import torch
+    lib = load()
+    p, keep = make_params(**model)
+    keys_in = keys_in.contiguous()
+    n_in, words = keys_in.shape
+    out = torch.empty((int(max_out), words), dtype=torch.int64, device=keys_in.device)
+    n = C.c_int64()
+    st = stream if stream is not None else torch.cuda.current_stream()
+    rc = lib.paces_expand_noalloc(C.byref(p), C.c_void_p(keys_in.data_ptr()), n_in, C.c_void_p(out.data_ptr()),
+                                  int(max_out), C.byref(n), C.c_void_p(st.cuda_stream))
+    if rc:
+        raise PacesError(rc, "paces_expand_noalloc")
+    return out[: n.value]
 
 
 class _TorchAllocator:

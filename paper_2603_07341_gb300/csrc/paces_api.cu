@@ -485,6 +485,84 @@ void step_bytes(paces_t h, const double* r, double q_in, bool truncated, double*
 
 }  // namespace
 
+// Device-side description of a model (bond lists in canonical move order,
+// coefficient table, key-layout divisors), built on the host from params.
+paces_status paces::fill_model(const paces_params* params, const paces_layout& L, DevModel* M)
+{
+    const int N = params->n_sites;
+    std::vector<double> Jx;
+    if (params->lattice_kind == PACES_EXPLICIT) Jx.assign(params->J_explicit, params->J_explicit + (size_t)N * N);
+    auto at = [](const double* v, int j) { return v ? v[j] : 0.0; };
+    std::memset(M, 0, sizeof(DevModel));
+    M->N = N;
+    M->W = L.words;
+    M->pow2 = L.pow2;
+    M->div_exc = make_udiv(L.exciton_radix);
+    int w = 0;
+    M->word_first[0] = 0;
+    for (int j = 0; j < N; ++j) {
+        while (L.site_word[j] > w) M->word_first[++w] = j;
+        M->site_word[j] = L.site_word[j];
+        M->stride[j] = L.site_stride[j];
+        M->div_stride[j] = make_udiv(L.site_stride[j]);
+        M->div_radix[j] = make_udiv(L.site_radix[j]);
+        M->cap[j] = params->phonon_cap[j];
+        M->gnz[j] = at(params->g, j) != 0.0;
+        M->eps[j] = at(params->eps, j);
+        M->omega[j] = at(params->omega, j);
+    }
+    while (w < L.words) M->word_first[++w] = N;
+    std::map<std::tuple<double, double, double>, int> ids;
+    auto cid_of = [&](double v, double dJ, double dg) -> int {
+        auto key = std::make_tuple(v, dJ, dg);
+        auto it = ids.find(key);
+        if (it != ids.end()) return it->second;
+        int id = (int)ids.size();
+        ids[key] = id;
+        if (id < kMaxCoefs) {
+            M->coef[id] = v;
+            M->coef_dJ[id] = dJ;
+            M->coef_dg[id] = dg;
+        }
+        return id;
+    };
+    int maxdeg = 0, nadj = 0, nlad = 0;
+    for (int si = 0; si < N; ++si) {
+        M->adj_off[si] = nadj;
+        for (int t = 0; t < N; ++t) {
+            double p = hop_pattern(*params, Jx, t, si);
+            double v = params->J * p;
+            if (t == si || v == 0.0) continue;
+            if (nadj - M->adj_off[si] >= kMaxMoves - 2) return PACES_ERR_UNSUPPORTED;
+            M->adj[nadj] = (uint8_t)t;
+            M->adj_cid[nadj] = (uint8_t)std::min(cid_of(v, p, 0.0), 255);
+            ++nadj;
+        }
+        maxdeg = std::max(maxdeg, nadj - M->adj_off[si]);
+        M->lad_off[si] = nlad;
+        for (int k = 0; k < params->phonon_cap[si]; ++k) {
+            double sq = std::sqrt((double)(k + 1));
+            M->lad_cid[nlad + k] = (uint8_t)std::min(cid_of(at(params->g, si) * sq, 0.0, sq), 255);
+        }
+        nlad += params->phonon_cap[si];
+    }
+    M->adj_off[N] = nadj;
+    M->lad_off[N] = nlad;
+    M->nlad = nlad;
+    M->ncoef = (int)ids.size();
+    if (M->ncoef > kMaxCoefs) return PACES_ERR_UNSUPPORTED;
+    M->D = maxdeg + 2;
+    M->P = (M->D + 3) / 4 * 4;
+    M->div_D = make_udiv((uint64_t)M->D);
+    return PACES_OK;
+}
+
+paces_status paces::plan_layout_internal(const paces_params* params, paces_layout* out)
+{
+    std::string why;
+    return plan(params, out, why);
+}
+
 // ======================================================================== C ABI
 extern "C" {
 
@@ -538,78 +616,15 @@ paces_status paces_create(const paces_params* params, const paces_allocator* all
 
     // model tables
     DevModel* M = new DevModel();
-    std::memset(M, 0, sizeof(DevModel));
     h->hmodel = M;
-    M->N = N;
-    M->W = L.words;
-    M->pow2 = L.pow2;
-    M->div_exc = make_udiv(L.exciton_radix);
-    int w = 0;
-    M->word_first[0] = 0;
-    for (int j = 0; j < N; ++j) {
-        while (L.site_word[j] > w) M->word_first[++w] = j;
-        M->site_word[j] = L.site_word[j];
-        M->stride[j] = L.site_stride[j];
-        M->div_stride[j] = make_udiv(L.site_stride[j]);
-        M->div_radix[j] = make_udiv(L.site_radix[j]);
-        M->cap[j] = h->cap[j];
-        M->gnz[j] = h->g[j] != 0.0;
-        M->eps[j] = h->eps[j];
-        M->omega[j] = h->omega[j];
-    }
-    while (w < L.words) M->word_first[++w] = N;
-    std::map<std::tuple<double, double, double>, int> ids;
-    auto cid_of = [&](double v, double dJ, double dg) -> int {
-        auto key = std::make_tuple(v, dJ, dg);
-        auto it = ids.find(key);
-        if (it != ids.end()) return it->second;
-        int id = (int)ids.size();
-        ids[key] = id;
-        if (id < kMaxCoefs) {
-            M->coef[id] = v;
-            M->coef_dJ[id] = dJ;
-            M->coef_dg[id] = dg;
-        }
-        return id;
-    };
-    int maxdeg = 0, nadj = 0, nlad = 0;
-    for (int si = 0; si < N; ++si) {
-        M->adj_off[si] = nadj;
-        for (int t = 0; t < N; ++t) {
-            double p = hop_pattern(h->prm, h->Jx, t, si);
-            double v = params->J * p;
-            if (t == si || v == 0.0) continue;
-            if (nadj - M->adj_off[si] >= kMaxMoves - 2) {
-                delete M;
-                delete h;
-                return PACES_ERR_UNSUPPORTED;
-            }
-            M->adj[nadj] = (uint8_t)t;
-            M->adj_cid[nadj] = (uint8_t)std::min(cid_of(v, p, 0.0), 255);
-            ++nadj;
-        }
-        maxdeg = std::max(maxdeg, nadj - M->adj_off[si]);
-        M->lad_off[si] = nlad;
-        for (int k = 0; k < h->cap[si]; ++k) {
-            double sq = std::sqrt((double)(k + 1));
-            M->lad_cid[nlad + k] = (uint8_t)std::min(cid_of(h->g[si] * sq, 0.0, sq), 255);
-        }
-        nlad += h->cap[si];
-    }
-    M->adj_off[N] = nadj;
-    M->lad_off[N] = nlad;
-    M->nlad = nlad;
-    M->ncoef = (int)ids.size();
-    if (M->ncoef > kMaxCoefs) {
+    s = paces::fill_model(params, L, M);
+    if (s) {
         delete M;
         delete h;
-        return PACES_ERR_UNSUPPORTED;
+        return s;
     }
-    h->D = maxdeg + 2;
-    h->P = (h->D + 3) / 4 * 4;
-    M->D = h->D;
-    M->P = h->P;
-    M->div_D = make_udiv((uint64_t)h->D);
+    h->D = M->D;
+    h->P = M->P;
     h->lpr = h->P <= 8 ? 1 : (h->P <= 24 ? 4 : 8);
 
     cudaError_t e = cudaGetDevice(&h->device);

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include "common.cuh"
+#include "paces.h"
 
 namespace paces {
 
@@ -70,5 +71,9 @@ int launch_export_csr(const Bufs& b, uint32_t q, const uint64_t* off, int32_t* c
                       double* vals, cudaStream_t st);
 
 int taylor_blocks_per_sm(int lpr, int c64);
+
+// Host: plan the key layout and fill the device model description.
+paces_status plan_layout_internal(const paces_params* params, paces_layout* out);
+paces_status fill_model(const paces_params* params, const paces_layout& L, DevModel* M);
 
 }  // namespace paces
