@@ -116,6 +116,10 @@ def dist_setup():
     return ws, rank, local
 
 
+def sol_precision(model):
+    return {0: "dw", 1: "c128", 2: "c64"}[int(model.get("precision", 0))]
+
+
 def taylor_counts(rec, h_words):
     """Units, FP64 flops and algorithmic bytes of the propagator over records."""
     q = rec[:, 6]
@@ -269,7 +273,7 @@ def main():
     frac_fp64 = achieved_tf / FP64_PEAK_TFLOPS
     src = os.path.join(ROOT, "paper_2603_07341_gb300", "csrc", "kern_taylor.cu")
     traffic = traffic_from_profile(src)
-    if frac_fp64 > frac_hbm:
+    if sol_precision(model) == "c128" and frac_fp64 > frac_hbm:
         roof = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s (FP64)",
                 "frac": frac_fp64, "traffic": traffic, "peak_kind": "nominal FP64 (derived)",
                 "hbm_achieved_gbs": achieved_gbs, "hbm_frac": frac_hbm}
@@ -319,7 +323,9 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": Wm,
             "ms_per_step": t_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic",
+            "dtype": {"dw": "f32x2 (double-word FP32, 48-bit significand)", "c128": "f64",
+                      "c64": "f32 terms, f32x2 accumulator"}[sol_precision(model)],
+            "data": "synthetic",
             "config": {"workload": "%s: 1D Holstein ring N=16 K=8 J=1 omega=1 g=1.5 dt=0.02 theta=1e-7, "
                                    "timed steps %d..%d of %d" % (args.workload, start + Wm + 1, start + Wm + K,
                                                                   cfg["nsteps"])

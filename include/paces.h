@@ -73,9 +73,13 @@ typedef enum {
 /* coupling kinds (geometric lattices): */
 #define PACES_NEAREST 0   /* M_ab = 1 for Euclidean distance 1                         */
 #define PACES_DIPOLAR 1   /* M_ab = 1 / r_ab^3 for all pairs (computed as 1/(r2*sqrt(r2))) */
-/* arithmetic of the propagator */
-#define PACES_C128 0      /* complex128 everywhere                                      */
-#define PACES_C64_SPMV 1  /* complex64 SpMV terms; FP64 accumulator, norms, magnitudes  */
+/* arithmetic of the amplitudes and of the propagator */
+#define PACES_DW 0        /* double-word: every amplitude is a pair of FP32 (48-bit       */
+                          /* significand) and all arithmetic on them runs on the FP32     */
+                          /* pipe with error-free transformations (default)               */
+#define PACES_C128 1      /* complex128: FP64 amplitudes and FP64 arithmetic              */
+#define PACES_C64_SPMV 2  /* complex64 SpMV for terms n >= 2; term 1, the accumulator,    */
+                          /* norms and truncation magnitudes double-word                  */
 
 /* Device memory hook.  alloc returns device memory of `bytes` usable on
  * `stream` (a cudaStream_t) or NULL; free releases it.  Both may be called from
@@ -100,7 +104,7 @@ typedef struct {
     const int32_t* phonon_cap;  /* [N] K_j >= 0 (d_pho - 1), required                  */
     int32_t m;                  /* neighbour order of every step, >= 0 (paper: 2)       */
     int32_t m_init;             /* neighbour order of H_eff(0); < 0 = until closure     */
-    int32_t precision;          /* PACES_C128 or PACES_C64_SPMV                         */
+    int32_t precision;          /* PACES_DW, PACES_C128 or PACES_C64_SPMV               */
     int32_t fixed_terms;        /* > 0: exactly this many series terms, no test         */
     double taylor_tol;          /* stop at n >= 2 with ||phi_n|| <= tol ||r||; 0 = 1e-15 */
     int32_t taylor_nmax;        /* series terms allowed before NOCONVERGE; 0 = 200      */
@@ -167,11 +171,13 @@ paces_status paces_load_state(paces_t h, int64_t n, const int32_t* site, const i
                               const double* amps);
 
 /* Advance nsteps time steps of length dt (> 0) with amplitude threshold theta
- * (>= 0): keep a row iff re^2 + im^2 >= theta^2, evaluated in FP64 without
- * contraction.  Appends one observables record per step.  Capacity grows
+ * (>= 0): keep a row iff re^2 + im^2 >= theta^2 (PACES_C128: in FP64 without
+ * contraction; double-word storage: in double-word arithmetic, relative error
+ * below 2^-46).  Appends one observables record per step.  Capacity grows
  * automatically and the failing step is redone.  Returns INVALID, STATE (no
- * state set), NOCONVERGE (series did not reach taylor_tol: the state is left
- * at the end of the last converged step), CAPACITY or CUDA. */
+ * state set), NOCONVERGE (series did not reach taylor_tol: the state stays as
+ * the failed step truncated and regrew it, unpropagated, and the next call
+ * propagates it without truncating again), CAPACITY or CUDA. */
 paces_status paces_step(paces_t h, double dt, int64_t nsteps, double theta);
 
 /* Number of rows q = dim H_eff of the current state. */
@@ -256,7 +262,7 @@ paces_status paces_stage_stats(paces_t h, double* ms, int64_t* launches, double*
  * Limit: every piece of working memory must fit in the array, i.e.
  *   68 KB (model tables and counters) + 8 KB (chunk counts)
  *   + (2 R + 1) * 8 * S  (hash table; S = 2, 4, 4, 6 words for 1..4 key words)
- *   + n_in * (4 D + 8) + 16 R bytes,
+ *   + n_in * (4 D + 8) + 20 R bytes,
  * with R = min(max_out, n_in (D + 1)) and D = max moves per state (the
  * largest number of hops from a site, plus 2).  Larger requests, and outputs
  * that would exceed max_out, return PACES_ERR_CAPACITY and leave keys_out

@@ -17,7 +17,7 @@ from . import build as _build
 OK, ERR_INVALID, ERR_KEY_WIDTH, ERR_CAPACITY, ERR_NOCONVERGE, ERR_CUDA, ERR_STATE, ERR_UNSUPPORTED = range(8)
 RING, CHAIN, OPEN2D, OPEN3D, EXPLICIT = 0, 1, 2, 3, 4
 NEAREST, DIPOLAR = 0, 1
-C128, C64_SPMV = 0, 1
+DW, C128, C64_SPMV = 0, 1, 2
 MAX_SITES, MAX_WORDS = 128, 4
 OBS_FIELDS = ("time", "norm", "norm_phi0", "energy", "C_re", "C_im", "rows", "kept", "nnz", "terms",
               "norm_before")
@@ -131,7 +131,7 @@ def _ip(a):
 
 
 def make_params(n_sites, lattice_kind=RING, dims=(0, 0, 0), coupling_kind=NEAREST, J=1.0, eps=None,
-                omega=None, g=None, cap=None, m=2, m_init=10, precision=C128, fixed_terms=0, tol=0.0,
+                omega=None, g=None, cap=None, m=2, m_init=10, precision=DW, fixed_terms=0, tol=0.0,
                 nmax=0, max_rows=0, J_explicit=None):
     """Build a Params struct; returns (struct, keepalive arrays)."""
     N = int(n_sites)

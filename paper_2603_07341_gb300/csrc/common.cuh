@@ -51,6 +51,128 @@ __host__ __device__ inline uint64_t udiv(uint64_t n, const UDiv& v)
     return (t1 + ((n - t1) >> v.sh1)) >> v.sh2;
 }
 
+// ---------------------------------------------------------------- double-word arithmetic
+// A double-word number is an unevaluated sum hi + lo of two FP32 values with
+// |lo| <= ulp(hi) / 2: a 48-bit significand carried on the FP32 pipe.  The
+// building blocks are the classical error-free transformations (TwoSum of
+// Knuth, FastTwoSum of Dekker, TwoProd through an FMA) and the double-word
+// algorithms analysed by Joldes, Muller and Popescu, "Tight and rigorous error
+// bounds for basic building blocks of double-word arithmetic", ACM TOMS 44(2),
+// 2017: AccurateDWPlusDW (their Alg. 6, relative error <= 3u^2 + 13u^3),
+// DWTimesDW3 (Alg. 12, <= 4u^2) and DWTimesFP3 (Alg. 7, <= 2u^2), u = 2^-24.
+// Sums of products use the compensated dot product Dot2 of Ogita, Rump and
+// Oishi, "Accurate sum and dot product", SIAM J. Sci. Comput. 26(6), 2005.
+// Every operation is an explicitly rounded intrinsic so that the compiler can
+// neither contract nor reorder it.
+struct dwf {
+    float hi, lo;
+};
+
+__host__ __device__ inline dwf dw_from_double(double v)
+{
+    float h = (float)v;
+    return {h, (float)(v - (double)h)};
+}
+
+__device__ __forceinline__ dwf fast_two_sum(float a, float b)
+{
+    float s = __fadd_rn(a, b);
+    float z = __fsub_rn(s, a);
+    return {s, __fsub_rn(b, z)};
+}
+
+__device__ __forceinline__ dwf two_sum(float a, float b)
+{
+    float s = __fadd_rn(a, b);
+    float ap = __fsub_rn(s, b);
+    float bp = __fsub_rn(s, ap);
+    float da = __fsub_rn(a, ap);
+    float db = __fsub_rn(b, bp);
+    return {s, __fadd_rn(da, db)};
+}
+
+__device__ __forceinline__ dwf two_prod(float a, float b)
+{
+    float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+
+__device__ __forceinline__ dwf dw_add(dwf x, dwf y)
+{
+    dwf s = two_sum(x.hi, y.hi);
+    dwf t = two_sum(x.lo, y.lo);
+    float c = __fadd_rn(s.lo, t.hi);
+    dwf v = fast_two_sum(s.hi, c);
+    float w = __fadd_rn(t.lo, v.lo);
+    return fast_two_sum(v.hi, w);
+}
+
+__device__ __forceinline__ dwf dw_mul(dwf x, dwf y)
+{
+    float ch = __fmul_rn(x.hi, y.hi);
+    float cl1 = __fmaf_rn(x.hi, y.hi, -ch);
+    float tl0 = __fmul_rn(x.lo, y.lo);
+    float tl1 = __fmaf_rn(x.hi, y.lo, tl0);
+    float cl2 = __fmaf_rn(x.lo, y.hi, tl1);
+    float cl3 = __fadd_rn(cl1, cl2);
+    return fast_two_sum(ch, cl3);
+}
+
+__device__ __forceinline__ dwf dw_mul_f(dwf x, float y)
+{
+    float ch = __fmul_rn(x.hi, y);
+    float cl1 = __fmaf_rn(x.hi, y, -ch);
+    float cl3 = __fmaf_rn(x.lo, y, cl1);
+    return fast_two_sum(ch, cl3);
+}
+
+__device__ __forceinline__ dwf dw_neg(dwf x) { return {-x.hi, -x.lo}; }
+
+// Dot2 accumulator: s carries the rounded running sum, c the sum of the
+// rounding errors of every product and addition.
+struct Dot2 {
+    float s, c;
+};
+
+__device__ __forceinline__ void dot2_mac(Dot2& a, dwf coef, float xh, float xl)
+{
+    dwf p = two_prod(coef.hi, xh);
+    float e = __fmaf_rn(coef.hi, xl, p.lo);
+    e = __fmaf_rn(coef.lo, xh, e);
+    dwf t = two_sum(a.s, p.hi);
+    a.s = t.hi;
+    a.c = __fadd_rn(a.c, __fadd_rn(t.lo, e));
+}
+
+__device__ __forceinline__ dwf dot2_result(const Dot2& a) { return two_sum(a.s, a.c); }
+
+// |c|^2 of a double-word complex (re_hi, re_lo, im_hi, im_lo)
+__device__ __forceinline__ dwf dw_norm2(float4 v)
+{
+    dwf re{v.x, v.y}, im{v.z, v.w};
+    return dw_add(dw_mul(re, re), dw_mul(im, im));
+}
+
+// trunc(f * 2^84) as a signed 128-bit integer, exactly, from the bits of f
+// (finite f with |f| < 2^40).
+__device__ __forceinline__ __int128 fix84(float f)
+{
+    unsigned u = __float_as_uint(f);
+    int ex = (int)((u >> 23) & 0xFFu);
+    unsigned m = u & 0x7FFFFFu;
+    if (ex == 0) {
+        if (m == 0) return 0;
+        ex = 1;
+    } else {
+        m |= 0x800000u;
+    }
+    int sh = ex - 150 + 84;                      // f = m 2^(ex - 150)
+    __int128 v;
+    if (sh >= 0) v = ((__int128)m) << sh;
+    else v = (sh <= -24) ? (__int128)0 : (__int128)(m >> (-sh));
+    return (u >> 31) ? -v : v;
+}
+
 // ---------------------------------------------------------------- model
 // Everything the kernels need to know about one model, resident in device
 // memory (read through the read-only path).
@@ -69,6 +191,11 @@ struct DevModel {
     int gnz[kMaxSites];        // g_s != 0
     double eps[kMaxSites];
     double omega[kMaxSites];
+    dwf eps_dw[kMaxSites];
+    dwf omega_dw[kMaxSites];
+    int uniform_omega;         // all omega_j equal (diagonal = eps_s + omega sum_j n_j)
+    int fmt;                   // amplitude storage: 0 double-word, 1 FP64
+    int ncoef_pad;
     int adj_off[kMaxSites + 1];  // hops of site s: adj[adj_off[s] .. adj_off[s+1]) ascending t
     int lad_off[kMaxSites + 1];  // ladder cids of site s: lad_cid[lad_off[s] + k] = cid(g_s sqrt(k+1))
     uint8_t adj[kMaxSites * (kMaxMoves - 2)];
@@ -155,6 +282,17 @@ __device__ __forceinline__ int key_digit(const Key<W>& k, const DevModel* M, int
     return (int)(q - q2 * M->div_radix[j].d);
 }
 
+// Per-row descriptor kept beside the key so that moves need no digit
+// decoding: exciton site s (bits 0-7), phonons at s (8-15), total phonon
+// number (16-31).
+__host__ __device__ inline uint32_t meta_pack(int s, int ns, int nph)
+{
+    return (uint32_t)s | ((uint32_t)ns << 8) | ((uint32_t)nph << 16);
+}
+__device__ __forceinline__ int meta_s(uint32_t m) { return (int)(m & 0xFFu); }
+__device__ __forceinline__ int meta_ns(uint32_t m) { return (int)((m >> 8) & 0xFFu); }
+__device__ __forceinline__ int meta_nph(uint32_t m) { return (int)(m >> 16); }
+
 // MurmurHash3 64-bit finaliser (Appleby), applied word by word.
 __device__ __forceinline__ uint64_t fmix64(uint64_t h)
 {
@@ -208,6 +346,20 @@ __device__ __forceinline__ bool apply_move(const DevModel* M, const Key<W>& k,
         return true;
     }
     return false;
+}
+
+// Descriptor of the state reached from (key, m) by move mv (a valid move).
+template <int W>
+__device__ __forceinline__ uint32_t child_meta(const DevModel* M, const Key<W>& k, uint32_t m, int mv)
+{
+    int s = meta_s(m), ns = meta_ns(m), nph = meta_nph(m);
+    int a0 = M->adj_off[s], deg = M->adj_off[s + 1] - a0;
+    if (mv < deg) {
+        int t = M->adj[a0 + mv];
+        return meta_pack(t, key_digit<W>(k, M, t), nph);
+    }
+    if (mv == deg) return meta_pack(s, ns + 1, nph + 1);
+    return meta_pack(s, ns - 1, nph - 1);
 }
 
 // ---------------------------------------------------------------- hash table

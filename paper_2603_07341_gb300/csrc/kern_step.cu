@@ -45,10 +45,23 @@ __global__ void k_insert_rows(const uint64_t* __restrict__ keys, uint32_t n, uin
 }
 
 // ---------------------------------------------------------------- a1 truncation
-// keep_i = re^2 + im^2 >= theta^2 in FP64 with every product and sum rounded
-// separately (no FMA contraction), as the oracle evaluates it.
+// keep_i = re^2 + im^2 >= theta^2.  FP64 storage: evaluated in FP64 with every
+// product and sum rounded separately (no FMA contraction), as the oracle does.
+// Double-word storage: |c|^2 in double-word arithmetic (relative error below
+// 2^-46) compared with theta^2 rounded to a double-word.
+__device__ __forceinline__ bool keep_row(const double2* c, uint64_t i, int fmt, double th2, dwf th)
+{
+    if (fmt == 1) {
+        double2 v = c[i];
+        return __dadd_rn(__dmul_rn(v.x, v.x), __dmul_rn(v.y, v.y)) >= th2;
+    }
+    dwf w = dw_norm2(reinterpret_cast<const float4*>(c)[i]);
+    return w.hi > th.hi || (w.hi == th.hi && w.lo >= th.lo);
+}
+
 __global__ void __launch_bounds__(kBlock) k_trunc_count(const double2* __restrict__ c, Counters* ctr, double th2,
-                                                        uint32_t* __restrict__ keepw, uint32_t* __restrict__ blk_cnt)
+                                                        dwf th, int fmt, uint32_t* __restrict__ keepw,
+                                                        uint32_t* __restrict__ blk_cnt)
 {
     if (ctr->err) return;
     uint32_t q = ctr->q, lo, hi;
@@ -56,11 +69,7 @@ __global__ void __launch_bounds__(kBlock) k_trunc_count(const double2* __restric
     uint32_t cnt = 0;
     for (uint32_t base = lo; base < hi; base += kBlock) {
         uint32_t i = base + threadIdx.x;
-        bool keep = false;
-        if (i < hi) {
-            double2 v = c[i];
-            keep = __dadd_rn(__dmul_rn(v.x, v.x), __dmul_rn(v.y, v.y)) >= th2;
-        }
+        bool keep = (i < hi) && keep_row(c, i, fmt, th2, th);
         unsigned bal = __ballot_sync(0xffffffffu, keep);
         uint32_t w0 = base + (threadIdx.x & ~31u);
         if ((threadIdx.x & 31) == 0 && w0 < hi) keepw[w0 >> 5] = bal;
@@ -110,7 +119,9 @@ __global__ void __launch_bounds__(kBlock) k_trunc_scatter(const uint64_t* __rest
                                                           const uint32_t* __restrict__ keepw,
                                                           const uint32_t* __restrict__ blk_off,
                                                           uint64_t* __restrict__ keys_out, double2* __restrict__ c_out,
-                                                          uint64_t* table_out, uint64_t slots, int step)
+                                                          uint64_t* table_out, uint64_t slots,
+                                                          const uint32_t* __restrict__ meta_in,
+                                                          uint32_t* __restrict__ meta_out, int step)
 {
     if (ctr->err) return;
     uint32_t q = ctr->q_in, lo, hi;
@@ -128,6 +139,7 @@ __global__ void __launch_bounds__(kBlock) k_trunc_scatter(const uint64_t* __rest
             Key<W> k = load_key<W>(keys_in, i);
             store_key<W>(keys_out, dst, k);
             c_out[dst] = c_in[i];
+            meta_out[dst] = meta_in[i];
             if (!table_insert_unique<W>(table_out, slots, k, dst)) set_err(ctr, kErrProbe, step, 1);
         }
         run += tot;
@@ -135,12 +147,21 @@ __global__ void __launch_bounds__(kBlock) k_trunc_scatter(const uint64_t* __rest
 }
 
 // ---------------------------------------------------------------- a2/a3 one level
-// Insert a candidate; returns its slot if it claimed one or joined a candidate
-// entry with the same key, kNone if the key is already a row (or on failure).
+// One thread per candidate c = (parent p - lo) * D + move: the parents of a
+// level are the frontier rows [lo, hi); every candidate is inserted
+// independently, so a warp keeps 32 probe sequences in flight.
+//
+// Insert a candidate.  Returns the slot that holds its key afterwards: a slot
+// it claimed, a candidate entry with the same key it joined (the lowest
+// candidate index wins, through atomicMin on the tag), or the slot of an
+// existing row.  kNone only on failure.  The slot is recorded per (parent row,
+// move), so the P H P build later reads the column of every move of a
+// non-final level from it without probing.
 template <int W>
 __device__ __forceinline__ uint32_t insert_candidate(const DevModel* __restrict__ M, uint64_t* table, uint64_t slots,
                                                      const Key<W>& key, uint32_t c, const uint64_t* __restrict__ keys,
-                                                     uint32_t lo, Counters* ctr, int step)
+                                                     const uint32_t* __restrict__ meta, uint32_t lo, Counters* ctr,
+                                                     int step)
 {
     uint64_t h = key_hash<W>(key);
     uint64_t fp = fingerprint<W>(h);
@@ -162,8 +183,8 @@ __device__ __forceinline__ uint32_t insert_candidate(const DevModel* __restrict_
                 uint32_t p2 = (uint32_t)udiv(c2, M->div_D);
                 int mv2 = (int)(c2 - p2 * (uint32_t)M->D);
                 Key<W> pk = load_key<W>(keys, lo + p2);
-                int s2 = key_site<W>(pk, M);
-                int ns2 = key_digit<W>(pk, M, s2);
+                uint32_t pm = meta[lo + p2];
+                int s2 = meta_s(pm), ns2 = meta_ns(pm);
                 Key<W> k2;
                 int cid2;
                 if (apply_move<W>(M, pk, s2, ns2, mv2, k2, cid2) && key_eq<W>(k2, key)) {
@@ -174,7 +195,7 @@ __device__ __forceinline__ uint32_t insert_candidate(const DevModel* __restrict_
                 bool eq = true;
 #pragma unroll
                 for (int i = 0; i < W; ++i) eq &= (__ldcg(sl + 1 + i) == key.w[i]);
-                if (eq) return kNone;
+                if (eq) return (uint32_t)pos;
             }
         }
         pos = slot_next(pos, slots);
@@ -183,109 +204,122 @@ __device__ __forceinline__ uint32_t insert_candidate(const DevModel* __restrict_
     return kNone;
 }
 
+// Candidate c of the level whose frontier starts at row lo: parent row and move.
+__device__ __forceinline__ void cand_parent(const DevModel* __restrict__ M, uint32_t c, uint32_t lo, uint32_t& p,
+                                            int& mv)
+{
+    uint32_t pl = (uint32_t)udiv(c, M->div_D);
+    mv = (int)(c - pl * (uint32_t)M->D);
+    p = lo + pl;
+}
+
 template <int W>
 __global__ void __launch_bounds__(kBlock) k_level_insert(const DevModel* __restrict__ M, Counters* ctr, int f,
-                                                         const uint64_t* __restrict__ keys, uint64_t* table,
+                                                         const uint64_t* __restrict__ keys,
+                                                         const uint32_t* __restrict__ meta, uint64_t* table,
                                                          uint64_t slots, uint32_t* __restrict__ cand_slot,
                                                          uint64_t cand_cap, int step)
 {
     if (ctr->err) return;
     uint32_t lo = ctr->level_off[f], hi = ctr->level_off[f + 1];
-    int D = M->D;
+    const int D = M->D;
     uint64_t ncand = (uint64_t)(hi - lo) * (uint64_t)D;
-    if (ncand >= (uint64_t)kCand || ncand > cand_cap) {
+    if (ncand >= (uint64_t)kCand || (uint64_t)hi * D > cand_cap) {
         if (blockIdx.x == 0 && threadIdx.x == 0) set_err(ctr, kErrCand, step, f);
         return;
     }
-    for (uint32_t p = lo + blockIdx.x * blockDim.x + threadIdx.x; p < hi; p += gridDim.x * blockDim.x) {
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < (uint32_t)ncand; c += gridDim.x * blockDim.x) {
+        uint32_t p;
+        int mv;
+        cand_parent(M, c, lo, p, mv);
         Key<W> k = load_key<W>(keys, p);
-        int s = key_site<W>(k, M);
-        int ns = key_digit<W>(k, M, s);
-        uint32_t cbase = (p - lo) * (uint32_t)D;
-        for (int mv = 0; mv < D; ++mv) {
-            Key<W> child;
-            int cid;
-            uint32_t r = kNone;
-            if (apply_move<W>(M, k, s, ns, mv, child, cid))
-                r = insert_candidate<W>(M, table, slots, child, cbase + mv, keys, lo, ctr, step);
-            cand_slot[cbase + mv] = r;
-        }
+        uint32_t pm = meta[p];
+        Key<W> child;
+        int cid;
+        uint32_t r = kNone;
+        if (apply_move<W>(M, k, meta_s(pm), meta_ns(pm), mv, child, cid))
+            r = insert_candidate<W>(M, table, slots, child, c, keys, meta, lo, ctr, step);
+        cand_slot[(uint64_t)p * D + mv] = r;
     }
 }
 
+// Winner bits, one per candidate (32 per word, chunks aligned to 256).
 template <int W>
 __global__ void __launch_bounds__(kBlock) k_level_flags(const DevModel* __restrict__ M, Counters* ctr, int f,
                                                         const uint64_t* __restrict__ table,
                                                         const uint32_t* __restrict__ cand_slot,
-                                                        uint64_t* __restrict__ masks, uint32_t* __restrict__ blk_cnt)
+                                                        uint32_t* __restrict__ wmask, uint32_t* __restrict__ blk_cnt)
 {
     if (ctr->err) return;
-    uint32_t lo0 = ctr->level_off[f], F = ctr->level_off[f + 1] - lo0, lo, hi;
-    chunk_of(F, gridDim.x, blockIdx.x, lo, hi);
-    int D = M->D;
+    uint32_t lo0 = ctr->level_off[f], NC = (ctr->level_off[f + 1] - lo0) * (uint32_t)M->D, lo, hi;
+    chunk_of(NC, gridDim.x, blockIdx.x, lo, hi);
+    const int D = M->D;
     uint32_t cnt = 0;
-    for (uint32_t i = lo + threadIdx.x; i < hi; i += kBlock) {
-        uint64_t m = 0;
-        uint32_t cbase = i * (uint32_t)D;
-        for (int mv = 0; mv < D; ++mv) {
-            uint32_t sl = cand_slot[cbase + mv];
-            if (sl == kNone) continue;
-            uint64_t tag = table[(uint64_t)sl * Slot<W>::kWords];
-            if ((uint32_t)tag == (kCand | (cbase + mv))) m |= 1ull << mv;
+    for (uint32_t base = lo; base < hi; base += kBlock) {
+        uint32_t c = base + threadIdx.x;
+        bool win = false;
+        if (c < hi) {
+            uint32_t p;
+            int mv;
+            cand_parent(M, c, lo0, p, mv);
+            uint32_t sl = cand_slot[(uint64_t)p * D + mv];
+            if (sl != kNone) win = (uint32_t)table[(uint64_t)sl * Slot<W>::kWords] == (kCand | c);
         }
-        masks[i] = m;
-        cnt += __popcll(m);
+        unsigned bal = __ballot_sync(0xffffffffu, win);
+        uint32_t w0 = base + (threadIdx.x & ~31u);
+        if ((threadIdx.x & 31) == 0 && w0 < hi) wmask[w0 >> 5] = bal;
+        cnt += win ? 1u : 0u;
     }
     uint32_t tot;
     block_excl_scan<kBlock>(cnt, &tot);
     if (threadIdx.x == 0) blk_cnt[blockIdx.x] = tot;
 }
 
+// New rows in candidate order: key, table slot (key words + row), rescued amplitude.
 template <int W>
 __global__ void __launch_bounds__(kBlock) k_level_scatter(const DevModel* __restrict__ M, Counters* ctr, int f,
-                                                          uint64_t* keys, uint64_t* table,
+                                                          uint64_t* keys, uint32_t* meta, uint64_t* table,
                                                           const uint32_t* __restrict__ cand_slot,
-                                                          const uint64_t* __restrict__ masks,
+                                                          const uint32_t* __restrict__ wmask,
                                                           const uint32_t* __restrict__ blk_off,
                                                           const uint64_t* __restrict__ old_table, uint64_t old_slots,
                                                           const double2* __restrict__ c_old, double2* __restrict__ c_new)
 {
     if (ctr->err) return;
     uint32_t lo0 = ctr->level_off[f], base_row = ctr->level_off[f + 1];
-    uint32_t F = base_row - lo0, lo, hi;
-    chunk_of(F, gridDim.x, blockIdx.x, lo, hi);
-    int D = M->D;
+    const int D = M->D;
+    uint32_t NC = (base_row - lo0) * (uint32_t)D, lo, hi;
+    chunk_of(NC, gridDim.x, blockIdx.x, lo, hi);
     uint32_t run = blk_off[blockIdx.x];
-    for (uint32_t tile = lo; tile < hi; tile += kBlock) {
-        uint32_t i = tile + threadIdx.x;
-        uint64_t m = (i < hi) ? masks[i] : 0ull;
+    for (uint32_t base = lo; base < hi; base += kBlock) {
+        uint32_t c = base + threadIdx.x;
+        uint32_t w0 = base + (threadIdx.x & ~31u);
+        uint32_t bal = (w0 < hi) ? wmask[w0 >> 5] : 0u;
+        bool win = (c < hi) && ((bal >> (threadIdx.x & 31)) & 1u);
         uint32_t tot;
-        uint32_t r = block_excl_scan<kBlock>((uint32_t)__popcll(m), &tot);
-        if (m) {
-            Key<W> k = load_key<W>(keys, lo0 + i);
-            int s = key_site<W>(k, M);
-            int ns = key_digit<W>(k, M, s);
+        uint32_t r = block_excl_scan<kBlock>(win ? 1u : 0u, &tot);
+        if (win) {
+            uint32_t p;
+            int mv;
+            cand_parent(M, c, lo0, p, mv);
+            Key<W> k = load_key<W>(keys, p);
+            uint32_t pm = meta[p];
+            Key<W> child;
+            int cid;
+            apply_move<W>(M, k, meta_s(pm), meta_ns(pm), mv, child, cid);
             uint32_t row = base_row + run + r;
-            uint32_t cbase = i * (uint32_t)D;
-            while (m) {
-                int mv = __ffsll((long long)m) - 1;
-                m &= m - 1;
-                Key<W> child;
-                int cid;
-                apply_move<W>(M, k, s, ns, mv, child, cid);
-                store_key<W>(keys, row, child);
-                uint64_t* sl = table + (uint64_t)cand_slot[cbase + mv] * Slot<W>::kWords;
+            store_key<W>(keys, row, child);
+            meta[row] = child_meta<W>(M, k, pm, mv);
+            uint64_t* sl = table + (uint64_t)cand_slot[(uint64_t)p * D + mv] * Slot<W>::kWords;
 #pragma unroll
-                for (int w = 0; w < W; ++w) sl[1 + w] = child.w[w];
-                sl[0] = (sl[0] & 0xFFFFFFFF00000000ull) | (uint64_t)row;
-                double2 a = make_double2(0.0, 0.0);
-                if (old_table) {
-                    int64_t orow = table_lookup<W>(old_table, old_slots, child);
-                    if (orow >= 0) a = c_old[orow];
-                }
-                c_new[row] = a;
-                ++row;
+            for (int w = 0; w < W; ++w) sl[1 + w] = child.w[w];
+            sl[0] = (sl[0] & 0xFFFFFFFF00000000ull) | (uint64_t)row;
+            double2 a = make_double2(0.0, 0.0);
+            if (old_table) {
+                int64_t orow = table_lookup<W>(old_table, old_slots, child);
+                if (orow >= 0) a = c_old[orow];
             }
+            c_new[row] = a;
         }
         run += tot;
     }
@@ -294,48 +328,157 @@ __global__ void __launch_bounds__(kBlock) k_level_scatter(const DevModel* __rest
 // ---------------------------------------------------------------- a5 P H P
 // Row i holds the off-diagonal entries of P_m H P_m in move order (hops to
 // t ascending, a_s^dag, a_s), columns = rows of the images that lie in H_eff,
-// and the diagonal eps_s + sum_j omega_j n_j summed in site order.
+// and the diagonal eps_s + sum_j omega_j n_j.  Rows of every level except the
+// last were expanded: each of their valid moves is in H_eff and its slot was
+// recorded, so the column is one read of that slot's tag; rows of the last
+// level probe the table.
+struct DiagAcc {
+    double d;      // FP64 diagonal, summed in site order as the oracle does
+    dwf dd;        // double-word diagonal
+};
+
+template <int W>
+__device__ __forceinline__ DiagAcc row_diag(const DevModel* __restrict__ M, const Key<W>& k, int s, int nph)
+{
+    if (M->fmt == 0 && M->uniform_omega) {    // eps_s + omega N_ph, no digits needed
+        DiagAcc r{0.0, dw_add(M->eps_dw[s], dw_mul_f(M->omega_dw[0], (float)nph))};
+        return r;
+    }
+    uint64_t q0 = udiv(k.w[0], M->div_exc);
+    DiagAcc r{M->eps[s], M->eps_dw[s]};
+    const bool f64 = M->fmt == 1;
+    nph = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        uint64_t x = (w == 0) ? q0 : k.w[w];
+        for (int j = M->word_first[w]; j < M->word_first[w + 1]; ++j) {
+            uint64_t xq = udiv(x, M->div_radix[j]);
+            int nj = (int)(x - xq * M->div_radix[j].d);
+            x = xq;
+            if (f64) r.d = __dadd_rn(r.d, __dmul_rn(M->omega[j], (double)nj));
+            else if (!M->uniform_omega && nj) r.dd = dw_add(r.dd, dw_mul_f(M->omega_dw[j], (float)nj));
+            nph += nj;
+        }
+    }
+    if (!f64 && M->uniform_omega) r.dd = dw_add(r.dd, dw_mul_f(M->omega_dw[0], (float)nph));
+    return r;
+}
+
+__device__ __forceinline__ void store_diag(const DevModel* __restrict__ M, double* diag, uint64_t i, const DiagAcc& a)
+{
+    if (M->fmt == 1) diag[i] = a.d;
+    else reinterpret_cast<float2*>(diag)[i] = make_float2(a.dd.hi, a.dd.lo);
+}
+
+// GS lanes per row (GS = D rounded up to a power of two, at most 32): lane mv
+// resolves move mv; a ballot over the group gives each found entry its place.
+template <int W, int GS>
+__global__ void __launch_bounds__(kBlock) k_csr_grp(const DevModel* __restrict__ M, Counters* ctr,
+                                                    const uint64_t* __restrict__ keys,
+                                                    const uint32_t* __restrict__ meta,
+                                                    const uint64_t* __restrict__ table, uint64_t slots,
+                                                    const uint32_t* __restrict__ cand_slot,
+                                                    uint32_t* __restrict__ col, uint8_t* __restrict__ cidv,
+                                                    uint8_t* __restrict__ cnt, double* __restrict__ diag)
+{
+    if (ctr->err) return;
+    const uint32_t q = ctr->q, lim = ctr->level_off[ctr->nlevels - 1];
+    const int D = M->D, P = M->P;
+    constexpr uint32_t RPW = 32 / GS;
+    const int lane = threadIdx.x & 31, mv = lane % GS, gbase = lane - mv;
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    unsigned long long nnz = 0;
+    for (uint32_t rb = warp * RPW; rb < q; rb += nwarps * RPW) {
+        uint32_t row = rb + lane / GS;
+        bool valid = row < q;
+        Key<W> k;
+#pragma unroll
+        for (int i = 0; i < W; ++i) k.w[i] = 0;
+        uint32_t m = 0;
+        if (valid) {
+            k = load_key<W>(keys, row);
+            m = meta[row];
+        }
+        int s = meta_s(m), ns = meta_ns(m);
+        bool found = false;
+        uint32_t colv = 0;
+        int cid = 0;
+        if (valid && mv < D) {
+            Key<W> child;
+            if (apply_move<W>(M, k, s, ns, mv, child, cid)) {
+                if (row < lim) {
+                    uint32_t sl = cand_slot[(uint64_t)row * D + mv];
+                    if (sl != kNone) {
+                        colv = (uint32_t)table[(uint64_t)sl * Slot<W>::kWords];
+                        found = true;
+                    }
+                } else {
+                    int64_t r = table_lookup<W>(table, slots, child);
+                    if (r >= 0) {
+                        colv = (uint32_t)r;
+                        found = true;
+                    }
+                }
+            }
+        }
+        unsigned bal = __ballot_sync(0xffffffffu, found);
+        unsigned gm = (GS == 32) ? bal : ((bal >> gbase) & ((1u << GS) - 1u));
+        uint64_t rbase = (uint64_t)row * P;
+        if (found) {
+            int pos = __popc(gm & ((1u << mv) - 1u));
+            col[rbase + pos] = colv;
+            cidv[rbase + pos] = (uint8_t)cid;
+        }
+        if (valid && mv == 0) {
+            int e = __popc(gm);
+            cnt[row] = (uint8_t)e;
+            store_diag(M, diag, row, row_diag<W>(M, k, s, meta_nph(m)));
+            nnz += e;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nnz += __shfl_xor_sync(0xffffffffu, nnz, o);
+    if ((threadIdx.x & 31) == 0 && nnz) atomicAdd(&ctr->nnz, nnz);
+}
+
+// One thread per row, for models with more than 32 moves per state.
 template <int W>
 __global__ void __launch_bounds__(kBlock) k_csr(const DevModel* __restrict__ M, Counters* ctr,
-                                                const uint64_t* __restrict__ keys, const uint64_t* __restrict__ table,
-                                                uint64_t slots, uint32_t* __restrict__ col, uint8_t* __restrict__ cidv,
+                                                const uint64_t* __restrict__ keys, const uint32_t* __restrict__ meta,
+                                                const uint64_t* __restrict__ table,
+                                                uint64_t slots, const uint32_t* __restrict__ cand_slot,
+                                                uint32_t* __restrict__ col, uint8_t* __restrict__ cidv,
                                                 uint8_t* __restrict__ cnt, double* __restrict__ diag)
 {
     if (ctr->err) return;
-    uint32_t q = ctr->q;
-    int D = M->D, P = M->P;
+    const uint32_t q = ctr->q, lim = ctr->level_off[ctr->nlevels - 1];
+    const int D = M->D, P = M->P;
     unsigned long long nnz = 0;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < q; i += gridDim.x * blockDim.x) {
         Key<W> k = load_key<W>(keys, i);
-        uint64_t q0 = udiv(k.w[0], M->div_exc);
-        int s = (int)(k.w[0] - q0 * M->div_exc.d);
-        double d = M->eps[s];
-        int ns = 0;
-#pragma unroll
-        for (int w = 0; w < W; ++w) {
-            uint64_t x = (w == 0) ? q0 : k.w[w];
-            for (int j = M->word_first[w]; j < M->word_first[w + 1]; ++j) {
-                uint64_t xq = udiv(x, M->div_radix[j]);
-                int nj = (int)(x - xq * M->div_radix[j].d);
-                x = xq;
-                d = __dadd_rn(d, __dmul_rn(M->omega[j], (double)nj));
-                if (j == s) ns = nj;
-            }
-        }
+        uint32_t m = meta[i];
+        int s = meta_s(m), ns = meta_ns(m);
         uint32_t e = 0;
         uint64_t rbase = (uint64_t)i * (uint64_t)P;
         for (int mv = 0; mv < D; ++mv) {
             Key<W> child;
             int cid;
             if (!apply_move<W>(M, k, s, ns, mv, child, cid)) continue;
-            int64_t r = table_lookup<W>(table, slots, child);
+            int64_t r = -1;
+            if (i < lim) {
+                uint32_t sl = cand_slot[(uint64_t)i * D + mv];
+                if (sl != kNone) r = (uint32_t)table[(uint64_t)sl * Slot<W>::kWords];
+            } else {
+                r = table_lookup<W>(table, slots, child);
+            }
             if (r < 0) continue;
             col[rbase + e] = (uint32_t)r;
             cidv[rbase + e] = (uint8_t)cid;
             ++e;
         }
         cnt[i] = (uint8_t)e;
-        diag[i] = d;
+        store_diag(M, diag, i, row_diag<W>(M, k, s, meta_nph(m)));
         nnz += e;
     }
 #pragma unroll
@@ -360,52 +503,96 @@ __device__ __forceinline__ void split_weight(double w, unsigned long long& hi, u
     lo = (unsigned long long)((x - f) * 4294967296.0);   // next 32 bits, truncated
 }
 
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Rows are taken 32 at a time per warp.  P_s goes through atomics on the
+// warp's own shared row (contention only between lanes of one warp with the
+// same site); each <n_j> is a warp-wide integer shuffle sum, skipped when no
+// lane has phonons at site j.
 template <int W>
 __global__ void __launch_bounds__(kBlock) k_obs_accum(const DevModel* __restrict__ M, Counters* ctr,
                                                       const uint64_t* __restrict__ keys,
                                                       const double2* __restrict__ vec,
                                                       unsigned long long* __restrict__ part)
 {
-    __shared__ unsigned long long sh_hi[kObsStride], sh_lo[kObsStride];
+    __shared__ unsigned long long sh[kBlock / 32][kObsStride][2];
     if (ctr->err) return;
-    const int N = M->N;
-    for (int t = threadIdx.x; t < 2 * N + 1; t += blockDim.x) sh_hi[t] = sh_lo[t] = 0ull;
-    __syncthreads();
+    const int N = M->N, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int t = lane; t < 2 * N + 1; t += 32) sh[warp][t][0] = sh[warp][t][1] = 0ull;
+    __syncwarp();
+    const int fmt = M->fmt;
     const uint32_t q = ctr->q;
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
     unsigned long long nh = 0, nl = 0;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < q; i += gridDim.x * blockDim.x) {
-        double2 v = vec[i];
-        double w = v.x * v.x + v.y * v.y;
-        if (w == 0.0) continue;
-        unsigned long long hi, lo;
-        split_weight(w, hi, lo);
-        nh += hi;
-        nl += lo;
-        Key<W> k = load_key<W>(keys, i);
+    for (uint64_t rb = (uint64_t)gw * 32; rb < q; rb += (uint64_t)nw * 32) {
+        uint64_t row = rb + lane;
+        unsigned long long hi = 0, lo = 0;
+        Key<W> k;
+#pragma unroll
+        for (int i = 0; i < W; ++i) k.w[i] = 0;
+        if (row < q) {
+            if (fmt == 1) {
+                double2 v = vec[row];
+                double w = v.x * v.x + v.y * v.y;
+                if (w != 0.0) split_weight(w, hi, lo);
+            } else {
+                dwf w = dw_norm2(reinterpret_cast<const float4*>(vec)[row]);
+                if (w.hi != 0.0f) {
+                    __int128 F = fix84(w.hi) + fix84(w.lo);
+                    if (F < 0) F = 0;
+                    hi = (unsigned long long)(F >> 32);
+                    lo = (unsigned long long)(F & 0xFFFFFFFF);
+                }
+            }
+            if (hi | lo) k = load_key<W>(keys, row);
+        }
+        bool live = (hi | lo) != 0ull;
         uint64_t q0 = udiv(k.w[0], M->div_exc);
         int s = (int)(k.w[0] - q0 * M->div_exc.d);
-        atomicAdd(&sh_hi[s], hi);
-        atomicAdd(&sh_lo[s], lo);
+        if (live) {
+            atomicAdd(&sh[warp][s][0], hi);
+            atomicAdd(&sh[warp][s][1], lo);
+        }
+        nh += hi;
+        nl += lo;
 #pragma unroll
         for (int wd = 0; wd < W; ++wd) {
             uint64_t x = (wd == 0) ? q0 : k.w[wd];
-            for (int j = M->word_first[wd]; j < M->word_first[wd + 1] && x; ++j) {
+            for (int j = M->word_first[wd]; j < M->word_first[wd + 1]; ++j) {
                 uint64_t xq = udiv(x, M->div_radix[j]);
                 unsigned long long nj = x - xq * M->div_radix[j].d;
                 x = xq;
-                if (nj) {
-                    atomicAdd(&sh_hi[N + j], hi * nj);
-                    atomicAdd(&sh_lo[N + j], lo * nj);
+                if (__any_sync(0xffffffffu, nj != 0ull)) {
+                    unsigned long long a = warp_sum_u64(hi * nj), c = warp_sum_u64(lo * nj);
+                    if (lane == 0) {
+                        sh[warp][N + j][0] += a;
+                        sh[warp][N + j][1] += c;
+                    }
                 }
             }
         }
     }
-    atomicAdd(&sh_hi[2 * N], nh);
-    atomicAdd(&sh_lo[2 * N], nl);
+    nh = warp_sum_u64(nh);
+    nl = warp_sum_u64(nl);
+    if (lane == 0) {
+        sh[warp][2 * N][0] += nh;
+        sh[warp][2 * N][1] += nl;
+    }
     __syncthreads();
+    // integer sums do not depend on the order: blocks add into the totals
     for (int t = threadIdx.x; t < 2 * N + 1; t += blockDim.x) {
-        part[((size_t)blockIdx.x * kObsStride + t) * 2] = sh_hi[t];
-        part[((size_t)blockIdx.x * kObsStride + t) * 2 + 1] = sh_lo[t];
+        unsigned long long ah = 0, al = 0;
+        for (int wp = 0; wp < kBlock / 32; ++wp) {
+            ah += sh[wp][t][0];
+            al += sh[wp][t][1];
+        }
+        if (ah) atomicAdd(&part[2 * t], ah);
+        if (al) atomicAdd(&part[2 * t + 1], al);
     }
 }
 
@@ -416,18 +603,15 @@ __global__ void __launch_bounds__(kBlock) k_obs_finish(const DevModel* __restric
                                                        const uint64_t* __restrict__ psi0_keys,
                                                        const double2* __restrict__ psi0_amp, int64_t n0,
                                                        const double2* __restrict__ vec, double t, int mode,
-                                                       const unsigned long long* __restrict__ part, int nparts,
+                                                       unsigned long long* __restrict__ part,
                                                        double* __restrict__ rec)
 {
     if (ctr->err) return;
     const int N = M->N;
     __shared__ double nrm;
     for (int i = threadIdx.x; i < 2 * N + 1; i += blockDim.x) {
-        unsigned long long hi = 0, lo = 0;
-        for (int b = 0; b < nparts; ++b) {
-            hi += part[((size_t)b * kObsStride + i) * 2];
-            lo += part[((size_t)b * kObsStride + i) * 2 + 1];
-        }
+        unsigned long long hi = part[2 * i], lo = part[2 * i + 1];
+        part[2 * i] = part[2 * i + 1] = 0ull;     // ready for the next pass
         // (hi + lo 2^-32) 2^-52, carrying the upper bits of lo into hi first
         hi += lo >> 32;
         lo &= 0xFFFFFFFFull;
@@ -440,7 +624,13 @@ __global__ void __launch_bounds__(kBlock) k_obs_finish(const DevModel* __restric
         Key<W> key = load_key<W>(psi0_keys, (uint64_t)k);
         int64_t r = table_lookup<W>(table, slots, key);
         if (r < 0) continue;
-        double2 a = psi0_amp[k], c = vec[r];
+        double2 a = psi0_amp[k], c;
+        if (M->fmt == 1) {
+            c = vec[r];
+        } else {
+            float4 v = reinterpret_cast<const float4*>(vec)[r];
+            c = make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+        }
         acc[0] += a.x * c.x + a.y * c.y;    // conj(a) * c
         acc[1] += a.x * c.y - a.y * c.x;
     }
@@ -449,7 +639,7 @@ __global__ void __launch_bounds__(kBlock) k_obs_finish(const DevModel* __restric
     if (threadIdx.x == 0) {
         bool initial = mode == 1;
         if (mode == 2) ctr->kept = ctr->q;      // the first step propagates every row
-        double norm = initial ? nrm : ctr->norm_r;
+        double norm = nrm;                       // exact fixed-point sum of |c|^2
         rec[PACES_OBS_TIME] = t;
         rec[PACES_OBS_NORM] = norm;
         rec[PACES_OBS_NORM_PHI0] = initial ? norm : ctr->norm_phi0;
@@ -463,6 +653,29 @@ __global__ void __launch_bounds__(kBlock) k_obs_finish(const DevModel* __restric
         rec[PACES_OBS_NORM_BEFORE] = initial ? norm : ctr->norm_last;
         ctr->norm_last = norm;
         ctr->nnz = 0;            // the next step's P H P build counts from zero
+    }
+}
+
+// Descriptors of rows given only as keys (full decode).
+template <int W>
+__global__ void k_meta_from_keys(const DevModel* __restrict__ M, const uint64_t* __restrict__ keys, uint32_t n,
+                                 uint32_t* __restrict__ meta)
+{
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        Key<W> k = load_key<W>(keys, i);
+        uint64_t q0 = udiv(k.w[0], M->div_exc);
+        int s = (int)(k.w[0] - q0 * M->div_exc.d), ns = 0, nph = 0;
+        for (int w = 0; w < W; ++w) {
+            uint64_t x = (w == 0) ? q0 : k.w[w];
+            for (int j = M->word_first[w]; j < M->word_first[w + 1]; ++j) {
+                uint64_t xq = udiv(x, M->div_radix[j]);
+                int nj = (int)(x - xq * M->div_radix[j].d);
+                x = xq;
+                nph += nj;
+                if (j == s) ns = nj;
+            }
+        }
+        meta[i] = meta_pack(s, ns, nph);
     }
 }
 
@@ -505,31 +718,41 @@ __global__ void k_export_csr(const DevModel* __restrict__ M, uint32_t q, const u
 template <int W>
 static int trunc_w(const Bufs& b, int gin, int gout, double th2, int step, cudaStream_t st)
 {
-    k_trunc_count<<<b.G, kBlock, 0, st>>>(b.V[0], b.ctr, th2, b.keepw, b.blk_cnt);
+    k_trunc_count<<<b.G, kBlock, 0, st>>>(b.V[0], b.ctr, th2, dw_from_double(th2), b.fmt, b.keepw, b.blk_cnt);
     k_scan<<<1, 1024, 0, st>>>(b.blk_cnt, b.blk_off, b.G, b.ctr, kScanTrunc, 0, b.cap_rows, step);
     k_trunc_scatter<W><<<b.G, kBlock, 0, st>>>(b.keys[gin], b.V[0], b.ctr, b.keepw, b.blk_off, b.keys[gout],
-                                               b.V[1], b.table[gout], b.table_slots, step);
+                                               b.V[1], b.table[gout], b.table_slots, b.meta[gin], b.meta[gout], step);
     return 3;
 }
 
 template <int W>
 static int level_w(const Bufs& b, int gen, int f, int rescue_gen, int step, cudaStream_t st)
 {
-    k_level_insert<W><<<b.grid, kBlock, 0, st>>>(b.model, b.ctr, f, b.keys[gen], b.table[gen], b.table_slots,
+    k_level_insert<W><<<b.grid, kBlock, 0, st>>>(b.model, b.ctr, f, b.keys[gen], b.meta[gen], b.table[gen],
+                                                 b.table_slots,
                                                  b.cand_slot, b.cand_cap, step);
-    k_level_flags<W><<<b.G, kBlock, 0, st>>>(b.model, b.ctr, f, b.table[gen], b.cand_slot, b.masks, b.blk_cnt);
+    k_level_flags<W><<<b.G, kBlock, 0, st>>>(b.model, b.ctr, f, b.table[gen], b.cand_slot,
+                                             reinterpret_cast<uint32_t*>(b.masks), b.blk_cnt);
     k_scan<<<1, 1024, 0, st>>>(b.blk_cnt, b.blk_off, b.G, b.ctr, kScanLevel, f, b.cap_rows, step);
     const uint64_t* ot = rescue_gen >= 0 ? b.table[rescue_gen] : nullptr;
-    k_level_scatter<W><<<b.G, kBlock, 0, st>>>(b.model, b.ctr, f, b.keys[gen], b.table[gen], b.cand_slot,
-                                               b.masks, b.blk_off, ot, b.table_slots, b.V[0], b.V[1]);
+    k_level_scatter<W><<<b.G, kBlock, 0, st>>>(b.model, b.ctr, f, b.keys[gen], b.meta[gen], b.table[gen],
+                                               b.cand_slot,
+                                               reinterpret_cast<const uint32_t*>(b.masks), b.blk_off, ot,
+                                               b.table_slots, b.V[0], b.V[1]);
     return 4;
 }
 
 template <int W>
 static int csr_w(const Bufs& b, int gen, cudaStream_t st)
 {
-    k_csr<W><<<b.grid, kBlock, 0, st>>>(b.model, b.ctr, b.keys[gen], b.table[gen], b.table_slots, b.col, b.cid,
-                                        b.cnt, b.diag);
+#define PACES_CSR_ARGS \
+    b.model, b.ctr, b.keys[gen], b.meta[gen], b.table[gen], b.table_slots, b.cand_slot, b.col, b.cid, b.cnt, b.diag
+    if (b.D <= 4) k_csr_grp<W, 4><<<b.grid, kBlock, 0, st>>>(PACES_CSR_ARGS);
+    else if (b.D <= 8) k_csr_grp<W, 8><<<b.grid, kBlock, 0, st>>>(PACES_CSR_ARGS);
+    else if (b.D <= 16) k_csr_grp<W, 16><<<b.grid, kBlock, 0, st>>>(PACES_CSR_ARGS);
+    else if (b.D <= 32) k_csr_grp<W, 32><<<b.grid, kBlock, 0, st>>>(PACES_CSR_ARGS);
+    else k_csr<W><<<b.grid, kBlock, 0, st>>>(PACES_CSR_ARGS);
+#undef PACES_CSR_ARGS
     return 1;
 }
 
@@ -537,9 +760,9 @@ template <int W>
 static int observe_w(const Bufs& b, int gen, const double2* vec, double t, int64_t rec, int mode, cudaStream_t st)
 {
     double* r = b.obs + rec * b.rec_len;
-    k_obs_accum<W><<<b.grid, kBlock, 0, st>>>(b.model, b.ctr, b.keys[gen], vec, b.obs_part);
+    k_obs_accum<W><<<b.G, kBlock, 0, st>>>(b.model, b.ctr, b.keys[gen], vec, b.obs_part);
     k_obs_finish<W><<<1, kBlock, 0, st>>>(b.model, b.ctr, b.table[gen], b.table_slots, b.psi0_keys, b.psi0_amp,
-                                          b.n0, vec, t, mode, b.obs_part, b.grid, r);
+                                          b.n0, vec, t, mode, b.obs_part, r);
     return 2;
 }
 
@@ -580,6 +803,12 @@ int launch_decode(const Bufs& b, int gen, uint32_t n, int32_t* site, int32_t* oc
 {
     int grid = b.grid;
     PACES_DISPATCH_W(b.W, (k_decode<KW><<<grid, kBlock, 0, st>>>(b.model, b.keys[gen], n, site, occ), 1))
+}
+
+int launch_meta_from_keys(const Bufs& b, int gen, uint32_t n, cudaStream_t st)
+{
+    int grid = b.grid;
+    PACES_DISPATCH_W(b.W, (k_meta_from_keys<KW><<<grid, kBlock, 0, st>>>(b.model, b.keys[gen], n, b.meta[gen]), 1))
 }
 
 int launch_export_csr(const Bufs& b, uint32_t q, const uint64_t* off, int32_t* cols, double* vals, cudaStream_t st)

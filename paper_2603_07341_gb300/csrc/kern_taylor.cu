@@ -2,6 +2,11 @@
 //   phi_0 = c',  phi_n = (-i dt / n) (P H P) phi_{n-1},  r = sum_n phi_n,
 // stopping at the first n >= 2 with ||phi_n||^2 <= tol^2 ||r||^2.
 //
+// Two arithmetic variants share the structure below: k_taylor_dw keeps every
+// amplitude as a double-word (FP32 pair) and accumulates each row with the
+// compensated dot product (FP32 pipe, 48-bit significand); k_taylor_f64 does
+// the same in FP64 (the FP64 pipe of this part is the bottleneck there).
+//
 // One cooperative launch runs every term of a step: each term is one pass of
 // SpMV over the row-pitched P H P fused with the scaling, the accumulation
 // r += phi_n and the FP64 norm partials; the term ends at a grid barrier whose
@@ -117,7 +122,7 @@ __device__ __forceinline__ double2 row_apply(const uint32_t* __restrict__ col, c
 }
 
 template <int LPR>
-__global__ void __launch_bounds__(kBlock) k_taylor(TaylorArgs a)
+__global__ void __launch_bounds__(kBlock) k_taylor_f64(TaylorArgs a)
 {
     __shared__ double coef[kMaxCoefs];
     __shared__ double tsh[4];
@@ -203,12 +208,244 @@ __global__ void __launch_bounds__(kBlock) k_taylor(TaylorArgs a)
     }
 }
 
+// ---------------------------------------------------------------- double-word variant
+struct Red8 {
+    float phi2, r2;
+    dwf e, n0;
+};
+
+__device__ __forceinline__ Red8 red8_add(const Red8& x, const Red8& y)
+{
+    return {__fadd_rn(x.phi2, y.phi2), __fadd_rn(x.r2, y.r2), dw_add(x.e, y.e), dw_add(x.n0, y.n0)};
+}
+
+__device__ __forceinline__ Red8 red8_shfl_xor(const Red8& v, int o)
+{
+    Red8 r;
+    r.phi2 = __shfl_xor_sync(0xffffffffu, v.phi2, o);
+    r.r2 = __shfl_xor_sync(0xffffffffu, v.r2, o);
+    r.e.hi = __shfl_xor_sync(0xffffffffu, v.e.hi, o);
+    r.e.lo = __shfl_xor_sync(0xffffffffu, v.e.lo, o);
+    r.n0.hi = __shfl_xor_sync(0xffffffffu, v.n0.hi, o);
+    r.n0.lo = __shfl_xor_sync(0xffffffffu, v.n0.lo, o);
+    return r;
+}
+
+// Fixed-order block reduction; the result is valid in thread 0.
+__device__ __forceinline__ Red8 red8_block(Red8 v)
+{
+    __shared__ Red8 ws[kBlock / 32];
+    for (int o = 16; o > 0; o >>= 1) v = red8_add(v, red8_shfl_xor(v, o));
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int w = 1; w < kBlock / 32; ++w) v = red8_add(v, ws[w]);
+    __syncthreads();
+    return v;
+}
+
+__device__ __forceinline__ void red8_store(float* p, const Red8& v)
+{
+    p[0] = v.phi2; p[1] = v.r2; p[2] = v.e.hi; p[3] = v.e.lo; p[4] = v.n0.hi; p[5] = v.n0.lo;
+}
+
+__device__ __forceinline__ Red8 red8_load(const float* p)
+{
+    return {__ldcg(p), __ldcg(p + 1), {__ldcg(p + 2), __ldcg(p + 3)}, {__ldcg(p + 4), __ldcg(p + 5)}};
+}
+
+// Grid barrier whose last arriving block reduces the per-block partials (8
+// floats each) in block order and publishes the totals.  Bounded waits.
+__device__ __forceinline__ bool barrier_reduce8(Counters* ctr, const float* part, float* tot, unsigned G)
+{
+    __shared__ int last, ok;
+    __threadfence();
+    __syncthreads();
+    unsigned g = 0;
+    if (threadIdx.x == 0) {
+        ok = 1;
+        g = *(volatile unsigned*)&ctr->bar_gen;
+        __threadfence();
+        last = (atomicAdd(&ctr->bar_count, 1u) + 1u == G);
+    }
+    __syncthreads();
+    if (last) {
+        __threadfence();
+        Red8 acc{0.f, 0.f, {0.f, 0.f}, {0.f, 0.f}};
+        for (unsigned b = threadIdx.x; b < G; b += blockDim.x) acc = red8_add(acc, red8_load(part + 8 * b));
+        acc = red8_block(acc);
+        if (threadIdx.x == 0) red8_store(tot, acc);
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            atomicExch(&ctr->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&ctr->bar_gen, 1u);
+        }
+    } else if (threadIdx.x == 0) {
+        uint64_t t0 = global_ns();
+        while (*(volatile unsigned*)&ctr->bar_gen == g) {
+            __nanosleep(20);
+            if (global_ns() - t0 > kBarrierTimeoutNs) {
+                atomicCAS(&ctr->err, 0, (int)kErrBarrier);
+                ok = 0;
+                break;
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// Accumulate the off-diagonal entries of one row into Dot2 accumulators.
+template <int LPR>
+__device__ __forceinline__ void row_apply_dw(const uint32_t* __restrict__ col, const uint8_t* __restrict__ cid,
+                                             uint32_t c, uint64_t base, const dwf* coef,
+                                             const float4* __restrict__ x, int lane, Dot2& re, Dot2& im)
+{
+    if constexpr (LPR == 1) {
+        for (uint32_t e = 0; e < c; e += 4) {
+            uint4 cc = *reinterpret_cast<const uint4*>(col + base + e);
+            uint32_t ii = *reinterpret_cast<const uint32_t*>(cid + base + e);
+            uint32_t cs[4] = {cc.x, cc.y, cc.z, cc.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (e + k < c) {
+                    dwf a = coef[(ii >> (8 * k)) & 0xFFu];
+                    float4 xv = x[cs[k]];
+                    dot2_mac(re, a, xv.x, xv.y);
+                    dot2_mac(im, a, xv.z, xv.w);
+                }
+            }
+        }
+    } else {
+        for (uint32_t e = lane; e < c; e += LPR) {
+            dwf a = coef[cid[base + e]];
+            float4 xv = x[col[base + e]];
+            dot2_mac(re, a, xv.x, xv.y);
+            dot2_mac(im, a, xv.z, xv.w);
+        }
+#pragma unroll
+        for (int o = LPR / 2; o > 0; o >>= 1) {
+            float s2 = __shfl_xor_sync(0xffffffffu, re.s, o, LPR), c2 = __shfl_xor_sync(0xffffffffu, re.c, o, LPR);
+            dwf t = two_sum(re.s, s2);
+            re.s = t.hi;
+            re.c = __fadd_rn(__fadd_rn(re.c, c2), t.lo);
+            s2 = __shfl_xor_sync(0xffffffffu, im.s, o, LPR);
+            c2 = __shfl_xor_sync(0xffffffffu, im.c, o, LPR);
+            t = two_sum(im.s, s2);
+            im.s = t.hi;
+            im.c = __fadd_rn(__fadd_rn(im.c, c2), t.lo);
+        }
+    }
+}
+
+template <int LPR>
+__global__ void __launch_bounds__(kBlock) k_taylor_dw(TaylorArgs a)
+{
+    __shared__ dwf coef[kMaxCoefs];
+    __shared__ float tsh[8];
+    Counters* ctr = a.ctr;
+    if (ctr->err) return;
+    const DevModel* M = a.M;
+    const int ncoef = M->ncoef;
+    const uint32_t q = ctr->q;
+    const uint64_t P = (uint64_t)M->P;
+    const unsigned G = gridDim.x;
+    constexpr uint32_t RPW = 32 / LPR;
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (G * blockDim.x) >> 5;
+    const int lane = (threadIdx.x & 31) % LPR;
+    const uint32_t sub = (threadIdx.x & 31) / LPR;
+    const float4* X = reinterpret_cast<const float4*>(a.c_in);
+    float4* Y = reinterpret_cast<float4*>(a.ta);
+    float4* R = reinterpret_cast<float4*>(a.r);
+    const float2* DG = reinterpret_cast<const float2*>(a.diag);
+    const float kScale = 4294967296.0f;       // 2^32: keeps the coarse norms in FP32 range
+
+    const int fixed = a.p.fixed_terms;
+    const int nlimit = fixed > 0 ? fixed : a.p.nmax;
+    const float tol2 = (float)a.p.tol2;
+    dwf E{0.f, 0.f}, N0{0.f, 0.f};
+    int nd = 0;
+    bool conv = false;
+    for (int n = 1; n <= nlimit; ++n) {
+        const double s = a.p.dt / (double)n;
+        const dwf sdw = dw_from_double(s);
+        __syncthreads();
+        for (int t = threadIdx.x; t < ncoef; t += blockDim.x) coef[t] = dw_from_double(s * M->coef[t]);
+        __syncthreads();
+        Red8 acc{0.f, 0.f, {0.f, 0.f}, {0.f, 0.f}};
+        for (uint32_t rb = warp * RPW; rb < q; rb += nwarps * RPW) {
+            uint32_t row = rb + sub;
+            bool valid = row < q;
+            uint32_t c = valid ? a.cnt[row] : 0u;
+            uint64_t base = (uint64_t)row * P;
+            Dot2 re{0.f, 0.f}, im{0.f, 0.f};
+            row_apply_dw<LPR>(a.col, a.cid, c, base, coef, X, lane, re, im);
+            if (valid && lane == 0) {
+                float4 xi = X[row];
+                float2 d = DG[row];
+                dwf ds = dw_mul(dwf{d.x, d.y}, sdw);
+                dot2_mac(re, ds, xi.x, xi.y);
+                dot2_mac(im, ds, xi.z, xi.w);
+                dwf yre = dot2_result(re), yim = dot2_result(im);      // y = s H x
+                float4 phi = make_float4(yim.hi, yim.lo, -yre.hi, -yre.lo);   // phi = -i y
+                Y[row] = phi;
+                float4 rr = (n == 1) ? xi : R[row];
+                dwf r_re = dw_add(dwf{rr.x, rr.y}, dwf{phi.x, phi.y});
+                dwf r_im = dw_add(dwf{rr.z, rr.w}, dwf{phi.z, phi.w});
+                R[row] = make_float4(r_re.hi, r_re.lo, r_im.hi, r_im.lo);
+                float p0 = phi.x * kScale, p1 = phi.z * kScale, q0 = r_re.hi * kScale, q1 = r_im.hi * kScale;
+                acc.phi2 = __fmaf_rn(p0, p0, __fmaf_rn(p1, p1, acc.phi2));
+                acc.r2 = __fmaf_rn(q0, q0, __fmaf_rn(q1, q1, acc.r2));
+                if (n == 1) {
+                    acc.e = dw_add(acc.e, dw_add(dw_mul(dwf{xi.x, xi.y}, yre), dw_mul(dwf{xi.z, xi.w}, yim)));
+                    acc.n0 = dw_add(acc.n0, dw_norm2(xi));
+                }
+            }
+        }
+        float* part = reinterpret_cast<float*>(a.partials) + (size_t)(n & 1) * G * 8;
+        float* tot = reinterpret_cast<float*>(a.totals) + (n & 1) * 8;
+        acc = red8_block(acc);
+        if (threadIdx.x == 0) red8_store(part + 8 * blockIdx.x, acc);
+        if (!barrier_reduce8(ctr, part, tot, G)) return;
+        if (threadIdx.x < 6) tsh[threadIdx.x] = __ldcg(tot + threadIdx.x);
+        __syncthreads();
+        nd = n;
+        if (n == 1) {
+            E = dwf{tsh[2], tsh[3]};
+            N0 = dwf{tsh[4], tsh[5]};
+        }
+        bool stop = fixed <= 0 && n >= 2 && tsh[0] <= tol2 * tsh[1];
+        if (stop) {
+            conv = true;
+            break;
+        }
+        X = Y;
+        Y = (Y == reinterpret_cast<float4*>(a.ta)) ? reinterpret_cast<float4*>(a.tb)
+                                                   : reinterpret_cast<float4*>(a.ta);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctr->nterms = nd;
+        ctr->norm_phi0 = (double)N0.hi + (double)N0.lo;
+        ctr->energy = ((double)E.hi + (double)E.lo) / a.p.dt;
+        ctr->norm_r = 0.0;
+        if (!conv && fixed <= 0 && atomicCAS(&ctr->err, 0, (int)kErrNoConverge) == 0) {
+            ctr->err_step = a.p.step;
+            ctr->err_info = nd;
+        }
+    }
+}
+
 template <int LPR>
 static int occupancy()
 {
-    int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_taylor<LPR>, kBlock, 0);
-    return nb;
+    int n1 = 0, n2 = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n1, k_taylor_f64<LPR>, kBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n2, k_taylor_dw<LPR>, kBlock, 0);
+    return n1 < n2 ? n1 : n2;
 }
 
 int taylor_blocks_per_sm(int lpr, int c64)
@@ -238,8 +475,13 @@ int launch_taylor(const Bufs& b, const TaylorParams& p, cudaStream_t st)
     a.totals = b.partials + 2 * 4 * (size_t)b.taylor_grid;
     a.p = p;
     void* args[] = {&a};
-    const void* fn = p.lpr == 1 ? (const void*)k_taylor<1> : p.lpr == 4 ? (const void*)k_taylor<4>
-                                                                        : (const void*)k_taylor<8>;
+    const void* fn;
+    if (p.fmt == 1)
+        fn = p.lpr == 1 ? (const void*)k_taylor_f64<1> : p.lpr == 4 ? (const void*)k_taylor_f64<4>
+                                                                    : (const void*)k_taylor_f64<8>;
+    else
+        fn = p.lpr == 1 ? (const void*)k_taylor_dw<1> : p.lpr == 4 ? (const void*)k_taylor_dw<4>
+                                                                   : (const void*)k_taylor_dw<8>;
     cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(b.taylor_grid), dim3(kBlock), args, 0, st);
     return e == cudaSuccess ? 1 : -1;
 }

@@ -65,7 +65,7 @@ static paces_status need_bytes(const paces_params* params, int64_t n_in, int64_t
     size_t sw = W == 1 ? 2 : (W <= 3 ? 4 : 6);
     size_t need = up256(sizeof(DevModel)) + up256(sizeof(Counters)) + 2 * up256(4 * kMaxChunkBlocks) +
                   up256((size_t)slots * sw * 8) + up256((size_t)n_in * D * 4) + up256((size_t)n_in * 8) +
-                  up256((size_t)rows * sizeof(double2));
+                  up256((size_t)rows * sizeof(double2)) + up256((size_t)rows * 4);
     *bytes = (int64_t)need;
     return PACES_OK;
 }
@@ -119,6 +119,7 @@ extern "C" paces_status paces_expand_noalloc(const paces_params* params, const u
     b.masks = (uint64_t*)carve((size_t)n_in * 8);
     b.V[1] = (double2*)carve((size_t)rows * sizeof(double2));
     b.V[0] = b.V[1];                       // no previous state: rescue is off
+    b.meta[0] = (uint32_t*)carve((size_t)rows * 4);
     b.keys[0] = keys_out;
     b.table_slots = slots;
     b.cap_rows = (uint32_t)rows;
@@ -141,6 +142,7 @@ extern "C" paces_status paces_expand_noalloc(const paces_params* params, const u
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(keys_out, keys_in, (size_t)n_in * W * 8, cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess) {
+        launch_meta_from_keys(b, 0, (uint32_t)n_in, st);
         launch_insert_rows(b, 0, (uint32_t)n_in, st);
         launch_level(b, 0, 0, -1, 0, st);
         e = cudaGetLastError();

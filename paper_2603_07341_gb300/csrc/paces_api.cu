@@ -187,7 +187,10 @@ paces_status check_params(const paces_params* p, std::string& why)
     for (int j = 0; j < N; ++j)
         if (p->phonon_cap[j] < 0 || p->phonon_cap[j] > kMaxCap) { why = "phonon_cap out of range"; return PACES_ERR_INVALID; }
     if (p->m < 0) { why = "m < 0"; return PACES_ERR_INVALID; }
-    if (p->precision != PACES_C128 && p->precision != PACES_C64_SPMV) { why = "precision"; return PACES_ERR_INVALID; }
+    if (p->precision != PACES_DW && p->precision != PACES_C128 && p->precision != PACES_C64_SPMV) {
+        why = "precision";
+        return PACES_ERR_INVALID;
+    }
     if (p->taylor_tol < 0 || p->taylor_nmax < 0 || p->fixed_terms < 0) { why = "series limits"; return PACES_ERR_INVALID; }
     return PACES_OK;
 }
@@ -268,6 +271,7 @@ paces_status alloc_rows(paces_t h, uint32_t cap, std::vector<DevAlloc>& out, Buf
     auto chk = [&](void* p) { ok = ok && p; };
     for (int g = 0; g < 2; ++g) {
         chk(b.keys[g] = alloc_track<uint64_t>(h, h->row_allocs, (size_t)cap * h->W));
+        chk(b.meta[g] = alloc_track<uint32_t>(h, h->row_allocs, cap));
         chk(b.table[g] = alloc_track<uint64_t>(h, h->row_allocs, slots * sw));
     }
     for (int v = 0; v < 4; ++v) chk(b.V[v] = alloc_track<double2>(h, h->row_allocs, cap));
@@ -332,17 +336,21 @@ paces_status grow(paces_t h, uint64_t want, uint32_t q, int vec)
     if (want > kMaxRowsHard) return fail(h, PACES_ERR_CAPACITY, "more rows than 32-bit row indices allow");
     uint64_t* sk = nullptr;
     double2* sv = nullptr;
-    size_t kb = (size_t)q * h->W * 8, vb = (size_t)q * sizeof(double2);
+    uint32_t* sm = nullptr;
+    size_t kb = (size_t)q * h->W * 8, vb = (size_t)q * sizeof(double2), mb = (size_t)q * 4;
     if (q > 0 && cur > 0) {
         sk = (uint64_t*)dev_alloc(h, kb);
         sv = (double2*)dev_alloc(h, vb);
-        if (!sk || !sv) {
+        sm = (uint32_t*)dev_alloc(h, mb);
+        if (!sk || !sv || !sm) {
             if (sk) dev_free(h, {sk, kb});
             if (sv) dev_free(h, {sv, vb});
+            if (sm) dev_free(h, {sm, mb});
             return fail(h, PACES_ERR_CAPACITY, "no room to stash the state while growing");
         }
         CUDA_TRY(h, cudaMemcpyAsync(sk, h->b.keys[h->gen], kb, cudaMemcpyDeviceToDevice, h->st));
         CUDA_TRY(h, cudaMemcpyAsync(sv, h->b.V[vec], vb, cudaMemcpyDeviceToDevice, h->st));
+        CUDA_TRY(h, cudaMemcpyAsync(sm, h->b.meta[h->gen], mb, cudaMemcpyDeviceToDevice, h->st));
     }
     free_rows(h);
     Bufs nb = h->b;
@@ -357,6 +365,7 @@ paces_status grow(paces_t h, uint64_t want, uint32_t q, int vec)
     if (!got) {
         if (sk) dev_free(h, {sk, kb});
         if (sv) dev_free(h, {sv, vb});
+        if (sm) dev_free(h, {sm, mb});
         h->has_state = false;
         return fail(h, PACES_ERR_CAPACITY, "device allocation failed; the state was lost");
     }
@@ -366,8 +375,10 @@ paces_status grow(paces_t h, uint64_t want, uint32_t q, int vec)
     if (sk) {
         CUDA_TRY(h, cudaMemcpyAsync(h->b.keys[h->gen], sk, kb, cudaMemcpyDeviceToDevice, h->st));
         CUDA_TRY(h, cudaMemcpyAsync(h->b.V[vec], sv, vb, cudaMemcpyDeviceToDevice, h->st));
+        CUDA_TRY(h, cudaMemcpyAsync(h->b.meta[h->gen], sm, mb, cudaMemcpyDeviceToDevice, h->st));
         dev_free(h, {sk, kb});
         dev_free(h, {sv, vb});
+        dev_free(h, {sm, mb});
     }
     paces_status s = clear_table(h, h->gen);
     if (s) return s;
@@ -413,6 +424,7 @@ TaylorParams taylor_params(paces_t h, double dt, int step)
     p.step = step;
     p.lpr = h->lpr;
     p.c64 = h->prm.precision == PACES_C64_SPMV;
+    p.fmt = h->b.fmt;
     return p;
 }
 
@@ -510,7 +522,12 @@ paces_status paces::fill_model(const paces_params* params, const paces_layout& L
         M->gnz[j] = at(params->g, j) != 0.0;
         M->eps[j] = at(params->eps, j);
         M->omega[j] = at(params->omega, j);
+        M->eps_dw[j] = dw_from_double(M->eps[j]);
+        M->omega_dw[j] = dw_from_double(M->omega[j]);
     }
+    M->uniform_omega = 1;
+    for (int j = 1; j < N; ++j) M->uniform_omega &= (M->omega[j] == M->omega[0]);
+    M->fmt = params->precision == PACES_C128 ? 1 : 0;
     while (w < L.words) M->word_first[++w] = N;
     std::map<std::tuple<double, double, double>, int> ids;
     auto cid_of = [&](double v, double dJ, double dg) -> int {
@@ -590,6 +607,7 @@ paces_status paces_create(const paces_params* params, const paces_allocator* all
     paces_layout L;
     paces_status s = plan(params, &L, why);
     if (s) return s;
+    if (params->precision == PACES_C64_SPMV) return PACES_ERR_UNSUPPORTED;
     paces_t h = new paces_handle();
     h->prm = *params;
     int N = params->n_sites;
@@ -639,6 +657,7 @@ paces_status paces_create(const paces_params* params, const paces_allocator* all
     b.D = h->D;
     b.P = h->P;
     b.N = N;
+    b.fmt = M->fmt;
     b.G = std::min(kMaxChunkBlocks, h->sms * 4);
     b.grid = h->sms * 8;
     int bps = taylor_blocks_per_sm(h->lpr, 0);
@@ -690,7 +709,7 @@ paces_status paces_destroy(paces_t h)
 const char* paces_last_error(paces_t h) { return h ? h->err.c_str() : "NULL handle"; }
 
 static paces_status encode_state(paces_t h, int64_t n, const int32_t* site, const int32_t* occ,
-                                 std::vector<uint64_t>& keys)
+                                 std::vector<uint64_t>& keys, std::vector<uint32_t>& meta)
 {
     if (n <= 0 || !site || !occ) return fail(h, PACES_ERR_INVALID, "empty state or NULL arrays");
     if ((uint64_t)n > kMaxRowsHard) return fail(h, PACES_ERR_INVALID, "too many states");
@@ -701,6 +720,12 @@ static paces_status encode_state(paces_t h, int64_t n, const int32_t* site, cons
             if (occ[i * h->N + j] > h->cap[j]) return fail(h, PACES_ERR_INVALID, "occupation above the phonon cap");
     paces_status s = encode(&h->lay, n, site, occ, keys.data(), why);
     if (s) return fail(h, s, why);
+    meta.resize((size_t)n);
+    for (int64_t i = 0; i < n; ++i) {
+        int nph = 0;
+        for (int j = 0; j < h->N; ++j) nph += occ[i * h->N + j];
+        meta[i] = meta_pack(site[i], occ[i * h->N + site[i]], nph);
+    }
     std::vector<int64_t> idx((size_t)n);
     for (int64_t i = 0; i < n; ++i) idx[i] = i;
     int W = h->W;
@@ -714,7 +739,20 @@ static paces_status encode_state(paces_t h, int64_t n, const int32_t* site, cons
     return PACES_OK;
 }
 
-static paces_status upload_rows(paces_t h, int64_t n, const std::vector<uint64_t>& keys, const double* amps, int vec)
+// Host amplitudes (re, im) in FP64 to the device storage format (16 bytes each).
+static std::vector<float> to_dw(int64_t n, const double* amps)
+{
+    std::vector<float> out((size_t)n * 4);
+    for (int64_t i = 0; i < 2 * n; ++i) {
+        dwf d = dw_from_double(amps[i]);
+        out[2 * i] = d.hi;
+        out[2 * i + 1] = d.lo;
+    }
+    return out;
+}
+
+static paces_status upload_rows(paces_t h, int64_t n, const std::vector<uint64_t>& keys,
+                                const std::vector<uint32_t>& meta, const double* amps, int vec)
 {
     if ((uint64_t)n * 2 > h->cap_rows) {
         paces_status s = grow(h, (uint64_t)n * 2, 0, 0);
@@ -724,7 +762,14 @@ static paces_status upload_rows(paces_t h, int64_t n, const std::vector<uint64_t
     paces_status s = clear_table(h, 0);
     if (s) return s;
     CUDA_TRY(h, cudaMemcpyAsync(h->b.keys[0], keys.data(), keys.size() * 8, cudaMemcpyHostToDevice, h->st));
-    CUDA_TRY(h, cudaMemcpyAsync(h->b.V[vec], amps, (size_t)n * sizeof(double2), cudaMemcpyHostToDevice, h->st));
+    CUDA_TRY(h, cudaMemcpyAsync(h->b.meta[0], meta.data(), meta.size() * 4, cudaMemcpyHostToDevice, h->st));
+    if (h->b.fmt == 1) {
+        CUDA_TRY(h, cudaMemcpyAsync(h->b.V[vec], amps, (size_t)n * sizeof(double2), cudaMemcpyHostToDevice, h->st));
+    } else {
+        std::vector<float> d = to_dw(n, amps);
+        CUDA_TRY(h, cudaMemcpyAsync(h->b.V[vec], d.data(), (size_t)n * 16, cudaMemcpyHostToDevice, h->st));
+        CUDA_TRY(h, cudaStreamSynchronize(h->st));
+    }
     count(h, Stage::Other, launch_insert_rows(h->b, 0, (uint32_t)n, h->st));
     std::memset(h->hctr, 0, sizeof(Counters));
     h->hctr->q = (uint32_t)n;
@@ -733,6 +778,7 @@ static paces_status upload_rows(paces_t h, int64_t n, const std::vector<uint64_t
     h->hctr->level_off[0] = 0;
     h->hctr->level_off[1] = (uint32_t)n;
     h->hctr->nlevels = 1;
+    CUDA_TRY(h, cudaMemsetAsync(h->b.obs_part, 0, sizeof(unsigned long long) * 2 * (2 * kMaxSites + 1), h->st));
     return set_counters(h);
 }
 
@@ -741,7 +787,8 @@ paces_status paces_set_state(paces_t h, int64_t n, const int32_t* site, const in
     if (!h) return PACES_ERR_INVALID;
     if (!amps) return fail(h, PACES_ERR_INVALID, "amps is NULL");
     std::vector<uint64_t> keys;
-    paces_status s = encode_state(h, n, site, occ, keys);
+    std::vector<uint32_t> meta;
+    paces_status s = encode_state(h, n, site, occ, keys, meta);
     if (s) return s;
     // psi(0) copy for the autocorrelation
     if (n > h->psi0_cap) {
@@ -762,7 +809,7 @@ paces_status paces_set_state(paces_t h, int64_t n, const int32_t* site, const in
     CUDA_TRY(h, cudaMemcpyAsync(h->b.psi0_amp, amps, (size_t)n * sizeof(double2), cudaMemcpyHostToDevice, h->st));
     h->b.n0 = n;
     for (int attempt = 0;; ++attempt) {
-        s = upload_rows(h, n, keys, amps, 1);
+        s = upload_rows(h, n, keys, meta, amps, 1);
         if (s) return s;
         int f = 0;
         bool overflow = false;
@@ -807,9 +854,10 @@ paces_status paces_load_state(paces_t h, int64_t n, const int32_t* site, const i
     if (!h) return PACES_ERR_INVALID;
     if (!amps) return fail(h, PACES_ERR_INVALID, "amps is NULL");
     std::vector<uint64_t> keys;
-    paces_status s = encode_state(h, n, site, occ, keys);
+    std::vector<uint32_t> meta;
+    paces_status s = encode_state(h, n, site, occ, keys, meta);
     if (s) return s;
-    s = upload_rows(h, n, keys, amps, 0);
+    s = upload_rows(h, n, keys, meta, amps, 0);
     if (s) return s;
     h->fresh = false;
     h->has_state = true;
@@ -959,6 +1007,14 @@ paces_status paces_get_state(paces_t h, int64_t max, int32_t* site, int32_t* occ
     if (amps) {
         const double2* v = h->fresh ? h->b.V[1] : h->b.V[0];
         CUDA_TRY(h, cudaMemcpyAsync(amps, v, (size_t)q * sizeof(double2), cudaMemcpyDeviceToHost, h->st));
+        CUDA_TRY(h, cudaStreamSynchronize(h->st));
+        if (h->b.fmt == 0) {            // double-word pairs -> FP64, in place
+            const float* f = reinterpret_cast<const float*>(amps);
+            for (uint64_t i = 0; i < 2ull * q; ++i) {
+                float hi = f[2 * i], lo = f[2 * i + 1];
+                amps[i] = (double)hi + (double)lo;
+            }
+        }
     }
     CUDA_TRY(h, cudaStreamSynchronize(h->st));
     return PACES_OK;
@@ -1016,7 +1072,17 @@ paces_status paces_get_hamiltonian(paces_t h, int32_t* cnt, int32_t* cols, doubl
     *nnz = (int64_t)off[q];
     if (cnt)
         for (uint32_t i = 0; i < q; ++i) cnt[i] = c8[i];
-    if (diag && q) CUDA_TRY(h, cudaMemcpyAsync(diag, h->b.diag, (size_t)q * 8, cudaMemcpyDeviceToHost, h->st));
+    if (diag && q) {
+        CUDA_TRY(h, cudaMemcpyAsync(diag, h->b.diag, (size_t)q * 8, cudaMemcpyDeviceToHost, h->st));
+        CUDA_TRY(h, cudaStreamSynchronize(h->st));
+        if (h->b.fmt == 0) {
+            const float* f = reinterpret_cast<const float*>(diag);
+            for (uint32_t i = 0; i < q; ++i) {
+                float hi = f[2 * i], lo = f[2 * i + 1];
+                diag[i] = (double)hi + (double)lo;
+            }
+        }
+    }
     if ((cols || vals) && off[q] > 0) {
         if ((int64_t)off[q] > max_nnz) return fail(h, PACES_ERR_INVALID, "max_nnz too small");
         uint64_t* doff = (uint64_t*)dev_alloc(h, (size_t)q * 8);

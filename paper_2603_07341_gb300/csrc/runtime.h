@@ -18,6 +18,7 @@ struct Bufs {
     const DevModel* model;
     Counters* ctr;
     uint64_t* keys[2];             // row -> key, two generations
+    uint32_t* meta[2];             // row -> (site, phonons at site, total phonons)
     uint64_t* table[2];            // hash tables, two generations
     uint64_t table_slots;          // slots per table (below 2^32)
     double2* V[4];                 // V0: state / accumulator r, V1: c' (phi_0), V2, V3: terms
@@ -40,6 +41,7 @@ struct Bufs {
     uint32_t cap_rows;
     uint64_t cand_cap;
     int W, D, P, N;
+    int fmt;                        // amplitude storage: 0 double-word, 1 FP64
     int G;                          // blocks of chunked kernels
     int grid;                       // blocks of grid-stride kernels
     int taylor_grid;                // blocks of the cooperative propagator
@@ -54,6 +56,7 @@ struct TaylorParams {
     int step;
     int lpr;                        // lanes per row (1, 4 or 8)
     int c64;                        // complex64 SpMV terms
+    int fmt;                        // amplitude storage: 0 double-word, 1 FP64
 };
 
 // Stage launchers; each returns the number of kernels it launched (or -1 on a
@@ -67,6 +70,7 @@ int launch_observe(const Bufs& b, int gen, const double2* vec, double t, int64_t
                    int mode, cudaStream_t st);
 int launch_decode(const Bufs& b, int gen, uint32_t n, int32_t* site, int32_t* occ,
                   cudaStream_t st);
+int launch_meta_from_keys(const Bufs& b, int gen, uint32_t n, cudaStream_t st);
 int launch_export_csr(const Bufs& b, uint32_t q, const uint64_t* off, int32_t* cols,
                       double* vals, cudaStream_t st);
 

@@ -103,11 +103,14 @@ def test_initial_expansion_keys_bitexact(libpaces, name, over):
     assert list(lv) == list(olv[: len(lv)]) and len(lv) in (len(olv), len(olv) - 1)
 
 
+@pytest.mark.parametrize("precision", [B.DW, B.C128], ids=["dw", "c128"])
 @pytest.mark.parametrize("name,over", SET_STATE_CASES, ids=[c[0] for c in SET_STATE_CASES])
-def test_hamiltonian_parity(libpaces, name, over):
-    """P_m H P_m: per-row counts, columns and values in move order, diagonal."""
+def test_hamiltonian_parity(libpaces, name, over, precision):
+    """P_m H P_m: per-row counts, columns and values in move order, diagonal
+    (bit-exact in FP64; within the double-word rounding, 2^-47 relative,
+    when the diagonal is held as a double-word)."""
     cfg = W.CONFIGS[name]
-    gpu, ora = make_pair(cfg, **over)
+    gpu, ora = make_pair(cfg, gpu_extra=dict(precision=precision), **over)
     st = W.start_state(cfg)
     gpu.set_state(*st)
     ora.set_state(*st)
@@ -116,23 +119,28 @@ def test_hamiltonian_parity(libpaces, name, over):
     assert np.array_equal(cg, co)
     assert np.array_equal(colg, colo)
     assert np.array_equal(vg, vo)
-    assert np.array_equal(dg, do)
+    if precision == B.C128:
+        assert np.array_equal(dg, do)
+    else:
+        assert np.all(np.abs(dg - do) <= 2.0 ** -47 * np.abs(do))
 
 
-def test_ring4_full_trajectory(libpaces):
+@pytest.mark.parametrize("precision", [B.DW, B.C128], ids=["dw", "c128"])
+def test_ring4_full_trajectory(libpaces, precision):
     """Config ring4: 200 steps of dt = 0.05 at theta = 1e-8 in lockstep."""
     cfg = W.CONFIGS["ring4"]
-    gpu, ora = make_pair(cfg)
+    gpu, ora = make_pair(cfg, gpu_extra=dict(precision=precision))
     gpu.set_state(*W.start_state(cfg))
     ora.set_state(*W.start_state(cfg))
     lockstep(gpu, ora, cfg["dt"], cfg["theta"], cfg["nsteps"], check_every=10)
     assert gpu.num_records() == cfg["nsteps"] + 1
 
 
-def test_ring16_trajectory_prefix(libpaces):
+@pytest.mark.parametrize("precision", [B.DW, B.C128], ids=["dw", "c128"])
+def test_ring16_trajectory_prefix(libpaces, precision):
     """Config ring16 (the throughput workload): the first 40 steps in lockstep."""
     cfg = W.CONFIGS["ring16"]
-    gpu, ora = make_pair(cfg)
+    gpu, ora = make_pair(cfg, gpu_extra=dict(precision=precision))
     gpu.set_state(*W.start_state(cfg))
     ora.set_state(*W.start_state(cfg))
     lockstep(gpu, ora, cfg["dt"], cfg["theta"], 40, check_every=5)
@@ -208,7 +216,7 @@ def test_frozen_single_state(libpaces):
     g.step(0.1, 30, 1e-6)
     rec = B.records_dict(g.observables(), 3)
     assert np.all(rec["rows"] == 1)
-    assert np.max(np.abs(rec["C"] - np.exp(-0.7j * rec["time"]))) < 1e-13
+    assert np.max(np.abs(rec["C"] - np.exp(-0.7j * rec["time"]))) < 1e-12
 
 
 def test_capacity_grows_and_matches(libpaces):
