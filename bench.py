@@ -28,7 +28,6 @@ import statistics
 import subprocess
 import sys
 import tempfile
-import threading
 import time
 
 import numpy as np
@@ -131,15 +130,24 @@ def taylor_counts(rec, h_words):
     return units, bytes_, flops
 
 
-def traffic_from_profile(kernel_src):
-    """ncu DRAM bytes per launch of the propagator, if taken on this source."""
-    path = os.path.join(ROOT, "profiles", "k_taylor_ring16_traffic.json")
+def traffic_from_profile(kernel_src, end_step):
+    """ncu DRAM bytes per launch of the propagator at this window, if the
+    summary in profiles/ was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "k_taylor_dw_ring16_traffic.md")
     if not os.path.exists(path):
         return None
-    with open(path) as f:
-        d = json.load(f)
+    fields = {}
+    for line in open(path):
+        if ":" in line and line.startswith("- "):
+            k, v = line[2:].split(":", 1)
+            fields[k.strip()] = v.strip()
     h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
-    return d.get("bytes_per_launch") if d.get("source_sha") == h else None
+    if fields.get("kernel source sha256[:16]") != h or fields.get("window end step") != str(end_step):
+        return None
+    try:
+        return float(fields["dram bytes per launch"])
+    except (KeyError, ValueError):
+        return None
 
 
 def cpu_baseline(cfg, budget_s=15.0, max_steps=None):
@@ -200,10 +208,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="ring16", choices=sorted(W.CONFIGS))
-    ap.add_argument("--end-step", type=int, default=None, help="last timed step (default: the config's)")
+    ap.add_argument("--end-step", type=int, default=500,
+                    help="last timed step (the ring16 trajectory has 1000; 0 = the whole trajectory)")
+    ap.add_argument("--precision", default="dw", choices=["dw", "c128"])
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     cfg = W.CONFIGS[args.workload]
     if args.impl == "reference":
@@ -226,42 +235,56 @@ def main():
     end = args.end_step or cfg["nsteps"]
     start = max(0, end - K - Wm)
     model = W.model_kwargs(cfg)
+    model["precision"] = {"dw": B.DW, "c128": B.C128}[args.precision]
     sol = B.Solver(**model)
-    sol.set_state(*W.start_state(cfg))
-    sol.step(cfg["dt"], start, cfg["theta"])            # advance to the window (untimed)
-    sol.step(cfg["dt"], Wm, cfg["theta"])               # warm-up
-    torch.cuda.synchronize()
-    win_state = sol.state() if not args.no_e2e else None
-    rec0 = sol.num_records()
 
     def barrier():
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
 
+    # psi(0) in pinned host memory; every step goes through the public API and
+    # reads its observables record back to the host (end to end, host clock)
+    site, occ, amps = W.start_state(cfg)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    site_p, occ_p = pin(site), pin(occ)
+    amps_p = pin(np.stack([amps.real, amps.imag], 1).reshape(-1))
     stream = sol.stream
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    sol.profile(True)
-    sol.stage_stats(reset=True)
-    with ClockSampler(local) as clk:
-        barrier()
-        e0.record(stream)
-        sol.step(cfg["dt"], K, cfg["theta"])
-        e1.record(stream)
-        barrier()
+    first_timed = start + Wm
+    all_units = 0.0
+    barrier()
+    t_host0 = time.perf_counter()
+    sol.set_state(site_p, occ_p, amps_p[0::2] + 1j * amps_p[1::2])
+    clk = ClockSampler(local)
+    for k in range(end):
+        if k == first_timed:
+            barrier()
+            sol.profile(True)
+            sol.stage_stats(reset=True)
+            clk.__enter__()
+            e0.record(stream)
+        sol.step(cfg["dt"], 1, cfg["theta"])
+        r = sol.observables(sol.num_records() - 1, 1)[0]
+        all_units += r[9] * r[6]
+    e1.record(stream)
+    barrier()
+    t_host = time.perf_counter() - t_host0
+    clk.__exit__(None, None, None)
     sol.profile(False)
     ms = e0.elapsed_time(e1)
     stage_ms, launches, stage_bytes = sol.stage_stats(reset=True)
-    rec = sol.observables(rec0, K)
+    rec = sol.observables(first_timed + 1, K)
     units, tbytes, tflops = taylor_counts(rec, sol)
     t_max = ms
     total_units = units
     if dist is not None:
-        tt = torch.tensor([ms, units], dtype=torch.float64, device="cuda")
+        tt = torch.tensor([ms, units, t_host, all_units], dtype=torch.float64, device="cuda")
         mx = tt.clone()
         dist.all_reduce(mx, op=dist.ReduceOp.MAX)
         dist.all_reduce(tt, op=dist.ReduceOp.SUM)
         t_max, total_units = float(mx[0]), float(tt[1])
+        t_host, all_units = float(mx[2]), float(tt[3])
     value = total_units / (t_max / 1e3)
 
     # roofline of the dominant kernel (the propagator), live CUDA events per launch
@@ -272,44 +295,24 @@ def main():
     frac_hbm = achieved_gbs / peak_gbs
     frac_fp64 = achieved_tf / FP64_PEAK_TFLOPS
     src = os.path.join(ROOT, "paper_2603_07341_gb300", "csrc", "kern_taylor.cu")
-    traffic = traffic_from_profile(src)
+    traffic = traffic_from_profile(src, end)
     if sol_precision(model) == "c128" and frac_fp64 > frac_hbm:
         roof = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s (FP64)",
                 "frac": frac_fp64, "traffic": traffic, "peak_kind": "nominal FP64 (derived)",
                 "hbm_achieved_gbs": achieved_gbs, "hbm_frac": frac_hbm}
     else:
         roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": peak_gbs, "unit": "GB/s",
-                "frac": frac_hbm, "traffic": traffic, "peak_kind": peak_kind + " (copy)",
-                "fp64_achieved_tflops": achieved_tf, "fp64_frac": frac_fp64}
-    roof["kernel"] = "k_taylor (one cooperative launch per time step)"
+                "frac": frac_hbm, "traffic": traffic, "peak_kind": peak_kind + " (copy), sustained"}
+    roof["kernel"] = ("k_taylor_f64" if sol_precision(model) == "c128" else "k_taylor_dw") + \
+        " (one cooperative launch per time step)"
     roof["algorithmic_bytes_per_launch"] = tbytes / K
 
-    # end to end through the public API with host buffers
-    e2e = None
-    if win_state is not None and rank == 0:
-        site, occ, amps = win_state
-        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
-        site_p, occ_p = pin(site), pin(occ)
-        amps_p = pin(np.stack([amps.real, amps.imag], 1).reshape(-1))
-        sol2 = B.Solver(**model)
-        sol2.set_state(*W.start_state(cfg))
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        sol2.load_state(site_p, occ_p, amps_p[0::2] + 1j * amps_p[1::2])
-        nrec = sol2.num_records()
-        out_units = 0.0
-        for k in range(K):
-            sol2.step(cfg["dt"], 1, cfg["theta"])
-            r = sol2.observables(nrec + k, 1)
-            out_units += r[0, 9] * r[0, 6]
-        torch.cuda.synchronize()
-        el = time.perf_counter() - t0
-        bi = site.nbytes + occ.nbytes + 16 * len(amps)
-        e2e = {"value": out_units / el, "unit": UNIT, "h2d_bytes_per_step": bi / K,
-               "d2h_bytes_per_step": sol2.rec_len * 8,
-               "note": "load_state of the window-start state from pinned host arrays, then per step "
-                       "paces_step(1) and a read-back of its observables record"}
-        sol2.close()
+    e2e = {"value": all_units / t_host, "unit": UNIT,
+           "h2d_bytes_per_step": (site.nbytes + occ.nbytes + amps_p.nbytes) / end,
+           "d2h_bytes_per_step": sol.rec_len * 8,
+           "note": "host clock over the whole run from psi(0) in pinned host memory: set_state, then "
+                   "%d x (paces_step(1) + read-back of that step's observables record); units over all "
+                   "%d steps" % (end, end)}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -340,6 +343,7 @@ def main():
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": int(launches[:5].sum()),
+            "wall_s_whole_run": t_host,
             "stages_ms_per_step": {n: float(m / K) for n, m in zip(B.STAGES, stage_ms)},
             "stage_algorithmic_gbs": {n: (float(b / (m / 1e3) / 1e9) if m > 0 else None)
                                       for n, b, m in zip(B.STAGES, stage_bytes, stage_ms)},
