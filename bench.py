@@ -210,7 +210,7 @@ def main():
     ap.add_argument("--workload", default="ring16", choices=sorted(W.CONFIGS))
     ap.add_argument("--end-step", type=int, default=500,
                     help="last timed step (the ring16 trajectory has 1000; 0 = the whole trajectory)")
-    ap.add_argument("--precision", default="dw", choices=["dw", "c128"])
+    ap.add_argument("--precision", default="dw", choices=["dw", "c128", "c64"])
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -235,7 +235,7 @@ def main():
     end = args.end_step or cfg["nsteps"]
     start = max(0, end - K - Wm)
     model = W.model_kwargs(cfg)
-    model["precision"] = {"dw": B.DW, "c128": B.C128}[args.precision]
+    model["precision"] = {"dw": B.DW, "c128": B.C128, "c64": B.C64_SPMV}[args.precision]
     sol = B.Solver(**model)
 
     def barrier():
@@ -303,7 +303,7 @@ def main():
     else:
         roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": peak_gbs, "unit": "GB/s",
                 "frac": frac_hbm, "traffic": traffic, "peak_kind": peak_kind + " (copy), sustained"}
-    roof["kernel"] = ("k_taylor_f64" if sol_precision(model) == "c128" else "k_taylor_dw") + \
+    roof["kernel"] = {"c128": "k_taylor_f64", "dw": "k_taylor_dw", "c64": "k_taylor_c64"}[sol_precision(model)] + \
         " (one cooperative launch per time step)"
     roof["algorithmic_bytes_per_launch"] = tbytes / K
 
@@ -329,10 +329,8 @@ def main():
             "dtype": {"dw": "f32x2 (double-word FP32, 48-bit significand)", "c128": "f64",
                       "c64": "f32 terms, f32x2 accumulator"}[sol_precision(model)],
             "data": "synthetic",
-            "config": {"workload": "%s: 1D Holstein ring N=16 K=8 J=1 omega=1 g=1.5 dt=0.02 theta=1e-7, "
-                                   "timed steps %d..%d of %d" % (args.workload, start + Wm + 1, start + Wm + K,
-                                                                  cfg["nsteps"])
-                       if args.workload == "ring16" else args.workload,
+            "config": {"workload": "%s: %s, timed steps %d..%d of %d" % (
+                           args.workload, W.describe(cfg), start + Wm + 1, start + Wm + K, cfg["nsteps"]),
                        "rows_mean": float(np.mean(q)), "rows_max": float(np.max(q)),
                        "nnz_mean": float(np.mean(rec[:, 8])), "terms_mean": float(np.mean(rec[:, 9])),
                        "parallelism": "replicas" if ws > 1 else "single GPU",

@@ -109,7 +109,25 @@ typedef struct {
     double taylor_tol;          /* stop at n >= 2 with ||phi_n|| <= tol ||r||; 0 = 1e-15 */
     int32_t taylor_nmax;        /* series terms allowed before NOCONVERGE; 0 = 200      */
     uint64_t max_rows;          /* initial row capacity hint; 0 = automatic (it grows)  */
+    int32_t batch;              /* realisations R of a static-disorder ensemble (0 or 1 */
+                                /* = one model); for R > 1 eps holds R*N site energies, */
+                                /* realisation r in eps[r*N .. r*N + N)                 */
+    int32_t reserved0;
 } paces_params;
+
+/* Ensembles (batch = R > 1).  The R realisations share every parameter except
+ * the site energies.  They are evolved together as one block-diagonal problem:
+ * the realisation index r is one more digit of every basis key, which no move
+ * changes, so one H_eff, one hash table and one launch of every stage serve all
+ * realisations, whatever their subspace sizes.  paces_set_state replicates
+ * psi(0) into every realisation; paces_get_state and paces_load_state carry r
+ * as an extra last column of occ (N + 1 columns).  Rows of one realisation
+ * appear in the same relative order as in a run of that realisation alone.
+ * The Taylor series stops on the norms of the whole ensemble.  Observables
+ * records then hold, after the fixed fields, P_s for every (r, s), <n_j> for
+ * every (r, j) and C_r(t) (re, im) for every r; the fixed C field is the mean
+ * over r.  Limit: R <= PACES_MAX_BATCH. */
+#define PACES_MAX_BATCH 4096
 
 /* Basis-key layout (App. A, generalised to mixed radix): a state (s, n_0..n_{N-1})
  * is the integer  s + N_s * sum_j n_j R_j  split over `words` 64-bit words; no
@@ -127,6 +145,10 @@ typedef struct {
     int32_t site_word[PACES_MAX_SITES];
     uint64_t site_stride[PACES_MAX_SITES];
     uint64_t site_radix[PACES_MAX_SITES];
+    int32_t batch_word;         /* ensembles: word, place value and radix of the   */
+    int32_t reserved1;          /* realisation digit (radix 1 for a single model)  */
+    uint64_t batch_stride;
+    uint64_t batch_radix;
 } paces_layout;
 
 /* Host-only: plan the key layout of a model.  No GPU is touched.
@@ -135,7 +157,8 @@ typedef struct {
 paces_status paces_plan_layout(const paces_params* params, paces_layout* out);
 
 /* Host-only: encode n states given in A form (App. A: site[n], occ[n*N]) into
- * keys[n*words] (word 0 first).  Returns INVALID if a digit is out of range. */
+ * keys[n*words] (word 0 first), in realisation 0 of an ensemble.  Returns
+ * INVALID if a digit is out of range. */
 paces_status paces_encode_keys(const paces_layout* layout, int64_t n, const int32_t* site,
                                const int32_t* occ, uint64_t* keys);
 
@@ -209,7 +232,7 @@ paces_status paces_get_hamiltonian(paces_t h, int32_t* cnt, int32_t* cols, doubl
 /* Observables, one record per time index (0 = psi(0), k = after step k).
  * Each record has paces_record_len() doubles: the fields below, then the site
  * populations P_s (N values; Eq. RMSD uses them) and the mean phonon numbers
- * <n_j> (N values). */
+ * <n_j> (N values); for ensembles see PACES_MAX_BATCH above. */
 #define PACES_OBS_TIME 0         /* t                                           */
 #define PACES_OBS_NORM 1         /* ||c||^2 after the step                      */
 #define PACES_OBS_NORM_PHI0 2    /* ||c'||^2 entering the propagator            */

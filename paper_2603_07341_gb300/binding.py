@@ -39,13 +39,16 @@ class Params(C.Structure):
                 ("eps", C.POINTER(C.c_double)), ("omega", C.POINTER(C.c_double)),
                 ("g", C.POINTER(C.c_double)), ("phonon_cap", C.POINTER(C.c_int32)), ("m", C.c_int32),
                 ("m_init", C.c_int32), ("precision", C.c_int32), ("fixed_terms", C.c_int32),
-                ("taylor_tol", C.c_double), ("taylor_nmax", C.c_int32), ("max_rows", C.c_uint64)]
+                ("taylor_tol", C.c_double), ("taylor_nmax", C.c_int32), ("max_rows", C.c_uint64),
+                ("batch", C.c_int32), ("reserved0", C.c_int32)]
 
 
 class Layout(C.Structure):
     _fields_ = [("n_sites", C.c_int32), ("words", C.c_int32), ("pow2", C.c_int32), ("reserved", C.c_int32),
                 ("exciton_radix", C.c_uint64), ("site_word", C.c_int32 * MAX_SITES),
-                ("site_stride", C.c_uint64 * MAX_SITES), ("site_radix", C.c_uint64 * MAX_SITES)]
+                ("site_stride", C.c_uint64 * MAX_SITES), ("site_radix", C.c_uint64 * MAX_SITES),
+                ("batch_word", C.c_int32), ("reserved1", C.c_int32), ("batch_stride", C.c_uint64),
+                ("batch_radix", C.c_uint64)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
@@ -132,12 +135,16 @@ def _ip(a):
 
 def make_params(n_sites, lattice_kind=RING, dims=(0, 0, 0), coupling_kind=NEAREST, J=1.0, eps=None,
                 omega=None, g=None, cap=None, m=2, m_init=10, precision=DW, fixed_terms=0, tol=0.0,
-                nmax=0, max_rows=0, J_explicit=None):
-    """Build a Params struct; returns (struct, keepalive arrays)."""
+                nmax=0, max_rows=0, J_explicit=None, batch=1):
+    """Build a Params struct; returns (struct, keepalive arrays).  For an
+    ensemble (batch R > 1) eps is [R, N] (or broadcastable to it)."""
     N = int(n_sites)
+    R = max(1, int(batch))
     vec = lambda v: np.ascontiguousarray(np.broadcast_to(np.asarray(0.0 if v is None else v,
                                                                     dtype=np.float64), (N,)))
-    keep = dict(eps=vec(eps), omega=vec(omega), g=vec(g),
+    epsv = np.ascontiguousarray(np.broadcast_to(np.asarray(0.0 if eps is None else eps, dtype=np.float64),
+                                                (R, N)).reshape(-1)) if R > 1 else vec(eps)
+    keep = dict(eps=epsv, omega=vec(omega), g=vec(g),
                 cap=np.ascontiguousarray(np.broadcast_to(np.asarray(4 if cap is None else cap,
                                                                     dtype=np.int32), (N,))))
     if J_explicit is not None:
@@ -155,6 +162,7 @@ def make_params(n_sites, lattice_kind=RING, dims=(0, 0, 0), coupling_kind=NEARES
     p.phonon_cap = _ip(keep["cap"])
     p.m, p.m_init, p.precision, p.fixed_terms = int(m), int(m_init), int(precision), int(fixed_terms)
     p.taylor_tol, p.taylor_nmax, p.max_rows = float(tol), int(nmax), int(max_rows)
+    p.batch = R
     return p, keep
 
 
@@ -235,6 +243,8 @@ class Solver:
             raise RuntimeError("paces needs a CUDA device")
         self._lib = load()
         self.N = int(model["n_sites"])
+        self.batch = max(1, int(model.get("batch", 1)))
+        self.ncols = self.N + (1 if self.batch > 1 else 0)
         self._params, self._keep = make_params(**model)
         self.device = torch.cuda.current_device()
         self.stream = stream if stream is not None else torch.cuda.current_stream()
@@ -278,7 +288,7 @@ class Solver:
         self._check(self._lib.paces_set_state(self._h, len(s), _ip(s), _ip(o), _dp(a)), "set_state")
 
     def load_state(self, site, occ, amps):
-        s, o, a = self._state_args(self.N, site, occ, amps)
+        s, o, a = self._state_args(self.ncols, site, occ, amps)
         self._check(self._lib.paces_load_state(self._h, len(s), _ip(s), _ip(o), _dp(a)), "load_state")
 
     def step(self, dt, nsteps=1, theta=0.0):
@@ -292,7 +302,7 @@ class Solver:
     def state(self):
         q = self.num_rows()
         site = np.zeros(q, dtype=np.int32)
-        occ = np.zeros((q, self.N), dtype=np.int32)
+        occ = np.zeros((q, self.ncols), dtype=np.int32)
         amps = np.zeros(2 * q)
         self._check(self._lib.paces_get_state(self._h, q, _ip(site), _ip(occ), _dp(amps)), "get_state")
         return site, occ, amps[0::2] + 1j * amps[1::2]
@@ -353,10 +363,19 @@ class Solver:
         return ms, launches, by
 
 
-def records_dict(rec, N):
-    """Split observables records into named columns, P[:, N] and nbar[:, N]."""
+def records_dict(rec, N, batch=1):
+    """Split observables records into named columns: P[:, N] and nbar[:, N], or
+    for an ensemble P[:, R, N], nbar[:, R, N] and C_r[:, R]."""
     d = {name: rec[:, i] for i, name in enumerate(OBS_FIELDS)}
     d["C"] = rec[:, 4] + 1j * rec[:, 5]
-    d["P"] = rec[:, OBS_FIXED:OBS_FIXED + N]
-    d["nbar"] = rec[:, OBS_FIXED + N:OBS_FIXED + 2 * N]
+    R = max(1, int(batch))
+    if R == 1:
+        d["P"] = rec[:, OBS_FIXED:OBS_FIXED + N]
+        d["nbar"] = rec[:, OBS_FIXED + N:OBS_FIXED + 2 * N]
+        return d
+    o = OBS_FIXED
+    d["P"] = rec[:, o:o + R * N].reshape(-1, R, N)
+    d["nbar"] = rec[:, o + R * N:o + 2 * R * N].reshape(-1, R, N)
+    c = rec[:, o + 2 * R * N:o + 2 * R * N + 2 * R].reshape(-1, R, 2)
+    d["C_r"] = c[:, :, 0] + 1j * c[:, :, 1]
     return d

@@ -194,6 +194,12 @@ struct DevModel {
     dwf eps_dw[kMaxSites];
     dwf omega_dw[kMaxSites];
     int uniform_omega;         // all omega_j equal (diagonal = eps_s + omega sum_j n_j)
+    int batch;                 // realisations R of an ensemble (1: one model)
+    int batch_word;            // realisation digit: word, place value, radix
+    UDiv div_batch_stride;
+    UDiv div_batch_radix;
+    const double* eps_b64;     // ensembles: eps[r * N + s] (FP64), device memory
+    const dwf* eps_bdw;        // ensembles: eps[r * N + s] (double-word)
     int fmt;                   // amplitude storage: 0 double-word, 1 FP64
     int ncoef_pad;
     int adj_off[kMaxSites + 1];  // hops of site s: adj[adj_off[s] .. adj_off[s+1]) ascending t
@@ -280,6 +286,16 @@ __device__ __forceinline__ int key_digit(const Key<W>& k, const DevModel* M, int
     uint64_t q = udiv(x, M->div_stride[j]);
     uint64_t q2 = udiv(q, M->div_radix[j]);
     return (int)(q - q2 * M->div_radix[j].d);
+}
+
+// Realisation index of a key (0 for a single model).
+template <int W>
+__device__ __forceinline__ int key_real(const Key<W>& k, const DevModel* M)
+{
+    if (M->batch <= 1) return 0;
+    uint64_t q = udiv(k.w[M->batch_word], M->div_batch_stride);
+    uint64_t q2 = udiv(q, M->div_batch_radix);
+    return (int)(q - q2 * M->div_batch_radix.d);
 }
 
 // Per-row descriptor kept beside the key so that moves need no digit

@@ -340,12 +340,19 @@ struct DiagAcc {
 template <int W>
 __device__ __forceinline__ DiagAcc row_diag(const DevModel* __restrict__ M, const Key<W>& k, int s, int nph)
 {
+    double e64 = M->eps[s];
+    dwf edw = M->eps_dw[s];
+    if (M->batch > 1) {                         // site energies of this key's realisation
+        int rz = key_real<W>(k, M);
+        e64 = M->eps_b64[rz * M->N + s];
+        edw = M->eps_bdw[rz * M->N + s];
+    }
     if (M->fmt == 0 && M->uniform_omega) {    // eps_s + omega N_ph, no digits needed
-        DiagAcc r{0.0, dw_add(M->eps_dw[s], dw_mul_f(M->omega_dw[0], (float)nph))};
+        DiagAcc r{0.0, dw_add(edw, dw_mul_f(M->omega_dw[0], (float)nph))};
         return r;
     }
     uint64_t q0 = udiv(k.w[0], M->div_exc);
-    DiagAcc r{M->eps[s], M->eps_dw[s]};
+    DiagAcc r{e64, edw};
     const bool f64 = M->fmt == 1;
     nph = 0;
 #pragma unroll
@@ -596,6 +603,142 @@ __global__ void __launch_bounds__(kBlock) k_obs_accum(const DevModel* __restrict
     }
 }
 
+// Ensembles: the same integer sums per (realisation, site), accumulated in
+// shared memory when the R x 2N table fits there, else in global memory.
+template <int W>
+__global__ void __launch_bounds__(kBlock) k_obs_accum_batch(const DevModel* __restrict__ M, Counters* ctr,
+                                                            const uint64_t* __restrict__ keys,
+                                                            const uint32_t* __restrict__ meta,
+                                                            const double2* __restrict__ vec,
+                                                            unsigned long long* __restrict__ acc, int use_shared)
+{
+    extern __shared__ unsigned long long shb[];
+    if (ctr->err) return;
+    const int N = M->N, R = M->batch, L = 2 * R * N + 1;
+    if (use_shared) {
+        for (int t = threadIdx.x; t < 2 * L; t += blockDim.x) shb[t] = 0ull;
+        __syncthreads();
+    }
+    unsigned long long* dst = use_shared ? shb : acc;
+    const int fmt = M->fmt;
+    const uint32_t q = ctr->q;
+    unsigned long long nh = 0, nl = 0;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < q; i += gridDim.x * blockDim.x) {
+        unsigned long long hi = 0, lo = 0;
+        if (fmt == 1) {
+            double2 v = vec[i];
+            double w = v.x * v.x + v.y * v.y;
+            if (w == 0.0) continue;
+            split_weight(w, hi, lo);
+        } else {
+            dwf w = dw_norm2(reinterpret_cast<const float4*>(vec)[i]);
+            if (w.hi == 0.0f) continue;
+            __int128 F = fix84(w.hi) + fix84(w.lo);
+            if (F <= 0) continue;
+            hi = (unsigned long long)(F >> 32);
+            lo = (unsigned long long)(F & 0xFFFFFFFF);
+        }
+        Key<W> k = load_key<W>(keys, i);
+        int rz = key_real<W>(k, M), s = meta_s(meta[i]);
+        atomicAdd(&dst[2 * (rz * N + s)], hi);
+        atomicAdd(&dst[2 * (rz * N + s) + 1], lo);
+        nh += hi;
+        nl += lo;
+        uint64_t q0 = udiv(k.w[0], M->div_exc);
+#pragma unroll
+        for (int wd = 0; wd < W; ++wd) {
+            uint64_t x = (wd == 0) ? q0 : k.w[wd];
+            for (int j = M->word_first[wd]; j < M->word_first[wd + 1]; ++j) {
+                uint64_t xq = udiv(x, M->div_radix[j]);
+                unsigned long long nj = x - xq * M->div_radix[j].d;
+                x = xq;
+                if (nj) {
+                    atomicAdd(&dst[2 * (R * N + rz * N + j)], hi * nj);
+                    atomicAdd(&dst[2 * (R * N + rz * N + j) + 1], lo * nj);
+                }
+            }
+        }
+    }
+    nh = warp_sum_u64(nh);
+    nl = warp_sum_u64(nl);
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&dst[2 * (L - 1)], nh);
+        atomicAdd(&dst[2 * (L - 1) + 1], nl);
+    }
+    if (use_shared) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < 2 * L; t += blockDim.x)
+            if (shb[t]) atomicAdd(&acc[t], shb[t]);
+    }
+}
+
+template <int W>
+__global__ void __launch_bounds__(kBlock) k_obs_finish_batch(const DevModel* __restrict__ M, Counters* ctr,
+                                                             const uint64_t* __restrict__ table, uint64_t slots,
+                                                             const uint64_t* __restrict__ psi0_keys,
+                                                             const double2* __restrict__ psi0_amp, int64_t n0,
+                                                             const double2* __restrict__ vec, double t, int mode,
+                                                             unsigned long long* __restrict__ acc,
+                                                             double* __restrict__ rec)
+{
+    if (ctr->err) return;
+    const int N = M->N, R = M->batch, L = 2 * R * N + 1;
+    __shared__ double nrm;
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
+        unsigned long long hi = acc[2 * i], lo = acc[2 * i + 1];
+        acc[2 * i] = acc[2 * i + 1] = 0ull;
+        hi += lo >> 32;
+        lo &= 0xFFFFFFFFull;
+        double v = (double)hi * 2.220446049250313e-16 + (double)lo * 5.169878828456423e-26;
+        if (i < L - 1) rec[PACES_OBS_FIXED + i] = v;
+        else nrm = v;
+    }
+    // C_r(t) = <psi0|psi(t)> restricted to realisation r (psi(0) is replicated in blocks of n0/R)
+    const int64_t per = n0 / R;
+    double csum[2] = {0.0, 0.0};
+    for (int rz = threadIdx.x; rz < R; rz += blockDim.x) {
+        double cr = 0.0, ci = 0.0;
+        for (int64_t k = (int64_t)rz * per; k < (int64_t)(rz + 1) * per; ++k) {
+            Key<W> key = load_key<W>(psi0_keys, (uint64_t)k);
+            int64_t r = table_lookup<W>(table, slots, key);
+            if (r < 0) continue;
+            double2 a = psi0_amp[k], c;
+            if (M->fmt == 1) {
+                c = vec[r];
+            } else {
+                float4 v = reinterpret_cast<const float4*>(vec)[r];
+                c = make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+            }
+            cr += a.x * c.x + a.y * c.y;
+            ci += a.x * c.y - a.y * c.x;
+        }
+        rec[PACES_OBS_FIXED + 2 * R * N + 2 * rz] = cr;
+        rec[PACES_OBS_FIXED + 2 * R * N + 2 * rz + 1] = ci;
+        csum[0] += cr;
+        csum[1] += ci;
+    }
+    __shared__ double cs[2];
+    block_sum<kBlock, 2>(csum, cs);
+    if (threadIdx.x == 0) {
+        bool initial = mode == 1;
+        if (mode == 2) ctr->kept = ctr->q;
+        double norm = nrm;
+        rec[PACES_OBS_TIME] = t;
+        rec[PACES_OBS_NORM] = norm;
+        rec[PACES_OBS_NORM_PHI0] = initial ? norm : ctr->norm_phi0;
+        rec[PACES_OBS_ENERGY] = initial ? 0.0 : ctr->energy;
+        rec[PACES_OBS_C_RE] = cs[0] / R;
+        rec[PACES_OBS_C_IM] = cs[1] / R;
+        rec[PACES_OBS_ROWS] = (double)ctr->q;
+        rec[PACES_OBS_KEPT] = (double)ctr->kept;
+        rec[PACES_OBS_NNZ] = initial ? 0.0 : (double)(ctr->nnz + ctr->q);
+        rec[PACES_OBS_TERMS] = initial ? 0.0 : (double)ctr->nterms;
+        rec[PACES_OBS_NORM_BEFORE] = initial ? norm : ctr->norm_last;
+        ctr->norm_last = norm;
+        ctr->nnz = 0;
+    }
+}
+
 // mode: 0 after a step, 1 the record of set_state, 2 after the first step
 template <int W>
 __global__ void __launch_bounds__(kBlock) k_obs_finish(const DevModel* __restrict__ M, Counters* ctr,
@@ -684,7 +827,7 @@ template <int W>
 __global__ void k_decode(const DevModel* __restrict__ M, const uint64_t* __restrict__ keys, uint32_t n,
                          int32_t* __restrict__ site, int32_t* __restrict__ occ)
 {
-    int N = M->N;
+    const int N = M->N, C = N + (M->batch > 1 ? 1 : 0);
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         Key<W> k = load_key<W>(keys, i);
         uint64_t q0 = udiv(k.w[0], M->div_exc);
@@ -693,10 +836,11 @@ __global__ void k_decode(const DevModel* __restrict__ M, const uint64_t* __restr
             uint64_t x = (w == 0) ? q0 : k.w[w];
             for (int j = M->word_first[w]; j < M->word_first[w + 1]; ++j) {
                 uint64_t xq = udiv(x, M->div_radix[j]);
-                occ[(uint64_t)i * N + j] = (int32_t)(x - xq * M->div_radix[j].d);
+                occ[(uint64_t)i * C + j] = (int32_t)(x - xq * M->div_radix[j].d);
                 x = xq;
             }
         }
+        if (C > N) occ[(uint64_t)i * C + N] = key_real<W>(k, M);
     }
 }
 
@@ -760,6 +904,17 @@ template <int W>
 static int observe_w(const Bufs& b, int gen, const double2* vec, double t, int64_t rec, int mode, cudaStream_t st)
 {
     double* r = b.obs + rec * b.rec_len;
+    if (b.batch > 1) {
+        size_t shm = sizeof(unsigned long long) * 2 * (size_t)(2 * b.batch * b.N + 1);
+        int use_shared = shm <= 200 * 1024;
+        if (use_shared)
+            cudaFuncSetAttribute(k_obs_accum_batch<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+        k_obs_accum_batch<W><<<b.G, kBlock, use_shared ? shm : 0, st>>>(b.model, b.ctr, b.keys[gen], b.meta[gen], vec,
+                                                                        b.obs_part, use_shared);
+        k_obs_finish_batch<W><<<1, kBlock, 0, st>>>(b.model, b.ctr, b.table[gen], b.table_slots, b.psi0_keys,
+                                                    b.psi0_amp, b.n0, vec, t, mode, b.obs_part, r);
+        return 2;
+    }
     k_obs_accum<W><<<b.G, kBlock, 0, st>>>(b.model, b.ctr, b.keys[gen], vec, b.obs_part);
     k_obs_finish<W><<<1, kBlock, 0, st>>>(b.model, b.ctr, b.table[gen], b.table_slots, b.psi0_keys, b.psi0_amp,
                                           b.n0, vec, t, mode, b.obs_part, r);

@@ -439,13 +439,187 @@ __global__ void __launch_bounds__(kBlock) k_taylor_dw(TaylorArgs a)
     }
 }
 
+// ---------------------------------------------------------------- complex64 terms
+// PACES_C64_SPMV: terms n <= kDwTerms as in k_taylor_dw; from term kDwTerms + 1 on,
+// the SpMV runs in plain complex64 (FP32 products and sums, coefficients
+// rounded to FP32), phi_n is stored as float2 and added into the double-word
+// accumulator r with an error-free sum.  The first terms carry most of the
+// weight (||phi_1|| ~ dt ||H||), so keeping them double-word bounds the error.
+constexpr int kDwTerms = 2;
+
+// double-word + float (Joldes et al., DWPlusFP, Alg. 4)
+__device__ __forceinline__ dwf dw_add_f(dwf x, float y)
+{
+    dwf s = two_sum(x.hi, y);
+    float v = __fadd_rn(x.lo, s.lo);
+    return fast_two_sum(s.hi, v);
+}
+
+template <int LPR>
+__device__ __forceinline__ float2 row_apply_f32(const uint32_t* __restrict__ col, const uint8_t* __restrict__ cid,
+                                                uint32_t c, uint64_t base, const float* coef,
+                                                const float2* __restrict__ x, int lane)
+{
+    float yr = 0.f, yi = 0.f;
+    if constexpr (LPR == 1) {
+        for (uint32_t e = 0; e < c; e += 4) {
+            uint4 cc = *reinterpret_cast<const uint4*>(col + base + e);
+            uint32_t ii = *reinterpret_cast<const uint32_t*>(cid + base + e);
+            uint32_t cs[4] = {cc.x, cc.y, cc.z, cc.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (e + k < c) {
+                    float a = coef[(ii >> (8 * k)) & 0xFFu];
+                    float2 xv = x[cs[k]];
+                    yr = __fmaf_rn(a, xv.x, yr);
+                    yi = __fmaf_rn(a, xv.y, yi);
+                }
+            }
+        }
+    } else {
+        for (uint32_t e = lane; e < c; e += LPR) {
+            float a = coef[cid[base + e]];
+            float2 xv = x[col[base + e]];
+            yr = __fmaf_rn(a, xv.x, yr);
+            yi = __fmaf_rn(a, xv.y, yi);
+        }
+#pragma unroll
+        for (int o = LPR / 2; o > 0; o >>= 1) {
+            yr += __shfl_xor_sync(0xffffffffu, yr, o, LPR);
+            yi += __shfl_xor_sync(0xffffffffu, yi, o, LPR);
+        }
+    }
+    return make_float2(yr, yi);
+}
+
+template <int LPR>
+__global__ void __launch_bounds__(kBlock) k_taylor_c64(TaylorArgs a)
+{
+    __shared__ dwf coef[kMaxCoefs];
+    __shared__ float coef32[kMaxCoefs];
+    __shared__ float tsh[8];
+    Counters* ctr = a.ctr;
+    if (ctr->err) return;
+    const DevModel* M = a.M;
+    const int ncoef = M->ncoef;
+    const uint32_t q = ctr->q;
+    const uint64_t P = (uint64_t)M->P;
+    const unsigned G = gridDim.x;
+    constexpr uint32_t RPW = 32 / LPR;
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (G * blockDim.x) >> 5;
+    const int lane = (threadIdx.x & 31) % LPR;
+    const uint32_t sub = (threadIdx.x & 31) / LPR;
+    const float4* X = reinterpret_cast<const float4*>(a.c_in);
+    float4* Y = reinterpret_cast<float4*>(a.ta);
+    float4* Y2 = reinterpret_cast<float4*>(a.tb);
+    float4* R = reinterpret_cast<float4*>(a.r);
+    float2* F[2] = {a.fa, a.fb};
+    const float2* DG = reinterpret_cast<const float2*>(a.diag);
+    const float kScale = 4294967296.0f;
+
+    const int fixed = a.p.fixed_terms;
+    const int nlimit = fixed > 0 ? fixed : a.p.nmax;
+    const float tol2 = (float)a.p.tol2;
+    dwf E{0.f, 0.f}, N0{0.f, 0.f};
+    int nd = 0;
+    bool conv = false;
+    for (int n = 1; n <= nlimit; ++n) {
+        const double s = a.p.dt / (double)n;
+        const dwf sdw = dw_from_double(s);
+        const float s32 = (float)s;
+        const bool dw_term = n <= kDwTerms;
+        __syncthreads();
+        for (int t = threadIdx.x; t < ncoef; t += blockDim.x) {
+            coef[t] = dw_from_double(s * M->coef[t]);
+            coef32[t] = (float)(s * M->coef[t]);
+        }
+        __syncthreads();
+        const float4* Xd = (n == 1) ? X : (n == 2 ? Y : nullptr);        // double-word input
+        float4* Yd = (n == 1) ? Y : Y2;                                  // double-word output
+        const float2* Xf = F[(n + 1) & 1];                               // complex64 input (n >= 3)
+        float2* Yf = F[n & 1];                                           // complex64 output
+        Red8 acc{0.f, 0.f, {0.f, 0.f}, {0.f, 0.f}};
+        for (uint32_t rb = warp * RPW; rb < q; rb += nwarps * RPW) {
+            uint32_t row = rb + sub;
+            bool valid = row < q;
+            uint32_t c = valid ? a.cnt[row] : 0u;
+            uint64_t base = (uint64_t)row * P;
+            float4 phi;
+            if (dw_term) {
+                Dot2 re{0.f, 0.f}, im{0.f, 0.f};
+                row_apply_dw<LPR>(a.col, a.cid, c, base, coef, Xd, lane, re, im);
+                if (!(valid && lane == 0)) continue;
+                float4 xi = Xd[row];
+                float2 d = DG[row];
+                dwf ds = dw_mul(dwf{d.x, d.y}, sdw);
+                dot2_mac(re, ds, xi.x, xi.y);
+                dot2_mac(im, ds, xi.z, xi.w);
+                dwf yre = dot2_result(re), yim = dot2_result(im);
+                phi = make_float4(yim.hi, yim.lo, -yre.hi, -yre.lo);
+                if (n < kDwTerms) Yd[row] = phi;
+                else Yf[row] = make_float2(phi.x + phi.y, phi.z + phi.w);   // next input, rounded
+                if (n == 1) {
+                    acc.e = dw_add(acc.e, dw_add(dw_mul(dwf{xi.x, xi.y}, yre), dw_mul(dwf{xi.z, xi.w}, yim)));
+                    acc.n0 = dw_add(acc.n0, dw_norm2(xi));
+                }
+            } else {
+                float2 y = row_apply_f32<LPR>(a.col, a.cid, c, base, coef32, Xf, lane);
+                if (!(valid && lane == 0)) continue;
+                float2 xi = Xf[row];
+                float2 d = DG[row];
+                float ds = __fmul_rn(d.x + d.y, s32);
+                y.x = __fmaf_rn(ds, xi.x, y.x);
+                y.y = __fmaf_rn(ds, xi.y, y.y);
+                Yf[row] = make_float2(y.y, -y.x);
+                phi = make_float4(y.y, 0.f, -y.x, 0.f);
+            }
+            float4 rr = (n == 1) ? X[row] : R[row];
+            dwf r_re = dw_term ? dw_add(dwf{rr.x, rr.y}, dwf{phi.x, phi.y}) : dw_add_f(dwf{rr.x, rr.y}, phi.x);
+            dwf r_im = dw_term ? dw_add(dwf{rr.z, rr.w}, dwf{phi.z, phi.w}) : dw_add_f(dwf{rr.z, rr.w}, phi.z);
+            R[row] = make_float4(r_re.hi, r_re.lo, r_im.hi, r_im.lo);
+            float p0 = phi.x * kScale, p1 = phi.z * kScale, q0 = r_re.hi * kScale, q1 = r_im.hi * kScale;
+            acc.phi2 = __fmaf_rn(p0, p0, __fmaf_rn(p1, p1, acc.phi2));
+            acc.r2 = __fmaf_rn(q0, q0, __fmaf_rn(q1, q1, acc.r2));
+        }
+        float* part = reinterpret_cast<float*>(a.partials) + (size_t)(n & 1) * G * 8;
+        float* tot = reinterpret_cast<float*>(a.totals) + (n & 1) * 8;
+        acc = red8_block(acc);
+        if (threadIdx.x == 0) red8_store(part + 8 * blockIdx.x, acc);
+        if (!barrier_reduce8(ctr, part, tot, G)) return;
+        if (threadIdx.x < 6) tsh[threadIdx.x] = __ldcg(tot + threadIdx.x);
+        __syncthreads();
+        nd = n;
+        if (n == 1) {
+            E = dwf{tsh[2], tsh[3]};
+            N0 = dwf{tsh[4], tsh[5]};
+        }
+        if (fixed <= 0 && n >= 2 && tsh[0] <= tol2 * tsh[1]) {
+            conv = true;
+            break;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctr->nterms = nd;
+        ctr->norm_phi0 = (double)N0.hi + (double)N0.lo;
+        ctr->energy = ((double)E.hi + (double)E.lo) / a.p.dt;
+        ctr->norm_r = 0.0;
+        if (!conv && fixed <= 0 && atomicCAS(&ctr->err, 0, (int)kErrNoConverge) == 0) {
+            ctr->err_step = a.p.step;
+            ctr->err_info = nd;
+        }
+    }
+}
+
 template <int LPR>
 static int occupancy()
 {
-    int n1 = 0, n2 = 0;
+    int n1 = 0, n2 = 0, n3 = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n1, k_taylor_f64<LPR>, kBlock, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n2, k_taylor_dw<LPR>, kBlock, 0);
-    return n1 < n2 ? n1 : n2;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n3, k_taylor_c64<LPR>, kBlock, 0);
+    int n = n1 < n2 ? n1 : n2;
+    return n < n3 ? n : n3;
 }
 
 int taylor_blocks_per_sm(int lpr, int c64)
@@ -479,6 +653,9 @@ int launch_taylor(const Bufs& b, const TaylorParams& p, cudaStream_t st)
     if (p.fmt == 1)
         fn = p.lpr == 1 ? (const void*)k_taylor_f64<1> : p.lpr == 4 ? (const void*)k_taylor_f64<4>
                                                                     : (const void*)k_taylor_f64<8>;
+    else if (p.c64)
+        fn = p.lpr == 1 ? (const void*)k_taylor_c64<1> : p.lpr == 4 ? (const void*)k_taylor_c64<4>
+                                                                    : (const void*)k_taylor_c64<8>;
     else
         fn = p.lpr == 1 ? (const void*)k_taylor_dw<1> : p.lpr == 4 ? (const void*)k_taylor_dw<4>
                                                                    : (const void*)k_taylor_dw<8>;

@@ -61,7 +61,7 @@ struct paces_handle {
     std::vector<int32_t> cap;
     paces_layout lay;
     DevModel* hmodel = nullptr;   // host copy
-    int W = 1, D = 4, P = 4, N = 1, lpr = 1;
+    int W = 1, D = 4, P = 4, N = 1, lpr = 1, R = 1;
     paces_allocator alloc{};
     bool has_alloc = false;
     cudaStream_t st = nullptr;
@@ -192,6 +192,7 @@ paces_status check_params(const paces_params* p, std::string& why)
         return PACES_ERR_INVALID;
     }
     if (p->taylor_tol < 0 || p->taylor_nmax < 0 || p->fixed_terms < 0) { why = "series limits"; return PACES_ERR_INVALID; }
+    if (p->batch < 0 || p->batch > PACES_MAX_BATCH) { why = "batch out of range"; return PACES_ERR_INVALID; }
     return PACES_OK;
 }
 
@@ -222,6 +223,15 @@ paces_status plan(const paces_params* p, paces_layout* L, std::string& why)
             l.site_radix[j] = r;
             prod *= r;
         }
+        uint64_t rb = (uint64_t)(p->batch > 1 ? p->batch : 1);
+        if (mode == 0) rb = next_pow2(rb);
+        if (prod * rb > lim) {
+            ++w;
+            prod = 1;
+        }
+        l.batch_word = w;
+        l.batch_stride = (uint64_t)prod;
+        l.batch_radix = rb;
         l.words = w + 1;
     }
     *L = cand[0].words <= cand[1].words ? cand[0] : cand[1];
@@ -527,6 +537,10 @@ paces_status paces::fill_model(const paces_params* params, const paces_layout& L
     }
     M->uniform_omega = 1;
     for (int j = 1; j < N; ++j) M->uniform_omega &= (M->omega[j] == M->omega[0]);
+    M->batch = params->batch > 1 ? params->batch : 1;
+    M->batch_word = L.batch_word;
+    M->div_batch_stride = make_udiv(L.batch_stride);
+    M->div_batch_radix = make_udiv(L.batch_radix);
     M->fmt = params->precision == PACES_C128 ? 1 : 0;
     while (w < L.words) M->word_first[++w] = N;
     std::map<std::tuple<double, double, double>, int> ids;
@@ -607,19 +621,20 @@ paces_status paces_create(const paces_params* params, const paces_allocator* all
     paces_layout L;
     paces_status s = plan(params, &L, why);
     if (s) return s;
-    if (params->precision == PACES_C64_SPMV) return PACES_ERR_UNSUPPORTED;
     paces_t h = new paces_handle();
     h->prm = *params;
     int N = params->n_sites;
     h->N = N;
     h->lay = L;
     h->W = L.words;
-    h->eps.assign(N, 0.0);
+    h->R = params->batch > 1 ? params->batch : 1;
+    h->eps.assign((size_t)N * h->R, 0.0);
     h->omega.assign(N, 0.0);
     h->g.assign(N, 0.0);
     h->cap.assign(params->phonon_cap, params->phonon_cap + N);
+    if (params->eps)
+        for (size_t j = 0; j < h->eps.size(); ++j) h->eps[j] = params->eps[j];
     for (int j = 0; j < N; ++j) {
-        if (params->eps) h->eps[j] = params->eps[j];
         if (params->omega) h->omega[j] = params->omega[j];
         if (params->g) h->g[j] = params->g[j];
     }
@@ -658,19 +673,37 @@ paces_status paces_create(const paces_params* params, const paces_allocator* all
     b.P = h->P;
     b.N = N;
     b.fmt = M->fmt;
+    b.batch = h->R;
     b.G = std::min(kMaxChunkBlocks, h->sms * 4);
     b.grid = h->sms * 8;
     int bps = taylor_blocks_per_sm(h->lpr, 0);
     if (bps < 1) bps = 1;
     b.taylor_grid = h->sms * bps;
-    b.rec_len = PACES_OBS_FIXED + 2 * N;
+    b.rec_len = PACES_OBS_FIXED + 2 * N * h->R + (h->R > 1 ? 2 * h->R : 0);
 
     b.model = alloc_track<DevModel>(h, h->fixed_allocs, 1);
     b.ctr = alloc_track<Counters>(h, h->fixed_allocs, 1);
     b.blk_cnt = alloc_track<uint32_t>(h, h->fixed_allocs, kMaxChunkBlocks);
     b.blk_off = alloc_track<uint32_t>(h, h->fixed_allocs, kMaxChunkBlocks);
     b.partials = alloc_track<double>(h, h->fixed_allocs, 8 * (size_t)b.taylor_grid + 16);
-    b.obs_part = alloc_track<unsigned long long>(h, h->fixed_allocs, (size_t)b.grid * (2 * kMaxSites + 1) * 2);
+    b.obs_part = alloc_track<unsigned long long>(h, h->fixed_allocs,
+                                                 std::max<size_t>((size_t)b.grid * (2 * kMaxSites + 1) * 2,
+                                                                  (size_t)(2 * N * h->R + 1) * 2));
+    if (h->R > 1) {      // per-realisation site energies for the diagonal
+        double* e64 = alloc_track<double>(h, h->fixed_allocs, h->eps.size());
+        dwf* edw = alloc_track<dwf>(h, h->fixed_allocs, h->eps.size());
+        if (!e64 || !edw) {
+            paces_destroy(h);
+            return PACES_ERR_CAPACITY;
+        }
+        std::vector<dwf> hd(h->eps.size());
+        for (size_t j = 0; j < hd.size(); ++j) hd[j] = dw_from_double(h->eps[j]);
+        cudaMemcpyAsync(e64, h->eps.data(), h->eps.size() * 8, cudaMemcpyHostToDevice, h->st);
+        cudaMemcpyAsync(edw, hd.data(), hd.size() * sizeof(dwf), cudaMemcpyHostToDevice, h->st);
+        cudaStreamSynchronize(h->st);
+        M->eps_b64 = e64;
+        M->eps_bdw = edw;
+    }
     if (!b.model || !b.ctr || !b.blk_cnt || !b.blk_off || !b.partials || !b.obs_part ||
         cudaMallocHost(&h->hctr, sizeof(Counters)) != cudaSuccess) {
         paces_destroy(h);
@@ -708,32 +741,56 @@ paces_status paces_destroy(paces_t h)
 
 const char* paces_last_error(paces_t h) { return h ? h->err.c_str() : "NULL handle"; }
 
+// Encode n states in A form.  ncols = N: realisation 0 (replicated into every
+// realisation of an ensemble when `replicate`); ncols = N + 1: the last column
+// is the realisation.  Checks ranges and that no state repeats.
 static paces_status encode_state(paces_t h, int64_t n, const int32_t* site, const int32_t* occ,
-                                 std::vector<uint64_t>& keys, std::vector<uint32_t>& meta)
+                                 std::vector<uint64_t>& keys, std::vector<uint32_t>& meta, int ncols,
+                                 bool replicate, std::vector<int64_t>* src = nullptr)
 {
     if (n <= 0 || !site || !occ) return fail(h, PACES_ERR_INVALID, "empty state or NULL arrays");
-    if ((uint64_t)n > kMaxRowsHard) return fail(h, PACES_ERR_INVALID, "too many states");
-    keys.resize((size_t)n * h->W);
-    std::string why;
-    for (int64_t i = 0; i < n; ++i)
-        for (int j = 0; j < h->N; ++j)
-            if (occ[i * h->N + j] > h->cap[j]) return fail(h, PACES_ERR_INVALID, "occupation above the phonon cap");
-    paces_status s = encode(&h->lay, n, site, occ, keys.data(), why);
-    if (s) return fail(h, s, why);
-    meta.resize((size_t)n);
+    const int N = h->N, W = h->W;
+    int64_t copies = replicate ? h->R : 1;
+    if ((uint64_t)n * copies > kMaxRowsHard) return fail(h, PACES_ERR_INVALID, "too many states");
+    std::vector<int32_t> occN((size_t)n * N);
+    std::vector<int32_t> real((size_t)n, 0);
     for (int64_t i = 0; i < n; ++i) {
-        int nph = 0;
-        for (int j = 0; j < h->N; ++j) nph += occ[i * h->N + j];
-        meta[i] = meta_pack(site[i], occ[i * h->N + site[i]], nph);
+        for (int j = 0; j < N; ++j) {
+            int32_t v = occ[i * ncols + j];
+            if (v < 0 || v > h->cap[j]) return fail(h, PACES_ERR_INVALID, "occupation outside [0, phonon cap]");
+            occN[i * N + j] = v;
+        }
+        if (ncols > N) {
+            real[i] = occ[i * ncols + N];
+            if (real[i] < 0 || real[i] >= h->R) return fail(h, PACES_ERR_INVALID, "realisation out of range");
+        }
     }
-    std::vector<int64_t> idx((size_t)n);
-    for (int64_t i = 0; i < n; ++i) idx[i] = i;
-    int W = h->W;
+    std::vector<uint64_t> base((size_t)n * W);
+    std::string why;
+    paces_status s = encode(&h->lay, n, site, occN.data(), base.data(), why);
+    if (s) return fail(h, s, why);
+    keys.resize((size_t)(n * copies) * W);
+    meta.resize((size_t)(n * copies));
+    if (src) src->resize((size_t)(n * copies));
+    for (int64_t c = 0; c < copies; ++c)
+        for (int64_t i = 0; i < n; ++i) {
+            int64_t o = c * n + i;
+            for (int w = 0; w < W; ++w) keys[o * W + w] = base[i * W + w];
+            uint64_t r = (uint64_t)(replicate ? c : real[i]);
+            keys[o * W + h->lay.batch_word] += r * h->lay.batch_stride;
+            int nph = 0;
+            for (int j = 0; j < N; ++j) nph += occN[i * N + j];
+            meta[o] = meta_pack(site[i], occN[i * N + site[i]], nph);
+            if (src) (*src)[o] = i;
+        }
+    int64_t tot = n * copies;
+    std::vector<int64_t> idx((size_t)tot);
+    for (int64_t i = 0; i < tot; ++i) idx[i] = i;
     auto less = [&](int64_t a, int64_t b) {
         return std::lexicographical_compare(&keys[a * W], &keys[a * W] + W, &keys[b * W], &keys[b * W] + W);
     };
     std::sort(idx.begin(), idx.end(), less);
-    for (int64_t i = 1; i < n; ++i)
+    for (int64_t i = 1; i < tot; ++i)
         if (std::equal(&keys[idx[i] * W], &keys[idx[i] * W] + W, &keys[idx[i - 1] * W]))
             return fail(h, PACES_ERR_INVALID, "duplicate basis states");
     return PACES_OK;
@@ -778,7 +835,9 @@ static paces_status upload_rows(paces_t h, int64_t n, const std::vector<uint64_t
     h->hctr->level_off[0] = 0;
     h->hctr->level_off[1] = (uint32_t)n;
     h->hctr->nlevels = 1;
-    CUDA_TRY(h, cudaMemsetAsync(h->b.obs_part, 0, sizeof(unsigned long long) * 2 * (2 * kMaxSites + 1), h->st));
+    CUDA_TRY(h, cudaMemsetAsync(h->b.obs_part, 0,
+                                sizeof(unsigned long long) * 2 * std::max(2 * kMaxSites + 1, 2 * h->N * h->R + 1),
+                                h->st));
     return set_counters(h);
 }
 
@@ -788,8 +847,16 @@ paces_status paces_set_state(paces_t h, int64_t n, const int32_t* site, const in
     if (!amps) return fail(h, PACES_ERR_INVALID, "amps is NULL");
     std::vector<uint64_t> keys;
     std::vector<uint32_t> meta;
-    paces_status s = encode_state(h, n, site, occ, keys, meta);
+    std::vector<int64_t> src;
+    paces_status s = encode_state(h, n, site, occ, keys, meta, h->N, true, &src);
     if (s) return s;
+    std::vector<double> ramps(2 * src.size());
+    for (size_t i = 0; i < src.size(); ++i) {
+        ramps[2 * i] = amps[2 * src[i]];
+        ramps[2 * i + 1] = amps[2 * src[i] + 1];
+    }
+    amps = ramps.data();
+    n = (int64_t)src.size();
     // psi(0) copy for the autocorrelation
     if (n > h->psi0_cap) {
         for (auto it = h->fixed_allocs.begin(); it != h->fixed_allocs.end();) {
@@ -855,7 +922,7 @@ paces_status paces_load_state(paces_t h, int64_t n, const int32_t* site, const i
     if (!amps) return fail(h, PACES_ERR_INVALID, "amps is NULL");
     std::vector<uint64_t> keys;
     std::vector<uint32_t> meta;
-    paces_status s = encode_state(h, n, site, occ, keys, meta);
+    paces_status s = encode_state(h, n, site, occ, keys, meta, h->N + (h->R > 1 ? 1 : 0), false);
     if (s) return s;
     s = upload_rows(h, n, keys, meta, amps, 0);
     if (s) return s;
@@ -995,14 +1062,15 @@ paces_status paces_get_state(paces_t h, int64_t max, int32_t* site, int32_t* occ
     if (q == 0) return PACES_OK;
     if (site || occ) {
         int32_t* ds = (int32_t*)dev_alloc(h, (size_t)q * 4);
-        int32_t* dox = (int32_t*)dev_alloc(h, (size_t)q * h->N * 4);
+        const int ncols = h->N + (h->R > 1 ? 1 : 0);
+        int32_t* dox = (int32_t*)dev_alloc(h, (size_t)q * ncols * 4);
         if (!ds || !dox) return fail(h, PACES_ERR_CAPACITY, "export buffers");
         count(h, Stage::Other, launch_decode(h->b, h->gen, q, ds, dox, h->st));
         if (site) CUDA_TRY(h, cudaMemcpyAsync(site, ds, (size_t)q * 4, cudaMemcpyDeviceToHost, h->st));
-        if (occ) CUDA_TRY(h, cudaMemcpyAsync(occ, dox, (size_t)q * h->N * 4, cudaMemcpyDeviceToHost, h->st));
+        if (occ) CUDA_TRY(h, cudaMemcpyAsync(occ, dox, (size_t)q * ncols * 4, cudaMemcpyDeviceToHost, h->st));
         CUDA_TRY(h, cudaStreamSynchronize(h->st));
         dev_free(h, {ds, (size_t)q * 4});
-        dev_free(h, {dox, (size_t)q * h->N * 4});
+        dev_free(h, {dox, (size_t)q * ncols * 4});
     }
     if (amps) {
         const double2* v = h->fresh ? h->b.V[1] : h->b.V[0];

@@ -42,6 +42,7 @@ struct Bufs {
     uint64_t cand_cap;
     int W, D, P, N;
     int fmt;                        // amplitude storage: 0 double-word, 1 FP64
+    int batch;                      // realisations of an ensemble (1: one model)
     int G;                          // blocks of chunked kernels
     int grid;                       // blocks of grid-stride kernels
     int taylor_grid;                // blocks of the cooperative propagator

@@ -60,6 +60,17 @@ def model_kwargs(cfg, **over):
                 m=int(c["m"]), m_init=int(c["m_init"]))
 
 
+def describe(cfg):
+    """One-line description of a workload."""
+    kinds = {RING: "ring", CHAIN: "open chain", OPEN2D: "open 2D", OPEN3D: "open 3D", EXPLICIT: "explicit"}
+    geo = "x".join(str(d) for d in cfg["dims"] if d > 1) if cfg["lattice_kind"] in (OPEN2D, OPEN3D) \
+        else "N=%d" % cfg["n_sites"]
+    coup = "J0/r^3 all pairs" if cfg["coupling_kind"] == DIPOLAR else "nearest-neighbour"
+    return ("Holstein %s %s, %s J=%g omega=%g g=%g K=%d, dt=%g theta=%g, start %s"
+            % (kinds[cfg["lattice_kind"]], geo, coup, cfg["J"], cfg["omega"], cfg["g"], cfg["cap"],
+               cfg["dt"], cfg["theta"], cfg["start"]))
+
+
 def start_state(cfg):
     """psi(0) in A form: (site[n], occ[n, N], amps[n] complex)."""
     N = cfg["n_sites"]
