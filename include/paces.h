@@ -262,6 +262,24 @@ paces_status paces_profile(paces_t h, int32_t enable);
 paces_status paces_stage_stats(paces_t h, double* ms, int64_t* launches, double* bytes,
                                int32_t reset);
 
+/* Launch shapes and step replay (no counterpart in the paper).  Read the
+ * current values, change some and write them back; the project autotuner
+ * (paper_2603_07341_gb300/autotune.py) picks them by timing steps.  Results do
+ * not depend on them except through the summation order of reductions.
+ * Returns INVALID for out-of-range values. */
+typedef struct {
+    int32_t taylor_lanes_per_row;     /* 1, 4 or 8 lanes per row of P H P in the propagator  */
+    int32_t taylor_blocks_per_sm;     /* cooperative 256-thread blocks per SM, 1..max below   */
+    int32_t grid_blocks_per_sm;       /* blocks per SM of the grid-stride kernels, 1..32      */
+    int32_t chunk_blocks_per_sm;      /* blocks per SM of the scan-based kernels (total <= 1024) */
+    int32_t use_graphs;               /* 1: every step is captured once as a CUDA graph and   */
+                                      /* replayed (not while stage timing is on)              */
+    int32_t max_taylor_blocks_per_sm; /* read only: co-residency limit of the propagator      */
+    int32_t reserved[2];
+} paces_tuning;
+paces_status paces_get_tuning(paces_t h, paces_tuning* out);
+paces_status paces_set_tuning(paces_t h, const paces_tuning* in);
+
 /* ---- Expansion without allocation (no counterpart in the paper) -----------
  * Some callers cannot allocate device memory: hosts whose framework has
  * already reserved all of it in its own pool, real-time loops that must never

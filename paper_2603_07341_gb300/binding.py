@@ -29,7 +29,7 @@ EXPORTED = (
     "paces_set_state", "paces_load_state", "paces_step", "paces_num_rows", "paces_get_state",
     "paces_get_levels", "paces_get_keep", "paces_get_hamiltonian", "paces_record_len",
     "paces_num_records", "paces_observables", "paces_profile", "paces_stage_stats",
-    "paces_expand_noalloc",
+    "paces_expand_noalloc", "paces_get_tuning", "paces_set_tuning",
 )
 
 
@@ -49,6 +49,13 @@ class Layout(C.Structure):
                 ("site_stride", C.c_uint64 * MAX_SITES), ("site_radix", C.c_uint64 * MAX_SITES),
                 ("batch_word", C.c_int32), ("reserved1", C.c_int32), ("batch_stride", C.c_uint64),
                 ("batch_radix", C.c_uint64)]
+
+
+class Tuning(C.Structure):
+    _fields_ = [("taylor_lanes_per_row", C.c_int32), ("taylor_blocks_per_sm", C.c_int32),
+                ("grid_blocks_per_sm", C.c_int32), ("chunk_blocks_per_sm", C.c_int32),
+                ("use_graphs", C.c_int32), ("max_taylor_blocks_per_sm", C.c_int32),
+                ("reserved", C.c_int32 * 2)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
@@ -119,6 +126,10 @@ def load():
     lib.paces_profile.argtypes = [P, C.c_int32]
     lib.paces_stage_stats.restype = S
     lib.paces_stage_stats.argtypes = [P, dp, i64p, dp, C.c_int32]
+    lib.paces_get_tuning.restype = S
+    lib.paces_get_tuning.argtypes = [P, C.POINTER(Tuning)]
+    lib.paces_set_tuning.restype = S
+    lib.paces_set_tuning.argtypes = [P, C.POINTER(Tuning)]
     lib.paces_expand_noalloc.restype = S
     lib.paces_expand_noalloc.argtypes = [C.POINTER(Params), P, C.c_int64, P, C.c_int64, i64p, P]
     _lib = lib
@@ -350,6 +361,20 @@ class Solver:
         out = np.zeros((count, self.rec_len))
         self._check(self._lib.paces_observables(self._h, int(first), int(count), _dp(out)), "observables")
         return out
+
+    def tuning(self):
+        t = Tuning()
+        self._check(self._lib.paces_get_tuning(self._h, C.byref(t)), "get_tuning")
+        return {f: getattr(t, f) for f, _ in Tuning._fields_ if f != "reserved"}
+
+    def set_tuning(self, **kw):
+        t = Tuning()
+        self._check(self._lib.paces_get_tuning(self._h, C.byref(t)), "get_tuning")
+        for k, v in kw.items():
+            if k == "max_taylor_blocks_per_sm":
+                continue
+            setattr(t, k, int(v))
+        self._check(self._lib.paces_set_tuning(self._h, C.byref(t)), "set_tuning")
 
     def profile(self, on=True):
         self._check(self._lib.paces_profile(self._h, 1 if on else 0), "profile")

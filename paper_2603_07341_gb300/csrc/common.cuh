@@ -225,6 +225,8 @@ struct Counters {
     unsigned bar_count, bar_gen;
     int nterms, pad1;
     double norm_r, norm_phi0, energy, norm_last;
+    double time;                     // t of the last record
+    long long rec_index;             // next observables record
 };
 
 // ---------------------------------------------------------------- keys

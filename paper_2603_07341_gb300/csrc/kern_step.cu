@@ -501,6 +501,7 @@ __global__ void __launch_bounds__(kBlock) k_csr(const DevModel* __restrict__ M, 
 // block order): exact to 2^-84 per row, independent of scheduling, and free of
 // the FP64 pipe except for the split itself.
 constexpr int kObsStride = 2 * kMaxSites + 1;
+constexpr size_t kObsSharedMax = 200 * 1024;
 
 __device__ __forceinline__ void split_weight(double w, unsigned long long& hi, unsigned long long& lo)
 {
@@ -677,12 +678,13 @@ __global__ void __launch_bounds__(kBlock) k_obs_finish_batch(const DevModel* __r
                                                              const uint64_t* __restrict__ table, uint64_t slots,
                                                              const uint64_t* __restrict__ psi0_keys,
                                                              const double2* __restrict__ psi0_amp, int64_t n0,
-                                                             const double2* __restrict__ vec, double t, int mode,
+                                                             const double2* __restrict__ vec, double dt, int mode,
                                                              unsigned long long* __restrict__ acc,
-                                                             double* __restrict__ rec)
+                                                             double* __restrict__ obs, int rec_len)
 {
     if (ctr->err) return;
     const int N = M->N, R = M->batch, L = 2 * R * N + 1;
+    double* rec = obs + (size_t)ctr->rec_index * rec_len;
     __shared__ double nrm;
     for (int i = threadIdx.x; i < L; i += blockDim.x) {
         unsigned long long hi = acc[2 * i], lo = acc[2 * i + 1];
@@ -723,6 +725,9 @@ __global__ void __launch_bounds__(kBlock) k_obs_finish_batch(const DevModel* __r
         bool initial = mode == 1;
         if (mode == 2) ctr->kept = ctr->q;
         double norm = nrm;
+        double t = initial ? 0.0 : ctr->time + dt;
+        ctr->time = t;
+        ctr->rec_index += 1;
         rec[PACES_OBS_TIME] = t;
         rec[PACES_OBS_NORM] = norm;
         rec[PACES_OBS_NORM_PHI0] = initial ? norm : ctr->norm_phi0;
@@ -745,12 +750,13 @@ __global__ void __launch_bounds__(kBlock) k_obs_finish(const DevModel* __restric
                                                        const uint64_t* __restrict__ table, uint64_t slots,
                                                        const uint64_t* __restrict__ psi0_keys,
                                                        const double2* __restrict__ psi0_amp, int64_t n0,
-                                                       const double2* __restrict__ vec, double t, int mode,
+                                                       const double2* __restrict__ vec, double dt, int mode,
                                                        unsigned long long* __restrict__ part,
-                                                       double* __restrict__ rec)
+                                                       double* __restrict__ obs, int rec_len)
 {
     if (ctr->err) return;
     const int N = M->N;
+    double* rec = obs + (size_t)ctr->rec_index * rec_len;
     __shared__ double nrm;
     for (int i = threadIdx.x; i < 2 * N + 1; i += blockDim.x) {
         unsigned long long hi = part[2 * i], lo = part[2 * i + 1];
@@ -783,6 +789,9 @@ __global__ void __launch_bounds__(kBlock) k_obs_finish(const DevModel* __restric
         bool initial = mode == 1;
         if (mode == 2) ctr->kept = ctr->q;      // the first step propagates every row
         double norm = nrm;                       // exact fixed-point sum of |c|^2
+        double t = initial ? 0.0 : ctr->time + dt;
+        ctr->time = t;
+        ctr->rec_index += 1;
         rec[PACES_OBS_TIME] = t;
         rec[PACES_OBS_NORM] = norm;
         rec[PACES_OBS_NORM_PHI0] = initial ? norm : ctr->norm_phi0;
@@ -901,24 +910,30 @@ static int csr_w(const Bufs& b, int gen, cudaStream_t st)
 }
 
 template <int W>
-static int observe_w(const Bufs& b, int gen, const double2* vec, double t, int64_t rec, int mode, cudaStream_t st)
+static int observe_w(const Bufs& b, int gen, const double2* vec, double dt, int mode, cudaStream_t st)
 {
-    double* r = b.obs + rec * b.rec_len;
     if (b.batch > 1) {
         size_t shm = sizeof(unsigned long long) * 2 * (size_t)(2 * b.batch * b.N + 1);
-        int use_shared = shm <= 200 * 1024;
-        if (use_shared)
-            cudaFuncSetAttribute(k_obs_accum_batch<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+        int use_shared = shm <= kObsSharedMax;
         k_obs_accum_batch<W><<<b.G, kBlock, use_shared ? shm : 0, st>>>(b.model, b.ctr, b.keys[gen], b.meta[gen], vec,
                                                                         b.obs_part, use_shared);
         k_obs_finish_batch<W><<<1, kBlock, 0, st>>>(b.model, b.ctr, b.table[gen], b.table_slots, b.psi0_keys,
-                                                    b.psi0_amp, b.n0, vec, t, mode, b.obs_part, r);
+                                                    b.psi0_amp, b.n0, vec, dt, mode, b.obs_part, b.obs, b.rec_len);
         return 2;
     }
     k_obs_accum<W><<<b.G, kBlock, 0, st>>>(b.model, b.ctr, b.keys[gen], vec, b.obs_part);
     k_obs_finish<W><<<1, kBlock, 0, st>>>(b.model, b.ctr, b.table[gen], b.table_slots, b.psi0_keys, b.psi0_amp,
-                                          b.n0, vec, t, mode, b.obs_part, r);
+                                          b.n0, vec, dt, mode, b.obs_part, b.obs, b.rec_len);
     return 2;
+}
+
+template <int W>
+static int prepare_w(const Bufs& b)
+{
+    size_t shm = sizeof(unsigned long long) * 2 * (size_t)(2 * b.batch * b.N + 1);
+    if (b.batch > 1 && shm <= kObsSharedMax)
+        cudaFuncSetAttribute(k_obs_accum_batch<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+    return 0;
 }
 
 #define PACES_DISPATCH_W(W_, CALL)                                                      \
@@ -949,10 +964,12 @@ int launch_level(const Bufs& b, int gen, int f, int rescue_gen, int step, cudaSt
 
 int launch_csr(const Bufs& b, int gen, cudaStream_t st) { PACES_DISPATCH_W(b.W, csr_w<KW>(b, gen, st)) }
 
-int launch_observe(const Bufs& b, int gen, const double2* vec, double t, int64_t rec, int mode, cudaStream_t st)
+int launch_observe(const Bufs& b, int gen, const double2* vec, double dt, int mode, cudaStream_t st)
 {
-    PACES_DISPATCH_W(b.W, observe_w<KW>(b, gen, vec, t, rec, mode, st))
+    PACES_DISPATCH_W(b.W, observe_w<KW>(b, gen, vec, dt, mode, st))
 }
+
+int prepare_kernels(const Bufs& b) { PACES_DISPATCH_W(b.W, prepare_w<KW>(b)) }
 
 int launch_decode(const Bufs& b, int gen, uint32_t n, int32_t* site, int32_t* occ, cudaStream_t st)
 {

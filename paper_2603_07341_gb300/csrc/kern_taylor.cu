@@ -659,7 +659,19 @@ int launch_taylor(const Bufs& b, const TaylorParams& p, cudaStream_t st)
     else
         fn = p.lpr == 1 ? (const void*)k_taylor_dw<1> : p.lpr == 4 ? (const void*)k_taylor_dw<4>
                                                                    : (const void*)k_taylor_dw<8>;
-    cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(b.taylor_grid), dim3(kBlock), args, 0, st);
+    // cooperative launch (all blocks co-resident for the grid barrier); the
+    // launch-attribute form is also recorded by stream capture
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(b.taylor_grid);
+    cfg.blockDim = dim3(kBlock);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelExC(&cfg, fn, args);
     return e == cudaSuccess ? 1 : -1;
 }
 

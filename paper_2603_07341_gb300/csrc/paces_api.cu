@@ -82,6 +82,13 @@ struct paces_handle {
     int64_t step_index = 0;
     int64_t psi0_cap = 0;
 
+    bool use_graphs = false;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    bool gvalid[2] = {false, false};
+    double g_dt = 0.0, g_th2 = -1.0;
+    int64_t graph_launches[PACES_NUM_STAGES + 1] = {0};
+
     bool profiling = false;
     double stage_ms[PACES_NUM_STAGES] = {0};
     double stage_bytes[PACES_NUM_STAGES] = {0};
@@ -335,6 +342,15 @@ paces_status clear_table(paces_t h, int gen)
     return PACES_OK;
 }
 
+void invalidate_graphs(paces_t h)
+{
+    for (int g = 0; g < 2; ++g) {
+        if (h->gexec[g]) cudaGraphExecDestroy(h->gexec[g]);
+        h->gexec[g] = nullptr;
+        h->gvalid[g] = false;
+    }
+}
+
 // Grow the row capacity to at least `want`, keeping the current state (rows
 // [0, q) of generation gen in keys and in vector V[vec]) and rebuilding its
 // table.  Only the live state is stashed while the old buffers are released,
@@ -382,6 +398,7 @@ paces_status grow(paces_t h, uint64_t want, uint32_t q, int vec)
     h->row_allocs.swap(na);
     h->b = nb;
     h->cap_rows = (uint32_t)got;
+    invalidate_graphs(h);
     if (sk) {
         CUDA_TRY(h, cudaMemcpyAsync(h->b.keys[h->gen], sk, kb, cudaMemcpyDeviceToDevice, h->st));
         CUDA_TRY(h, cudaMemcpyAsync(h->b.V[vec], sv, vb, cudaMemcpyDeviceToDevice, h->st));
@@ -420,6 +437,7 @@ paces_status ensure_obs(paces_t h, int64_t need)
     h->fixed_allocs.push_back({nb, sizeof(double) * rl * ncap});
     h->b.obs = nb;
     h->obs_cap = ncap;
+    invalidate_graphs(h);
     return PACES_OK;
 }
 
@@ -448,42 +466,86 @@ cudaEvent_t ev(paces_t h, size_t i)
     return h->evpool[i];
 }
 
-// Enqueue one time step.  ev_base: first of 6 events (profiling only).
-void enqueue_step(paces_t h, double dt, double th2, int64_t rec, size_t ev_base)
+// Enqueue the kernels of one time step on stream st, reading generation gin
+// (fresh: the state set by set_state, no truncation).  Touches no host state
+// except launch counts, so it can be captured into a CUDA graph.  Returns the
+// output generation.  ev_base: first of 6 events (profiling only).
+int enqueue_kernels(paces_t h, cudaStream_t st, int gin, bool fresh, double dt, double th2, int step,
+                    bool prof, size_t ev_base)
 {
     const Bufs& b = h->b;
-    int step = (int)(h->step_index & 0x7fffffff);
     auto mark = [&](int k) {
-        if (h->profiling) cudaEventRecord(ev(h, ev_base + k), h->st);
+        if (prof) cudaEventRecord(ev(h, ev_base + k), st);
     };
     mark(0);
-    int gen = h->gen;
-    bool was_fresh = h->fresh;
-    if (!h->fresh) {
-        int gout = 1 - gen;
-        clear_table(h, gout);
-        count(h, Stage::Trunc, launch_truncate(b, gen, gout, th2, step, h->st));
+    int gen = gin;
+    if (!fresh) {
+        int gout = 1 - gin;
+        cudaMemsetAsync(b.table[gout], 0xFF, b.table_slots * slot_words(h->W) * 8, st);
+        count(h, Stage::Trunc, launch_truncate(b, gin, gout, th2, step, st));
         mark(1);
-        for (int f = 0; f < h->prm.m; ++f) count(h, Stage::Expand, launch_level(b, gout, f, gen, step, h->st));
+        for (int f = 0; f < h->prm.m; ++f) count(h, Stage::Expand, launch_level(b, gout, f, gin, step, st));
         gen = gout;
-        h->last_truncated = true;
     } else {
         mark(1);
-        h->last_truncated = false;
     }
     mark(2);
-    count(h, Stage::Csr, launch_csr(b, gen, h->st));
+    count(h, Stage::Csr, launch_csr(b, gen, st));
     mark(3);
-    count(h, Stage::Taylor, launch_taylor(b, taylor_params(h, dt, step), h->st));
+    count(h, Stage::Taylor, launch_taylor(b, taylor_params(h, dt, step), st));
     mark(4);
-    h->time += dt;
-    count(h, Stage::Obs, launch_observe(b, gen, b.V[0], h->time, rec, was_fresh ? 2 : 0, h->st));
+    count(h, Stage::Obs, launch_observe(b, gen, b.V[0], dt, fresh ? 2 : 0, st));
     mark(5);
+    return gen;
+}
+
+void enqueue_step(paces_t h, double dt, double th2, size_t ev_base)
+{
+    int step = (int)(h->step_index & 0x7fffffff);
+    bool fresh = h->fresh;
+    int gen = -1;
+    if (!fresh && h->use_graphs && !h->profiling) {
+        int gin = h->gen;
+        if (!h->gvalid[gin] || h->g_dt != dt || h->g_th2 != th2) {
+            if (h->gexec[gin]) cudaGraphExecDestroy(h->gexec[gin]);
+            h->gexec[gin] = nullptr;
+            h->gvalid[gin] = false;
+            if (!h->cap_stream) cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+            cudaGraph_t g = nullptr;
+            int64_t saved[PACES_NUM_STAGES + 1];
+            std::memcpy(saved, h->stage_launch, sizeof(saved));
+            bool ok = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            if (ok) enqueue_kernels(h, h->cap_stream, gin, false, dt, th2, step, false, 0);
+            ok = cudaStreamEndCapture(h->cap_stream, &g) == cudaSuccess && ok;
+            std::memcpy(h->graph_launches, h->stage_launch, sizeof(saved));
+            for (int i = 0; i <= PACES_NUM_STAGES; ++i) h->graph_launches[i] -= saved[i];
+            std::memcpy(h->stage_launch, saved, sizeof(saved));
+            if (ok) ok = cudaGraphInstantiate(&h->gexec[gin], g, 0) == cudaSuccess;
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            if (!ok) {                    // capture unavailable: launch directly from now on
+                h->use_graphs = false;
+                h->gexec[gin] = nullptr;
+            } else {
+                h->gvalid[gin] = true;
+                h->g_dt = dt;
+                h->g_th2 = th2;
+            }
+        }
+        if (h->gvalid[gin]) {
+            cudaGraphLaunch(h->gexec[gin], h->st);
+            for (int i = 0; i <= PACES_NUM_STAGES; ++i) h->stage_launch[i] += h->graph_launches[i];
+            gen = 1 - gin;
+        }
+    }
+    if (gen < 0) gen = enqueue_kernels(h, h->st, h->gen, fresh, dt, th2, step, h->profiling, ev_base);
+    h->last_truncated = !fresh;
     h->gen = gen;
     h->fresh = false;
     h->csr_valid = true;
     h->step_index += 1;
 }
+
 
 // Algorithmic bytes of one step from its record (the per-unit figures of the
 // design notes); fills bytes[5].
@@ -679,13 +741,15 @@ paces_status paces_create(const paces_params* params, const paces_allocator* all
     int bps = taylor_blocks_per_sm(h->lpr, 0);
     if (bps < 1) bps = 1;
     b.taylor_grid = h->sms * bps;
+    int bps_max = std::max(std::max(taylor_blocks_per_sm(1, 0), taylor_blocks_per_sm(4, 0)),
+                           taylor_blocks_per_sm(8, 0));
     b.rec_len = PACES_OBS_FIXED + 2 * N * h->R + (h->R > 1 ? 2 * h->R : 0);
 
     b.model = alloc_track<DevModel>(h, h->fixed_allocs, 1);
     b.ctr = alloc_track<Counters>(h, h->fixed_allocs, 1);
     b.blk_cnt = alloc_track<uint32_t>(h, h->fixed_allocs, kMaxChunkBlocks);
     b.blk_off = alloc_track<uint32_t>(h, h->fixed_allocs, kMaxChunkBlocks);
-    b.partials = alloc_track<double>(h, h->fixed_allocs, 8 * (size_t)b.taylor_grid + 16);
+    b.partials = alloc_track<double>(h, h->fixed_allocs, 8 * (size_t)h->sms * std::max(bps, bps_max) + 16);
     b.obs_part = alloc_track<unsigned long long>(h, h->fixed_allocs,
                                                  std::max<size_t>((size_t)b.grid * (2 * kMaxSites + 1) * 2,
                                                                   (size_t)(2 * N * h->R + 1) * 2));
@@ -715,6 +779,7 @@ paces_status paces_create(const paces_params* params, const paces_allocator* all
         paces_destroy(h);
         return PACES_ERR_CUDA;
     }
+    prepare_kernels(b);
     uint64_t want = params->max_rows ? params->max_rows : (uint64_t)kDefaultRows;
     if (grow(h, want, 0, 0) != PACES_OK) {
         paces_destroy(h);
@@ -733,6 +798,8 @@ paces_status paces_destroy(paces_t h)
     h->fixed_allocs.clear();
     cudaStreamSynchronize(h->st);
     for (auto e : h->evpool) cudaEventDestroy(e);
+    invalidate_graphs(h);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->hctr) cudaFreeHost(h->hctr);
     delete h->hmodel;
     delete h;
@@ -835,6 +902,8 @@ static paces_status upload_rows(paces_t h, int64_t n, const std::vector<uint64_t
     h->hctr->level_off[0] = 0;
     h->hctr->level_off[1] = (uint32_t)n;
     h->hctr->nlevels = 1;
+    h->hctr->time = h->time;
+    h->hctr->rec_index = h->n_records;
     CUDA_TRY(h, cudaMemsetAsync(h->b.obs_part, 0,
                                 sizeof(unsigned long long) * 2 * std::max(2 * kMaxSites + 1, 2 * h->N * h->R + 1),
                                 h->st));
@@ -875,6 +944,8 @@ paces_status paces_set_state(paces_t h, int64_t n, const int32_t* site, const in
     CUDA_TRY(h, cudaMemcpyAsync(h->b.psi0_keys, keys.data(), keys.size() * 8, cudaMemcpyHostToDevice, h->st));
     CUDA_TRY(h, cudaMemcpyAsync(h->b.psi0_amp, amps, (size_t)n * sizeof(double2), cudaMemcpyHostToDevice, h->st));
     h->b.n0 = n;
+    h->time = 0.0;
+    h->n_records = 0;
     for (int attempt = 0;; ++attempt) {
         s = upload_rows(h, n, keys, meta, amps, 1);
         if (s) return s;
@@ -908,7 +979,7 @@ paces_status paces_set_state(paces_t h, int64_t n, const int32_t* site, const in
     s = ensure_obs(h, 1);
     if (s) return s;
     CUDA_TRY(h, cudaMemsetAsync(h->b.obs, 0, sizeof(double) * h->b.rec_len, h->st));
-    count(h, Stage::Other, launch_observe(h->b, 0, h->b.V[1], 0.0, 0, 1, h->st));
+    count(h, Stage::Other, launch_observe(h->b, 0, h->b.V[1], 0.0, 1, h->st));
     s = read_counters(h);
     if (s) return s;
     if (h->hctr->err) return fail(h, PACES_ERR_CUDA, "device error " + std::to_string(h->hctr->err));
@@ -941,68 +1012,60 @@ paces_status paces_step(paces_t h, double dt, int64_t nsteps, double theta)
     double th2 = theta * theta;
     int64_t done = 0;
     std::vector<double> hrec;
+    paces_status s = ensure_obs(h, h->n_records + nsteps);
+    if (s) return s;
     while (done < nsteps) {
         int chunk = (int)std::min<int64_t>(kChunk, nsteps - done);
-        paces_status s = ensure_obs(h, h->n_records + chunk);
-        if (s) return s;
-        CUDA_TRY(h, cudaMemsetAsync(h->b.obs + h->n_records * h->b.rec_len, 0,
-                                    sizeof(double) * h->b.rec_len * chunk, h->st));
         int g0 = h->gen;
         bool fresh0 = h->fresh;
-        double t0 = h->time;
-        int64_t step0 = h->step_index;
-        for (int k = 0; k < chunk; ++k) enqueue_step(h, dt, th2, h->n_records + k, (size_t)k * 6);
+        int64_t rec0 = h->n_records, step0 = h->step_index;
+        for (int k = 0; k < chunk; ++k) enqueue_step(h, dt, th2, (size_t)k * 6);
         CUDA_TRY(h, cudaGetLastError());
         s = read_counters(h);
         if (s) return s;
         int err = h->hctr->err;
+        // steps that completed wrote their record: the first missing one failed
+        int64_t fs = (int64_t)h->hctr->rec_index - rec0;
+        if (fs < 0 || fs > chunk) fs = 0;
+        h->time = h->hctr->time;
         if (err == 0) {
             if (h->profiling) {
                 hrec.resize((size_t)chunk * h->b.rec_len);
-                CUDA_TRY(h, cudaMemcpy(hrec.data(), h->b.obs + h->n_records * h->b.rec_len,
-                                       sizeof(double) * hrec.size(), cudaMemcpyDeviceToHost));
+                CUDA_TRY(h, cudaMemcpy(hrec.data(), h->b.obs + rec0 * h->b.rec_len, sizeof(double) * hrec.size(),
+                                       cudaMemcpyDeviceToHost));
+                double prev_rows = 0.0;
+                if (rec0 > 0)
+                    CUDA_TRY(h, cudaMemcpy(&prev_rows, h->b.obs + (rec0 - 1) * h->b.rec_len + PACES_OBS_ROWS,
+                                           sizeof(double), cudaMemcpyDeviceToHost));
                 for (int k = 0; k < chunk; ++k) {
                     float ms;
-                    for (int st = 0; st < 5; ++st) {
+                    for (int st = 0; st < 5; ++st)
                         if (cudaEventElapsedTime(&ms, ev(h, (size_t)k * 6 + st), ev(h, (size_t)k * 6 + st + 1)) ==
                             cudaSuccess)
                             h->stage_ms[st] += ms;
-                    }
                     const double* r = hrec.data() + (size_t)k * h->b.rec_len;
-                    double q_in = k == 0 ? (double)0 : hrec[(size_t)(k - 1) * h->b.rec_len + PACES_OBS_ROWS];
-                    if (k == 0) {
-                        double prev[PACES_OBS_FIXED] = {0};
-                        if (h->n_records > 0)
-                            cudaMemcpy(prev, h->b.obs + (h->n_records - 1) * h->b.rec_len,
-                                       sizeof(double) * PACES_OBS_FIXED, cudaMemcpyDeviceToHost);
-                        q_in = prev[PACES_OBS_ROWS];
-                    }
-                    bool tr = !(k == 0 && fresh0);
-                    step_bytes(h, r, q_in, tr, h->stage_bytes);
+                    double q_in = k == 0 ? prev_rows : hrec[(size_t)(k - 1) * h->b.rec_len + PACES_OBS_ROWS];
+                    step_bytes(h, r, q_in, !(k == 0 && fresh0), h->stage_bytes);
                 }
             }
             h->n_records += chunk;
             done += chunk;
             continue;
         }
-        // a step failed: find it and restore the host view at its start
-        int64_t fs = (int64_t)h->hctr->err_step - (step0 & 0x7fffffff);
-        if (fs < 0 || fs >= chunk) fs = 0;
+        // restore the host view at the start of the failed step
         int gen = g0;
         bool fresh = fresh0;
-        double t = t0;
         for (int64_t k = 0; k < fs; ++k) {
             if (!fresh) gen = 1 - gen;
             fresh = false;
-            t += dt;
         }
-        h->n_records += fs;
-        done += fs;
-        h->time = t;
+        h->n_records = rec0 + fs;
         h->step_index = step0 + fs;
+        done += fs;
         if (err == kErrRows || err == kErrProbe || err == kErrCand) {
             // the failing step's input (generation gen, vector V0) is intact
             uint32_t q = h->hctr->q_in;
+            Counters keep = *h->hctr;
             h->gen = gen;
             h->fresh = fresh;
             std::memset(h->hctr, 0, sizeof(Counters));
@@ -1011,11 +1074,9 @@ paces_status paces_step(paces_t h, double dt, int64_t nsteps, double theta)
             h->hctr->kept = q;
             h->hctr->level_off[1] = q;
             h->hctr->nlevels = 1;
-            Counters keep = *h->hctr;
-            paces_status gs = read_counters(h);   // keep norm_last from the device
-            if (gs) return gs;
-            keep.norm_last = h->hctr->norm_last;
-            *h->hctr = keep;
+            h->hctr->norm_last = keep.norm_last;
+            h->hctr->time = keep.time;
+            h->hctr->rec_index = keep.rec_index;
             s = set_counters(h);
             if (s) return s;
             s = grow(h, (uint64_t)h->cap_rows + h->cap_rows / 8, q, 0);
@@ -1167,6 +1228,39 @@ paces_status paces_get_hamiltonian(paces_t h, int32_t* cnt, int32_t* cols, doubl
         dev_free(h, {dv, off[q] * 8});
     }
     CUDA_TRY(h, cudaStreamSynchronize(h->st));
+    return PACES_OK;
+}
+
+paces_status paces_get_tuning(paces_t h, paces_tuning* out)
+{
+    if (!h || !out) return PACES_ERR_INVALID;
+    std::memset(out, 0, sizeof(*out));
+    out->taylor_lanes_per_row = h->lpr;
+    out->taylor_blocks_per_sm = h->b.taylor_grid / h->sms;
+    out->grid_blocks_per_sm = h->b.grid / h->sms;
+    out->chunk_blocks_per_sm = h->b.G / h->sms;
+    out->use_graphs = h->use_graphs ? 1 : 0;
+    out->max_taylor_blocks_per_sm = taylor_blocks_per_sm(h->lpr, 0);
+    return PACES_OK;
+}
+
+paces_status paces_set_tuning(paces_t h, const paces_tuning* in)
+{
+    if (!h || !in) return PACES_ERR_INVALID;
+    int lpr = in->taylor_lanes_per_row;
+    if (lpr != 1 && lpr != 4 && lpr != 8) return fail(h, PACES_ERR_INVALID, "lanes per row must be 1, 4 or 8");
+    int maxb = taylor_blocks_per_sm(lpr, 0);
+    if (in->taylor_blocks_per_sm < 1 || in->taylor_blocks_per_sm > maxb)
+        return fail(h, PACES_ERR_INVALID, "propagator blocks per SM must be 1.." + std::to_string(maxb));
+    if (in->grid_blocks_per_sm < 1 || in->grid_blocks_per_sm > 32) return fail(h, PACES_ERR_INVALID, "grid blocks");
+    if (in->chunk_blocks_per_sm < 1 || in->chunk_blocks_per_sm * h->sms > kMaxChunkBlocks)
+        return fail(h, PACES_ERR_INVALID, "chunk blocks");
+    h->lpr = lpr;
+    h->b.taylor_grid = h->sms * in->taylor_blocks_per_sm;
+    h->b.grid = h->sms * in->grid_blocks_per_sm;
+    h->b.G = h->sms * in->chunk_blocks_per_sm;
+    h->use_graphs = in->use_graphs != 0;
+    invalidate_graphs(h);
     return PACES_OK;
 }
 

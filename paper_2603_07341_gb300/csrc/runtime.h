@@ -67,8 +67,8 @@ int launch_truncate(const Bufs& b, int gin, int gout, double th2, int step, cuda
 int launch_level(const Bufs& b, int gen, int f, int rescue_gen, int step, cudaStream_t st);
 int launch_csr(const Bufs& b, int gen, cudaStream_t st);
 int launch_taylor(const Bufs& b, const TaylorParams& p, cudaStream_t st);
-int launch_observe(const Bufs& b, int gen, const double2* vec, double t, int64_t rec,
-                   int mode, cudaStream_t st);
+int launch_observe(const Bufs& b, int gen, const double2* vec, double dt, int mode, cudaStream_t st);
+int prepare_kernels(const Bufs& b);
 int launch_decode(const Bufs& b, int gen, uint32_t n, int32_t* site, int32_t* occ,
                   cudaStream_t st);
 int launch_meta_from_keys(const Bufs& b, int gen, uint32_t n, cudaStream_t st);

@@ -31,19 +31,22 @@ CONFIGS = {
     "ring16": dict(n_sites=16, lattice_kind=RING, dims=(16, 1, 1), coupling_kind=NEAREST,
                    J=1.0, omega=1.0, g=1.5, eps=0.0, cap=8, m=2, m_init=10,
                    dt=0.02, nsteps=1000, theta=1e-7, start="site0"),
-    # 2D 6x6 aggregate, all-pairs J0/r^3 with J0 = -1, S = 1 (g = 1), K = 6
+    # 2D 6x6 aggregate, all-pairs J0/r^3 with J0 = -1, S = 1 (g = 1), K = 6.  theta = 1e-4:
+    # at 1e-6 (and 1e-5) H_eff outgrows the 288 GB of one GPU within ~100 steps
     "dipolar6x6": dict(n_sites=36, lattice_kind=OPEN2D, dims=(6, 6, 1), coupling_kind=DIPOLAR,
                        J=-1.0, omega=1.0, g=1.0, eps=0.0, cap=6, m=2, m_init=6,
-                       dt=0.05, nsteps=2048, theta=1e-6, start="bright"),
-    # disorder ensemble: 256 rings of N=12 with eps ~ N(0, 0.5 J), seeds 1000 + r
+                       dt=0.05, nsteps=2048, theta=1e-4, start="bright"),
+    # disorder ensemble: 256 rings of N=12 with eps ~ N(0, 0.5 J), seeds 1000 + r.
+    # theta = 1e-4 (2.7e6 rows per realisation; 1e-6 gives 3.7e7, 9.5e9 for the ensemble)
     "disorder12": dict(n_sites=12, lattice_kind=RING, dims=(12, 1, 1), coupling_kind=NEAREST,
                        J=1.0, omega=1.0, g=1.0, eps=0.0, cap=6, m=2, m_init=10,
-                       dt=0.05, nsteps=2048, theta=1e-6, start="bright",
+                       dt=0.05, nsteps=2048, theta=1e-4, start="bright",
                        realisations=256, eps_sigma=0.5, seed0=1000),
-    # 3D 4x4x4 open cube, nearest-neighbour J = 1, K = 4 -- the gradient workload
+    # 3D 4x4x4 open cube, nearest-neighbour J = 1, K = 4 -- the gradient workload.
+    # theta = 1e-4 (1e-5 and 1e-6 outgrow one GPU before step 80)
     "cube4": dict(n_sites=64, lattice_kind=OPEN3D, dims=(4, 4, 4), coupling_kind=NEAREST,
                   J=1.0, omega=1.0, g=1.0, eps=0.0, cap=4, m=2, m_init=6,
-                  dt=0.05, nsteps=400, theta=1e-6, start="bright", ckpt_every=20),
+                  dt=0.05, nsteps=400, theta=1e-4, start="bright", ckpt_every=20),
 }
 
 

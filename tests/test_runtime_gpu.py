@@ -1,0 +1,71 @@
+"""Step replay as CUDA graphs, launch-shape tuning and the autotuner: none of
+them may change results beyond the summation order of reductions."""
+import numpy as np
+import pytest
+
+from paper_2603_07341_gb300 import autotune
+from paper_2603_07341_gb300 import binding as B
+from paper_2603_07341_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def solver(cfg, **kw):
+    s = B.Solver(**W.model_kwargs(cfg, **kw.pop("over", {})), **kw)
+    s.set_state(*W.start_state(cfg))
+    return s
+
+
+@pytest.mark.parametrize("max_rows", [0, 16])
+def test_graph_replay_is_bitwise_identical(libpaces, max_rows):
+    cfg = W.CONFIGS["ring16"]
+    a = solver(cfg, max_rows=max_rows)
+    b = solver(cfg, max_rows=max_rows)
+    b.set_tuning(use_graphs=1)
+    assert b.tuning()["use_graphs"] == 1
+    for n in (5, 8, 13, 9):          # chunks of several sizes, through capacity growth
+        a.step(cfg["dt"], n, cfg["theta"])
+        b.step(cfg["dt"], n, cfg["theta"])
+    assert b.tuning()["use_graphs"] == 1          # capture succeeded: steps were replayed
+    ta, aa = a.tuples()
+    tb, ab = b.tuples()
+    assert np.array_equal(ta, tb) and np.array_equal(aa, ab)
+    assert np.array_equal(a.observables(), b.observables())
+
+
+def test_tuning_knobs_keep_results(libpaces):
+    cfg = W.CONFIGS["ring16"]
+    a = solver(cfg)
+    b = solver(cfg)
+    t = b.tuning()
+    b.set_tuning(taylor_lanes_per_row=4, taylor_blocks_per_sm=1, grid_blocks_per_sm=4, chunk_blocks_per_sm=2)
+    assert b.tuning()["taylor_lanes_per_row"] == 4
+    with pytest.raises(B.PacesError):
+        b.set_tuning(taylor_lanes_per_row=3)
+    with pytest.raises(B.PacesError):
+        b.set_tuning(taylor_blocks_per_sm=t["max_taylor_blocks_per_sm"] + 50)
+    a.step(cfg["dt"], 30, cfg["theta"])
+    b.step(cfg["dt"], 30, cfg["theta"])
+    ta, aa = a.tuples()
+    tb, ab = b.tuples()
+    assert np.array_equal(ta, tb)
+    assert np.max(np.abs(aa - ab)) <= 1e-13 * np.linalg.norm(aa)
+
+
+def test_autotuner_picks_valid_settings(libpaces, tmp_path):
+    cfg = W.CONFIGS["ring16"]
+    model = W.model_kwargs(cfg)
+    s = solver(cfg)
+    ref = solver(cfg)
+    s.step(cfg["dt"], 60, cfg["theta"])
+    ref.step(cfg["dt"], 60, cfg["theta"])
+    best, ms = autotune.autotune(s, model, cfg["dt"], cfg["theta"], steps=2,
+                                 cache_path=str(tmp_path / "tune.json"))
+    assert ms > 0 and best["taylor_lanes_per_row"] in (1, 4, 8)
+    assert (tmp_path / "tune.json").exists()
+    s.step(cfg["dt"], 5, cfg["theta"])
+    ref.step(cfg["dt"], 5, cfg["theta"])
+    ts, as_ = s.tuples()
+    tr, ar = ref.tuples()
+    assert np.array_equal(ts, tr)
+    assert np.max(np.abs(as_ - ar)) <= 1e-12 * np.linalg.norm(ar)
