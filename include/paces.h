@@ -280,6 +280,46 @@ typedef struct {
 paces_status paces_get_tuning(paces_t h, paces_tuning* out);
 paces_status paces_set_tuning(paces_t h, const paces_tuning* in);
 
+/* ---- Gradients (an extension: the paper defines the forward map only) -----
+ * Reverse-mode derivative of a loss of recorded steps with respect to the
+ * model parameters p = [J, g, omega, eps_0 .. eps_{N-1}] of Eq. holstein:
+ * J scales every hopping amplitude (J_ab = J M_ab), g scales every g_j,
+ * omega shifts every omega_j together, eps_s is the energy of exciton site s.
+ * The subspace sequence (truncation Q, regrowth, rescue; Sec. 3) and the
+ * number of Taylor terms of every step (Eq. taylor) are held at the values the
+ * forward steps took: the derivative is that of the recorded map, which is
+ * what central differences with the truncation masks held fixed measure.
+ *
+ * paces_record(h, k): from the current state on (or from the next set_state
+ * or load_state), keep a copy of the state every k recorded steps (keys, row
+ * descriptors and amplitudes; about 8W + 20 bytes per row) plus dt and theta
+ * of every step.  k = 0 stops recording and frees the copies.  A new state
+ * restarts the recording.  UNSUPPORTED for batch > 1 or PACES_C64_SPMV.  While
+ * steps are recorded paces_set_tuning returns STATE (the replay must repeat
+ * the forward's reduction order bit for bit).  A step that fails for any
+ * reason other than capacity ends the recording (backward then returns STATE).
+ *
+ * paces_backward(h, nsteps, dL_dc_final, dL_dC, dL_dP, grad): nsteps must be
+ * the number of recorded steps.  Cotangents (host arrays, each may be NULL):
+ *   dL_dc_final [2 q]       dL/dRe c + i dL/dIm c on the rows of the current
+ *                           state, in paces_get_state order (re, im pairs);
+ *   dL_dC       [2 nsteps]  dL/dRe C + i dL/dIm C of the autocorrelation
+ *                           C(t) = <psi(0)|psi(t)> after recorded step k;
+ *   dL_dP       [nsteps N]  dL/dP_s of the site populations after step k.
+ * grad [3 + N] receives dL/dp.  The pass replays each segment of k steps from
+ * its copy, then re-runs every step once more keeping its Taylor terms
+ * (16 bytes per row per term) and its row map, and runs the reverse
+ * recurrence mu_{n-1} = gbar + (i dt / n) H mu_n in FP64.  Gradient sums are
+ * exact fixed-point integers (2^-72), independent of thread timing.  The
+ * current state and the observable records are restored unchanged; the
+ * recording stays valid.  Errors: STATE (no valid recording, or a replayed
+ * step diverged from its record), INVALID (nsteps, NULL grad, a per-row
+ * contribution beyond 2^50), CAPACITY (scratch of about 100 bytes per row of
+ * capacity plus the terms of the largest step). */
+paces_status paces_record(paces_t h, int32_t ckpt_every);
+paces_status paces_backward(paces_t h, int64_t nsteps, const double* dL_dc_final, const double* dL_dC,
+                            const double* dL_dP, double* grad);
+
 /* ---- Expansion without allocation (no counterpart in the paper) -----------
  * Some callers cannot allocate device memory: hosts whose framework has
  * already reserved all of it in its own pool, real-time loops that must never

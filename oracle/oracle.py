@@ -65,7 +65,7 @@ def _load():
         lib.or_stats.argtypes = [P, dp]
         lib.or_populations.argtypes = [P, dp, dp]
         lib.or_record.argtypes = [P, C.c_int]
-        lib.or_backward.argtypes = [P, C.c_int, dp, dp, dp]
+        lib.or_backward.argtypes = [P, C.c_int, dp, dp, dp, dp]
         _lib = lib
     return _lib
 
@@ -189,11 +189,12 @@ class Oracle:
     def record(self, on=True):
         self._lib.or_record(self._h, 1 if on else 0)
 
-    def backward(self, nsteps, dL_dc_final=None, dL_dC=None):
+    def backward(self, nsteps, dL_dc_final=None, dL_dC=None, dL_dP=None):
         """Gradient [J, g, omega, eps_0..eps_{N-1}] of a loss of the recorded steps.
 
         dL_dc_final: complex cotangent on the final rows (dL = Re(conj(g) dc));
-        dL_dC: complex dL/dRe C_k + i dL/dIm C_k for recorded steps k = 0..nsteps-1.
+        dL_dC: complex dL/dRe C_k + i dL/dIm C_k for recorded steps k = 0..nsteps-1;
+        dL_dP: real dL/dP_s(t_k), shape (nsteps, N), of the site populations.
         """
         def ri(z):
             if z is None:
@@ -201,8 +202,11 @@ class Oracle:
             z = np.asarray(z, dtype=np.complex128)
             return np.ascontiguousarray(np.stack([z.real, z.imag], 1).reshape(-1))
         a, b = ri(dL_dc_final), ri(dL_dC)
+        p = None if dL_dP is None else np.ascontiguousarray(dL_dP, dtype=np.float64).reshape(-1)
+        if p is not None and p.size != int(nsteps) * self.N:
+            raise ValueError("dL_dP must hold nsteps * N values")
         grad = np.zeros(3 + self.N)
-        rc = self._lib.or_backward(self._h, int(nsteps), _dp(a), _dp(b), _dp(grad))
+        rc = self._lib.or_backward(self._h, int(nsteps), _dp(a), _dp(b), _dp(p), _dp(grad))
         if rc:
             raise OracleError(rc, "or_backward")
         return grad

@@ -707,7 +707,7 @@ static void apply_dh(const oracle_t* o, int p, const cplx* x, cplx* y)
 }
 
 int or_backward(oracle_t* o, int nsteps_rec, const double* dL_dc_final, const double* dL_dC,
-                double* grad)
+                const double* dL_dP, double* grad)
 {
     if (!o || nsteps_rec != o->nrec || nsteps_rec <= 0) return OR_INVALID;
     int N = o->N, len = o->len, P = 3 + N;
@@ -732,13 +732,6 @@ int or_backward(oracle_t* o, int nsteps_rec, const double* dL_dc_final, const do
         int q = R->nrows, nt = R->nterms;
         rc = load_rec_rows(o, R);
         if (rc) break;
-        if (dL_dC) {   /* C(t_k) = sum_j conj(psi0_j) c(key_j)  =>  gbar_j += psi0_j w_k */
-            cplx w = dL_dC[2 * k] + I * dL_dC[2 * k + 1];
-            for (int j = 0; j < o->init.nrows; ++j) {
-                int i = rs_find(&o->rows, rs_row(&o->init, j));
-                if (i >= 0) gbar[i] += o->c0[j] * w;
-            }
-        }
         /* forward terms of this step, recomputed */
         size_t qs = (size_t)q + 1;
         cplx* phis = (cplx*)malloc(sizeof(cplx) * (size_t)(nt + 1) * qs);
@@ -750,6 +743,20 @@ int or_backward(oracle_t* o, int nsteps_rec, const double* dL_dc_final, const do
             apply_h(o, phis + (size_t)(n - 1) * qs, y);
             cplx f = -I * R->dt / (double)n;
             for (int i = 0; i < q; ++i) phis[(size_t)n * qs + i] = f * y[i];
+        }
+        if (dL_dC) {   /* C(t_k) = sum_j conj(psi0_j) c(key_j)  =>  gbar_j += psi0_j w_k */
+            cplx w = dL_dC[2 * k] + I * dL_dC[2 * k + 1];
+            for (int j = 0; j < o->init.nrows; ++j) {
+                int i = rs_find(&o->rows, rs_row(&o->init, j));
+                if (i >= 0) gbar[i] += o->c0[j] * w;
+            }
+        }
+        if (dL_dP) {   /* P_s(t_k) = sum_{i: site s} |c_i|^2  =>  gbar_i += 2 c_i dL/dP_s */
+            for (int i = 0; i < q; ++i) {
+                cplx c = 0.0;
+                for (int n = 0; n <= nt; ++n) c += phis[(size_t)n * qs + i];
+                gbar[i] += 2.0 * c * dL_dP[(size_t)k * N + rs_row(&o->rows, i)[0]];
+            }
         }
         /* reverse recurrence */
         memcpy(mu, gbar, sizeof(cplx) * (size_t)q);

@@ -80,7 +80,8 @@ void or_populations(const oracle_t* o, double* P, double* nbar);
 /* adjoint: see paces_oracle.c (Sec. on gradients) */
 int or_record(oracle_t* o, int on);
 int or_backward(oracle_t* o, int nsteps_rec, const double* dL_dc_final /*2*nrows or NULL*/,
-                const double* dL_dC /*2*(nsteps_rec) or NULL*/, double* grad /*3+N*/);
+                const double* dL_dC /*2*(nsteps_rec) or NULL*/,
+                const double* dL_dP /*N*(nsteps_rec) or NULL*/, double* grad /*3+N*/);
 
 #ifdef __cplusplus
 }

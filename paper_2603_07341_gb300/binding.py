@@ -29,7 +29,7 @@ EXPORTED = (
     "paces_set_state", "paces_load_state", "paces_step", "paces_num_rows", "paces_get_state",
     "paces_get_levels", "paces_get_keep", "paces_get_hamiltonian", "paces_record_len",
     "paces_num_records", "paces_observables", "paces_profile", "paces_stage_stats",
-    "paces_expand_noalloc", "paces_get_tuning", "paces_set_tuning",
+    "paces_expand_noalloc", "paces_get_tuning", "paces_set_tuning", "paces_record", "paces_backward",
 )
 
 
@@ -130,6 +130,10 @@ def load():
     lib.paces_get_tuning.argtypes = [P, C.POINTER(Tuning)]
     lib.paces_set_tuning.restype = S
     lib.paces_set_tuning.argtypes = [P, C.POINTER(Tuning)]
+    lib.paces_record.restype = S
+    lib.paces_record.argtypes = [P, C.c_int32]
+    lib.paces_backward.restype = S
+    lib.paces_backward.argtypes = [P, C.c_int64, dp, dp, dp, dp]
     lib.paces_expand_noalloc.restype = S
     lib.paces_expand_noalloc.argtypes = [C.POINTER(Params), P, C.c_int64, P, C.c_int64, i64p, P]
     _lib = lib
@@ -378,6 +382,35 @@ class Solver:
 
     def profile(self, on=True):
         self._check(self._lib.paces_profile(self._h, 1 if on else 0), "profile")
+
+    def record(self, ckpt_every=20):
+        """Record the following steps for backward(); a checkpoint every ckpt_every steps (0: stop)."""
+        self._check(self._lib.paces_record(self._h, int(ckpt_every)), "record")
+
+    def backward(self, nsteps, dL_dc_final=None, dL_dC=None, dL_dP=None):
+        """dL/d[J, g, omega, eps_0..eps_{N-1}] of a loss of the recorded steps.
+
+        dL_dc_final: complex cotangent on the current rows (state() order);
+        dL_dC: complex dL/dRe C_k + i dL/dIm C_k, one per recorded step;
+        dL_dP: real dL/dP_s(t_k), shape (nsteps, N)."""
+        def ri(z, n):
+            if z is None:
+                return None
+            z = np.asarray(z, dtype=np.complex128).reshape(-1)
+            if z.size != n:
+                raise ValueError("cotangent has %d entries, expected %d" % (z.size, n))
+            return np.ascontiguousarray(np.stack([z.real, z.imag], 1).reshape(-1))
+        nsteps = int(nsteps)
+        a = ri(dL_dc_final, self.num_rows()) if dL_dc_final is not None else None
+        c = ri(dL_dC, nsteps)
+        p = None
+        if dL_dP is not None:
+            p = np.ascontiguousarray(dL_dP, dtype=np.float64).reshape(-1)
+            if p.size != nsteps * self.N:
+                raise ValueError("dL_dP must hold nsteps * N values")
+        grad = np.zeros(3 + self.N)
+        self._check(self._lib.paces_backward(self._h, nsteps, _dp(a), _dp(c), _dp(p), _dp(grad)), "backward")
+        return grad
 
     def stage_stats(self, reset=False):
         ms = np.zeros(5)

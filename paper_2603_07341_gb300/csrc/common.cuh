@@ -33,6 +33,7 @@ enum DevErr : int {
     kErrCand = 3,        // candidate index space exhausted
     kErrNoConverge = 4,  // Taylor series not converged in nmax terms
     kErrBarrier = 5,     // a grid barrier waited past its time limit
+    kErrGradRange = 6,   // an adjoint row contribution left the fixed-point range
 };
 
 // ---------------------------------------------------------------- division
@@ -153,6 +154,13 @@ __device__ __forceinline__ dwf dw_norm2(float4 v)
     return dw_add(dw_mul(re, re), dw_mul(im, im));
 }
 
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 // trunc(f * 2^84) as a signed 128-bit integer, exactly, from the bits of f
 // (finite f with |f| < 2^40).
 __device__ __forceinline__ __int128 fix84(float f)
@@ -228,6 +236,15 @@ struct Counters {
     double time;                     // t of the last record
     long long rec_index;             // next observables record
 };
+
+// Record the first device error (code, step, detail); later ones are dropped.
+__device__ __forceinline__ void set_err(Counters* ctr, int code, int step, int info)
+{
+    if (atomicCAS(&ctr->err, 0, code) == 0) {
+        ctr->err_step = step;
+        ctr->err_info = info;
+    }
+}
 
 // ---------------------------------------------------------------- keys
 template <int W>

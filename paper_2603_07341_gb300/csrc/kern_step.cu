@@ -25,13 +25,6 @@ __device__ __forceinline__ void chunk_of(uint32_t n, uint32_t G, uint32_t b, uin
     hi = (uint32_t)(h < n ? h : n);
 }
 
-__device__ __forceinline__ void set_err(Counters* ctr, int code, int step, int info)
-{
-    if (atomicCAS(&ctr->err, 0, code) == 0) {
-        ctr->err_step = step;
-        ctr->err_info = info;
-    }
-}
 
 // ---------------------------------------------------------------- insert rows
 template <int W>
@@ -121,7 +114,8 @@ __global__ void __launch_bounds__(kBlock) k_trunc_scatter(const uint64_t* __rest
                                                           uint64_t* __restrict__ keys_out, double2* __restrict__ c_out,
                                                           uint64_t* table_out, uint64_t slots,
                                                           const uint32_t* __restrict__ meta_in,
-                                                          uint32_t* __restrict__ meta_out, int step)
+                                                          uint32_t* __restrict__ meta_out,
+                                                          uint32_t* __restrict__ from, int step)
 {
     if (ctr->err) return;
     uint32_t q = ctr->q_in, lo, hi;
@@ -140,6 +134,7 @@ __global__ void __launch_bounds__(kBlock) k_trunc_scatter(const uint64_t* __rest
             store_key<W>(keys_out, dst, k);
             c_out[dst] = c_in[i];
             meta_out[dst] = meta_in[i];
+            if (from) from[dst] = i;
             if (!table_insert_unique<W>(table_out, slots, k, dst)) set_err(ctr, kErrProbe, step, 1);
         }
         run += tot;
@@ -283,7 +278,8 @@ __global__ void __launch_bounds__(kBlock) k_level_scatter(const DevModel* __rest
                                                           const uint32_t* __restrict__ wmask,
                                                           const uint32_t* __restrict__ blk_off,
                                                           const uint64_t* __restrict__ old_table, uint64_t old_slots,
-                                                          const double2* __restrict__ c_old, double2* __restrict__ c_new)
+                                                          const double2* __restrict__ c_old, double2* __restrict__ c_new,
+                                                          uint32_t* __restrict__ from)
 {
     if (ctr->err) return;
     uint32_t lo0 = ctr->level_off[f], base_row = ctr->level_off[f + 1];
@@ -315,11 +311,13 @@ __global__ void __launch_bounds__(kBlock) k_level_scatter(const DevModel* __rest
             for (int w = 0; w < W; ++w) sl[1 + w] = child.w[w];
             sl[0] = (sl[0] & 0xFFFFFFFF00000000ull) | (uint64_t)row;
             double2 a = make_double2(0.0, 0.0);
+            int64_t orow = -1;
             if (old_table) {
-                int64_t orow = table_lookup<W>(old_table, old_slots, child);
+                orow = table_lookup<W>(old_table, old_slots, child);
                 if (orow >= 0) a = c_old[orow];
             }
             c_new[row] = a;
+            if (from) from[row] = orow >= 0 ? (uint32_t)orow : kNone;
         }
         run += tot;
     }
@@ -511,12 +509,6 @@ __device__ __forceinline__ void split_weight(double w, unsigned long long& hi, u
     lo = (unsigned long long)((x - f) * 4294967296.0);   // next 32 bits, truncated
 }
 
-__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
 
 // Rows are taken 32 at a time per warp.  P_s goes through atomics on the
 // warp's own shared row (contention only between lanes of one warp with the
@@ -874,7 +866,8 @@ static int trunc_w(const Bufs& b, int gin, int gout, double th2, int step, cudaS
     k_trunc_count<<<b.G, kBlock, 0, st>>>(b.V[0], b.ctr, th2, dw_from_double(th2), b.fmt, b.keepw, b.blk_cnt);
     k_scan<<<1, 1024, 0, st>>>(b.blk_cnt, b.blk_off, b.G, b.ctr, kScanTrunc, 0, b.cap_rows, step);
     k_trunc_scatter<W><<<b.G, kBlock, 0, st>>>(b.keys[gin], b.V[0], b.ctr, b.keepw, b.blk_off, b.keys[gout],
-                                               b.V[1], b.table[gout], b.table_slots, b.meta[gin], b.meta[gout], step);
+                                               b.V[1], b.table[gout], b.table_slots, b.meta[gin], b.meta[gout], b.from,
+                                               step);
     return 3;
 }
 
@@ -891,7 +884,7 @@ static int level_w(const Bufs& b, int gen, int f, int rescue_gen, int step, cuda
     k_level_scatter<W><<<b.G, kBlock, 0, st>>>(b.model, b.ctr, f, b.keys[gen], b.meta[gen], b.table[gen],
                                                b.cand_slot,
                                                reinterpret_cast<const uint32_t*>(b.masks), b.blk_off, ot,
-                                               b.table_slots, b.V[0], b.V[1]);
+                                               b.table_slots, b.V[0], b.V[1], b.from);
     return 4;
 }
 

@@ -31,6 +31,8 @@ struct TaylorArgs {
     float2* fb;
     double* partials;        // [2][G][4]
     double* totals;          // [2][4]
+    void* terms;             // adjoint re-runs: phi_n stored at [(n - 1) * q + row]
+    int term_max;
     TaylorParams p;
 };
 
@@ -164,6 +166,7 @@ __global__ void __launch_bounds__(kBlock) k_taylor_f64(TaylorArgs a)
                 yv.y = fma(d, xi.y, yv.y);
                 double2 phi = make_double2(s * yv.y, -s * yv.x);     // (-i s) y
                 y[row] = phi;
+                if (a.terms && n <= a.term_max) reinterpret_cast<double2*>(a.terms)[(size_t)(n - 1) * q + row] = phi;
                 double2 rr = (n == 1) ? xi : a.r[row];
                 rr.x += phi.x;
                 rr.y += phi.y;
@@ -393,6 +396,7 @@ __global__ void __launch_bounds__(kBlock) k_taylor_dw(TaylorArgs a)
                 dwf yre = dot2_result(re), yim = dot2_result(im);      // y = s H x
                 float4 phi = make_float4(yim.hi, yim.lo, -yre.hi, -yre.lo);   // phi = -i y
                 Y[row] = phi;
+                if (a.terms && n <= a.term_max) reinterpret_cast<float4*>(a.terms)[(size_t)(n - 1) * q + row] = phi;
                 float4 rr = (n == 1) ? xi : R[row];
                 dwf r_re = dw_add(dwf{rr.x, rr.y}, dwf{phi.x, phi.y});
                 dwf r_im = dw_add(dwf{rr.z, rr.w}, dwf{phi.z, phi.w});
@@ -647,6 +651,8 @@ int launch_taylor(const Bufs& b, const TaylorParams& p, cudaStream_t st)
     a.fb = b.F[1];
     a.partials = b.partials;
     a.totals = b.partials + 2 * 4 * (size_t)b.taylor_grid;
+    a.terms = b.terms;
+    a.term_max = b.term_max;
     a.p = p;
     void* args[] = {&a};
     const void* fn;

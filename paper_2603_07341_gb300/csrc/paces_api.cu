@@ -89,6 +89,21 @@ struct paces_handle {
     double g_dt = 0.0, g_th2 = -1.0;
     int64_t graph_launches[PACES_NUM_STAGES + 1] = {0};
 
+    // recording for the reverse pass: a checkpoint of the state every
+    // rec_every steps, plus dt and theta^2 of every recorded step
+    struct Ckpt {
+        int64_t step;             // recorded step that starts from this state
+        uint32_t q;
+        bool fresh;
+        double time;
+        DevAlloc mem;             // keys | meta | amplitudes
+    };
+    int rec_every = 0;
+    bool rec_valid = false;
+    int64_t rec_steps = 0, rec_base = 0;   // rec_base: record written by recorded step 0
+    std::vector<double> rec_dt, rec_th2;
+    std::vector<Ckpt> ckpts;
+
     bool profiling = false;
     double stage_ms[PACES_NUM_STAGES] = {0};
     double stage_bytes[PACES_NUM_STAGES] = {0};
@@ -547,6 +562,94 @@ void enqueue_step(paces_t h, double dt, double th2, size_t ev_base)
 }
 
 
+// ---------------------------------------------------------------- recording
+void drop_recording(paces_t h)
+{
+    for (auto& c : h->ckpts) dev_free(h, c.mem);
+    h->ckpts.clear();
+    h->rec_dt.clear();
+    h->rec_th2.clear();
+    h->rec_steps = 0;
+    h->rec_valid = h->rec_every > 0;
+    h->rec_base = h->n_records;
+}
+
+size_t state_bytes(paces_t h, uint32_t q, size_t* off_meta, size_t* off_vec)
+{
+    size_t kb = ((size_t)q * h->W * 8 + 255) & ~(size_t)255;
+    size_t mb = ((size_t)q * 4 + 255) & ~(size_t)255;
+    *off_meta = kb;
+    *off_vec = kb + mb;
+    return kb + mb + (size_t)q * 16 + 256;
+}
+
+// Copy rows [0, q) of generation gen (keys, meta, amplitudes of V[vec]) to dst.
+paces_status copy_state_out(paces_t h, int gen, int vec, uint32_t q, char* dst)
+{
+    size_t om, ov;
+    state_bytes(h, q, &om, &ov);
+    if (q == 0) return PACES_OK;
+    CUDA_TRY(h, cudaMemcpyAsync(dst, h->b.keys[gen], (size_t)q * h->W * 8, cudaMemcpyDeviceToDevice, h->st));
+    CUDA_TRY(h, cudaMemcpyAsync(dst + om, h->b.meta[gen], (size_t)q * 4, cudaMemcpyDeviceToDevice, h->st));
+    CUDA_TRY(h, cudaMemcpyAsync(dst + ov, h->b.V[vec], (size_t)q * 16, cudaMemcpyDeviceToDevice, h->st));
+    return PACES_OK;
+}
+
+// Make a copied state the live one (generation 0; V1 when fresh, else V0),
+// with its table rebuilt and one BFS level, so that a P H P build uses table
+// lookups for every row.
+paces_status restore_state(paces_t h, const char* src, uint32_t q, bool fresh, double time, int64_t rec_index,
+                           const Counters* base = nullptr)
+{
+    size_t om, ov;
+    state_bytes(h, q, &om, &ov);
+    int vec = fresh ? 1 : 0;
+    h->gen = 0;
+    paces_status s = clear_table(h, 0);
+    if (s) return s;
+    if (q > 0) {
+        CUDA_TRY(h, cudaMemcpyAsync(h->b.keys[0], src, (size_t)q * h->W * 8, cudaMemcpyDeviceToDevice, h->st));
+        CUDA_TRY(h, cudaMemcpyAsync(h->b.meta[0], src + om, (size_t)q * 4, cudaMemcpyDeviceToDevice, h->st));
+        CUDA_TRY(h, cudaMemcpyAsync(h->b.V[vec], src + ov, (size_t)q * 16, cudaMemcpyDeviceToDevice, h->st));
+        count(h, Stage::Other, launch_insert_rows(h->b, 0, q, h->st));
+    }
+    if (base) *h->hctr = *base;
+    else std::memset(h->hctr, 0, sizeof(Counters));
+    h->hctr->q = q;
+    h->hctr->q_in = q;
+    h->hctr->kept = q;
+    h->hctr->level_off[0] = 0;
+    h->hctr->level_off[1] = q;
+    h->hctr->nlevels = 1;
+    h->hctr->time = time;
+    h->hctr->rec_index = (uint32_t)rec_index;
+    h->hctr->err = 0;
+    s = set_counters(h);
+    if (s) return s;
+    h->fresh = fresh;
+    return PACES_OK;
+}
+
+// Checkpoint the live state before recorded step h->rec_steps.
+paces_status save_checkpoint(paces_t h)
+{
+    if (!h->ckpts.empty() && h->ckpts.back().step == h->rec_steps) return PACES_OK;
+    uint32_t q = h->hctr->q;
+    size_t om, ov, bytes = state_bytes(h, q, &om, &ov);
+    void* p = dev_alloc(h, bytes);
+    if (!p) return fail(h, PACES_ERR_CAPACITY, "checkpoint buffer");
+    bytes = (bytes + 255) & ~(size_t)255;
+    paces_handle::Ckpt c{h->rec_steps, q, h->fresh, h->hctr->time, {p, bytes}};
+    paces_status s = copy_state_out(h, h->gen, h->fresh ? 1 : 0, q, (char*)p);
+    if (s) {
+        dev_free(h, c.mem);
+        return s;
+    }
+    h->ckpts.push_back(c);
+    return PACES_OK;
+}
+
+
 // Algorithmic bytes of one step from its record (the per-unit figures of the
 // design notes); fills bytes[5].
 void step_bytes(paces_t h, const double* r, double q_in, bool truncated, double* bytes)
@@ -793,6 +896,7 @@ paces_status paces_destroy(paces_t h)
 {
     if (!h) return PACES_ERR_INVALID;
     cudaStreamSynchronize(h->st);
+    drop_recording(h);
     free_rows(h);
     for (auto& a : h->fixed_allocs) dev_free(h, a);
     h->fixed_allocs.clear();
@@ -984,6 +1088,7 @@ paces_status paces_set_state(paces_t h, int64_t n, const int32_t* site, const in
     if (s) return s;
     if (h->hctr->err) return fail(h, PACES_ERR_CUDA, "device error " + std::to_string(h->hctr->err));
     h->n_records = 1;
+    drop_recording(h);
     return PACES_OK;
 }
 
@@ -1001,6 +1106,7 @@ paces_status paces_load_state(paces_t h, int64_t n, const int32_t* site, const i
     h->has_state = true;
     h->csr_valid = false;
     h->last_truncated = false;
+    drop_recording(h);
     return PACES_OK;
 }
 
@@ -1014,8 +1120,19 @@ paces_status paces_step(paces_t h, double dt, int64_t nsteps, double theta)
     std::vector<double> hrec;
     paces_status s = ensure_obs(h, h->n_records + nsteps);
     if (s) return s;
+    bool recording = h->rec_every > 0 && h->rec_valid;
     while (done < nsteps) {
         int chunk = (int)std::min<int64_t>(kChunk, nsteps - done);
+        if (recording) {
+            if (h->rec_steps % h->rec_every == 0) {
+                s = save_checkpoint(h);
+                if (s) {
+                    h->rec_valid = false;
+                    return s;
+                }
+            }
+            chunk = (int)std::min<int64_t>(chunk, h->rec_every - h->rec_steps % h->rec_every);
+        }
         int g0 = h->gen;
         bool fresh0 = h->fresh;
         int64_t rec0 = h->n_records, step0 = h->step_index;
@@ -1050,6 +1167,11 @@ paces_status paces_step(paces_t h, double dt, int64_t nsteps, double theta)
             }
             h->n_records += chunk;
             done += chunk;
+            if (recording) {
+                h->rec_steps += chunk;
+                h->rec_dt.insert(h->rec_dt.end(), (size_t)chunk, dt);
+                h->rec_th2.insert(h->rec_th2.end(), (size_t)chunk, th2);
+            }
             continue;
         }
         // restore the host view at the start of the failed step
@@ -1062,6 +1184,11 @@ paces_status paces_step(paces_t h, double dt, int64_t nsteps, double theta)
         h->n_records = rec0 + fs;
         h->step_index = step0 + fs;
         done += fs;
+        if (recording) {
+            h->rec_steps += fs;
+            h->rec_dt.insert(h->rec_dt.end(), (size_t)fs, dt);
+            h->rec_th2.insert(h->rec_th2.end(), (size_t)fs, th2);
+        }
         if (err == kErrRows || err == kErrProbe || err == kErrCand) {
             // the failing step's input (generation gen, vector V0) is intact
             uint32_t q = h->hctr->q_in;
@@ -1083,6 +1210,7 @@ paces_status paces_step(paces_t h, double dt, int64_t nsteps, double theta)
             if (s) return s;
             continue;
         }
+        h->rec_valid = false;     // (capacity failures continued above)
         if (err == kErrNoConverge) {
             // the failed step's truncated and regrown state stays, unpropagated
             int nterm = h->hctr->err_info;
@@ -1247,6 +1375,8 @@ paces_status paces_get_tuning(paces_t h, paces_tuning* out)
 paces_status paces_set_tuning(paces_t h, const paces_tuning* in)
 {
     if (!h || !in) return PACES_ERR_INVALID;
+    if (h->rec_steps > 0)
+        return fail(h, PACES_ERR_STATE, "recorded steps must be replayed with the tuning they ran with");
     int lpr = in->taylor_lanes_per_row;
     if (lpr != 1 && lpr != 4 && lpr != 8) return fail(h, PACES_ERR_INVALID, "lanes per row must be 1, 4 or 8");
     int maxb = taylor_blocks_per_sm(lpr, 0);
@@ -1307,5 +1437,229 @@ paces_status paces_stage_stats(paces_t h, double* ms, int64_t* launches, double*
     }
     return PACES_OK;
 }
+
+paces_status paces_record(paces_t h, int32_t ckpt_every)
+{
+    if (!h || ckpt_every < 0) return PACES_ERR_INVALID;
+    if (ckpt_every > 0 && h->R > 1) return fail(h, PACES_ERR_UNSUPPORTED, "the reverse pass covers batch 1 only");
+    if (ckpt_every > 0 && h->prm.precision == PACES_C64_SPMV)
+        return fail(h, PACES_ERR_UNSUPPORTED, "the reverse pass needs double-word or FP64 amplitudes");
+    h->rec_every = ckpt_every;
+    drop_recording(h);
+    return PACES_OK;
+}
+
+paces_status paces_backward(paces_t h, int64_t nsteps, const double* dL_dc_final, const double* dL_dC,
+                            const double* dL_dP, double* grad)
+{
+    if (!h || !grad) return PACES_ERR_INVALID;
+    if (h->rec_every <= 0 || !h->rec_valid || !h->has_state)
+        return fail(h, PACES_ERR_STATE, "no valid recording: call paces_record before stepping");
+    if (nsteps <= 0 || nsteps != h->rec_steps)
+        return fail(h, PACES_ERR_INVALID, "nsteps must equal the recorded steps (" + std::to_string(h->rec_steps) + ")");
+    const int N = h->N, NP = 3 + N;
+    const int64_t S = h->rec_every;
+    const size_t rl = (size_t)h->b.rec_len;
+    paces_status s = read_counters(h);
+    if (s) return s;
+    const Counters live_ctr = *h->hctr;
+    const uint32_t q_live = live_ctr.q;
+    const int live_gen = h->gen;
+    const double live_time = h->time;
+
+    // forward records of the recorded steps (restored unchanged at the end)
+    std::vector<double> rec((size_t)nsteps * rl);
+    CUDA_TRY(h, cudaMemcpyAsync(rec.data(), h->b.obs + (size_t)h->rec_base * rl, sizeof(double) * rec.size(),
+                                cudaMemcpyDeviceToHost, h->st));
+    CUDA_TRY(h, cudaStreamSynchronize(h->st));
+    std::vector<uint32_t> qk((size_t)nsteps);
+    std::vector<int> ntk((size_t)nsteps);
+    size_t term_bytes = 256, seg_bytes = 256;
+    for (int64_t k = 0; k < nsteps; ++k) {
+        qk[k] = (uint32_t)rec[(size_t)k * rl + PACES_OBS_ROWS];
+        ntk[k] = (int)rec[(size_t)k * rl + PACES_OBS_TERMS];
+        term_bytes = std::max(term_bytes, (size_t)std::max(ntk[k] - 1, 0) * qk[k] * 16);
+    }
+    if (qk[nsteps - 1] != q_live) return fail(h, PACES_ERR_STATE, "the live state is not the last recorded one");
+    for (int64_t k0 = 0; k0 < nsteps; k0 += S) {
+        size_t tot = 0, om, ov;
+        for (int64_t k = k0 + 1; k < std::min(k0 + S, nsteps); ++k) tot += state_bytes(h, qk[k - 1], &om, &ov);
+        seg_bytes = std::max(seg_bytes, tot);
+    }
+
+    // device scratch, released (and the live state restored) on every exit
+    std::vector<DevAlloc> tmp;
+    auto get = [&](size_t bytes) -> char* {
+        bytes = (bytes + 255) & ~(size_t)255;
+        if (bytes == 0) bytes = 256;
+        void* p = dev_alloc(h, bytes);
+        if (p) tmp.push_back({p, bytes});
+        return (char*)p;
+    };
+    const uint64_t cap = h->cap_rows;
+    size_t om, ov;
+    char* live = get(state_bytes(h, q_live, &om, &ov));
+    char* seg = get(seg_bytes);
+    uint32_t* from = (uint32_t*)get(cap * 4);
+    char* terms = get(term_bytes);
+    double* acc = (double*)get(cap * 3 * 8);
+    double2* G[2] = {(double2*)get(cap * 16), (double2*)get(cap * 16)};
+    double2* MU[2] = {(double2*)get(cap * 16), (double2*)get(cap * 16)};
+    unsigned long long* bins = (unsigned long long*)get((size_t)3 * NP * 8);
+    double* dP = dL_dP ? (double*)get((size_t)nsteps * N * 8) : nullptr;
+    double2* dC = dL_dC ? (double2*)get((size_t)nsteps * 16) : nullptr;
+    bool ok = live && seg && from && terms && acc && G[0] && G[1] && MU[0] && MU[1] && bins &&
+              (!dL_dP || dP) && (!dL_dC || dC);
+    bool saved_live = false;
+    auto finish = [&](paces_status st) -> paces_status {
+        h->b.from = nullptr;
+        h->b.terms = nullptr;
+        h->b.term_max = 0;
+        cudaGetLastError();
+        std::string msg = h->err;
+        if (saved_live) {
+            paces_status r = restore_state(h, live, q_live, false, live_time, live_ctr.rec_index, &live_ctr);
+            if (r == PACES_OK)
+                r = cudaMemcpyAsync(h->b.obs + (size_t)h->rec_base * rl, rec.data(), sizeof(double) * rec.size(),
+                                    cudaMemcpyHostToDevice, h->st) == cudaSuccess ? PACES_OK : PACES_ERR_CUDA;
+            if (r != PACES_OK) {
+                h->has_state = false;
+                if (st == PACES_OK) st = r;
+            }
+            h->time = live_time;
+        }
+        cudaStreamSynchronize(h->st);
+        for (auto& a : tmp) dev_free(h, a);
+        cudaStreamSynchronize(h->st);
+        h->csr_valid = false;
+        h->last_truncated = false;
+        if (st != PACES_OK && !msg.empty()) h->err = msg;
+        return st;
+    };
+#define ADJ_TRY(call)                                                             \
+    do {                                                                          \
+        cudaError_t e_ = (call);                                                  \
+        if (e_ != cudaSuccess) return finish(cuda_fail(h, e_, #call));            \
+    } while (0)
+    if (!ok) return finish(fail(h, PACES_ERR_CAPACITY, "reverse-pass buffers"));
+    (void)live_gen;
+    s = copy_state_out(h, h->gen, 0, q_live, live);
+    if (s) return finish(s);
+    saved_live = true;
+
+    ADJ_TRY(cudaMemsetAsync(bins, 0, (size_t)3 * NP * 8, h->st));
+    if (dP) ADJ_TRY(cudaMemcpyAsync(dP, dL_dP, (size_t)nsteps * N * 8, cudaMemcpyHostToDevice, h->st));
+    if (dC) ADJ_TRY(cudaMemcpyAsync(dC, dL_dC, (size_t)nsteps * 16, cudaMemcpyHostToDevice, h->st));
+    int cur = 0;
+    if (dL_dc_final)
+        ADJ_TRY(cudaMemcpyAsync(G[cur], dL_dc_final, (size_t)q_live * 16, cudaMemcpyHostToDevice, h->st));
+    else
+        ADJ_TRY(cudaMemsetAsync(G[cur], 0, (size_t)q_live * 16, h->st));
+
+    const int P = h->P;
+    const int lpr = P <= 4 ? 1 : P <= 8 ? 2 : P <= 16 ? 4 : P <= 32 ? 8 : 16;
+    std::vector<__int128> T((size_t)NP, 0);
+    std::vector<unsigned long long> hb((size_t)3 * NP);
+    int gen = 0;
+
+    // one recorded step, replayed from the live buffers; capture: keep its
+    // terms and row map for the reverse pass
+    auto replay = [&](int64_t k, bool capture) -> paces_status {
+        if (capture) {
+            h->b.from = from;
+            h->b.terms = terms;
+            h->b.term_max = std::max(ntk[k] - 1, 0);
+        }
+        gen = enqueue_kernels(h, h->st, h->gen, h->fresh, h->rec_dt[k], h->rec_th2[k], (int)k, false, 0);
+        h->gen = gen;
+        h->b.from = nullptr;
+        h->b.terms = nullptr;
+        h->b.term_max = 0;
+        CUDA_TRY(h, cudaGetLastError());
+        paces_status r = read_counters(h);
+        if (r) return r;
+        if (h->hctr->err)
+            return fail(h, PACES_ERR_CUDA, "device error " + std::to_string(h->hctr->err) + " replaying step " +
+                                               std::to_string(k));
+        if (h->hctr->q != qk[k] || (int)h->hctr->nterms != ntk[k])
+            return fail(h, PACES_ERR_STATE, "replay of recorded step " + std::to_string(k) + " diverged");
+        h->fresh = false;
+        return PACES_OK;
+    };
+
+    const int64_t nseg = (nsteps + S - 1) / S;
+    for (int64_t sg = nseg - 1; sg >= 0; --sg) {
+        const int64_t k0 = sg * S, k1 = std::min(k0 + S, nsteps);
+        if (sg >= (int64_t)h->ckpts.size() || h->ckpts[sg].step != k0)
+            return finish(fail(h, PACES_ERR_STATE, "missing checkpoint"));
+        const paces_handle::Ckpt& C = h->ckpts[sg];
+        // forward over the segment, keeping the input state of every step
+        std::vector<size_t> off((size_t)(k1 - k0), 0);
+        std::vector<double> tin((size_t)(k1 - k0), C.time);
+        s = restore_state(h, (const char*)C.mem.p, C.q, C.fresh, C.time, h->rec_base + k0);
+        if (s) return finish(s);
+        size_t at = 0;
+        for (int64_t k = k0; k + 1 < k1; ++k) {
+            s = replay(k, false);
+            if (s) return finish(s);
+            off[k + 1 - k0] = at;
+            tin[k + 1 - k0] = h->hctr->time;
+            s = copy_state_out(h, gen, 0, qk[k], seg + at);
+            if (s) return finish(s);
+            at += state_bytes(h, qk[k], &om, &ov);
+        }
+        // reverse over the segment
+        for (int64_t k = k1 - 1; k >= k0; --k) {
+            if (k == k0) s = restore_state(h, (const char*)C.mem.p, C.q, C.fresh, C.time, h->rec_base + k0);
+            else s = restore_state(h, seg + off[k - k0], qk[k - 1], false, tin[k - k0], h->rec_base + k);
+            if (s) return finish(s);
+            s = replay(k, true);
+            if (s) return finish(s);
+            const uint32_t q = qk[k];
+            const int nt = ntk[k];
+            double2* gb = G[cur];
+            count(h, Stage::Other, launch_adj_obs(h->b, gen, h->b.V[0], dP ? dP + (size_t)k * N : nullptr,
+                                                  dC ? dC + k : nullptr, gb, h->st));
+            const double2* mu = gb;
+            int x = 0;
+            for (int n = nt; n >= 1; --n) {
+                const void* phi = n == 1 ? (const void*)h->b.V[1] : (const void*)(terms + (size_t)(n - 2) * q * 16);
+                count(h, Stage::Other, launch_adj_term(h->b, lpr, mu, phi, gb, MU[x], acc, cap, h->rec_dt[k] / n,
+                                                       n == nt, h->st));
+                mu = MU[x];
+                x ^= 1;
+            }
+            if (nt >= 1) {
+                count(h, Stage::Other, launch_adj_bins(h->b, gen, acc, cap, bins, h->st));
+                ADJ_TRY(cudaMemcpyAsync(hb.data(), bins, hb.size() * 8, cudaMemcpyDeviceToHost, h->st));
+                ADJ_TRY(cudaMemsetAsync(bins, 0, hb.size() * 8, h->st));
+            }
+            if (k > 0) {
+                ADJ_TRY(cudaMemsetAsync(G[1 - cur], 0, (size_t)qk[k - 1] * 16, h->st));
+                count(h, Stage::Other, launch_adj_scatter(h->b, from, mu, G[1 - cur], h->st));
+            }
+            ADJ_TRY(cudaGetLastError());
+            s = read_counters(h);
+            if (s) return finish(s);
+            if (h->hctr->err == kErrGradRange)
+                return finish(fail(h, PACES_ERR_INVALID, "a gradient contribution exceeds 2^50 in magnitude"));
+            if (h->hctr->err) return finish(fail(h, PACES_ERR_CUDA, "device error " + std::to_string(h->hctr->err)));
+            if (nt >= 1)
+                for (int p = 0; p < NP; ++p) {
+                    const __int128 two32 = (__int128)1 << 32, two64 = two32 * two32;
+                    T[p] += (__int128)(int64_t)hb[3 * p + 2] * two64 + (__int128)hb[3 * p + 1] * two32 +
+                            (__int128)hb[3 * p];
+                }
+            if (k > 0) cur ^= 1;
+        }
+    }
+    for (int p = 0; p < NP; ++p) {
+        int64_t hi = (int64_t)(T[p] >> 64);
+        uint64_t lo = (uint64_t)(T[p] & (__int128)0xFFFFFFFFFFFFFFFFull);
+        grad[p] = std::ldexp((double)hi, -8) + std::ldexp((double)lo, -72);
+    }
+    return finish(PACES_OK);
+}
+#undef ADJ_TRY
 
 }  // extern "C"

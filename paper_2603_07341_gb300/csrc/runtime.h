@@ -28,6 +28,9 @@ struct Bufs {
     uint8_t* cnt;                  // entries per row
     double* diag;                  // diagonal per row
     uint32_t* cand_slot;           // candidate -> table slot
+    uint32_t* from;                // adjoint re-runs: row -> row of the previous state (or kNone)
+    void* terms;                   // adjoint re-runs: Taylor terms phi_1.. [n][row], 16 bytes each
+    int term_max;                  // terms storable
     uint64_t* masks;               // winner bits per frontier row
     uint32_t* keepw;               // truncation bitmask
     uint32_t* blk_cnt;             // chunk counts
@@ -76,6 +79,15 @@ int launch_export_csr(const Bufs& b, uint32_t q, const uint64_t* off, int32_t* c
                       double* vals, cudaStream_t st);
 
 int taylor_blocks_per_sm(int lpr, int c64);
+
+// Reverse pass of one step (kern_adjoint.cu).
+int launch_adj_obs(const Bufs& b, int gen, const void* vec, const double* dLdP, const double2* wC, double2* gbar,
+                   cudaStream_t st);
+int launch_adj_term(const Bufs& b, int lpr, const double2* mu_in, const void* phi, const double2* gbar,
+                    double2* mu_out, double* acc, uint64_t acc_stride, double s, int first, cudaStream_t st);
+int launch_adj_bins(const Bufs& b, int gen, const double* acc, uint64_t acc_stride, unsigned long long* bins,
+                    cudaStream_t st);
+int launch_adj_scatter(const Bufs& b, const uint32_t* from, const double2* mu0, double2* gprev, cudaStream_t st);
 
 // Host: plan the key layout and fill the device model description.
 paces_status plan_layout_internal(const paces_params* params, paces_layout* out);

@@ -330,18 +330,19 @@ def _loss_run(params, keeps=None, record=False, nsteps=12, theta=2e-3):
     o.set_state([0, 1], [[0, 0, 0], [0, 0, 0]], [0.8, 0.6j])
     if record:
         o.record(True)
-    Cs, masks = [], []
+    Cs, masks, Ps = [], [], []
     for k in range(nsteps):
         kp = None if keeps is None or k == 0 else keeps[k]
         o.step(0.1, theta, kp)
         masks.append(o.last_keep() if k > 0 else None)
         st = o.stats()
         Cs.append(st["C_re"] + 1j * st["C_im"])
-    Cs = np.array(Cs)
+        Ps.append(o.populations()[0])
+    Cs, Ps = np.array(Cs), np.array(Ps)
     target = 0.3 * np.exp(-0.5j * np.arange(nsteps))
     P, _ = o.populations()
     L = P[0] + np.sum(np.abs(Cs - target) ** 2)
-    return L, o, masks, Cs, target
+    return L, o, masks, Cs, target, Ps
 
 
 def test_adjoint_matches_finite_differences():
@@ -350,7 +351,7 @@ def test_adjoint_matches_finite_differences():
     has no gradient: parity pinned by finite differences)."""
     eps = W.seeded_normal(3, 7) * 0.2
     base = (0.4, 0.7, 1.1, eps)
-    L0, o, masks, Cs, target = _loss_run(base, record=True)
+    L0, o, masks, Cs, target, _ = _loss_run(base, record=True)
     t, a = o.rows()
     dL_dc = np.where(t[:, 0] == 0, 2.0 * a, 0.0)
     grad = o.backward(len(Cs), dL_dc_final=dL_dc, dL_dC=2.0 * (Cs - target))
@@ -370,4 +371,34 @@ def test_adjoint_matches_finite_differences():
         lp = _loss_run(perturbed(p, h), keeps=masks)[0]
         lm = _loss_run(perturbed(p, -h), keeps=masks)[0]
         fd = (lp - lm) / (2 * h)
+        assert abs(grad[p] - fd) <= 1e-6 * max(1.0, abs(fd)), (p, grad[p], fd)
+
+
+def test_adjoint_population_cotangents_match_finite_differences():
+    """Loss sum_k sum_s a_ks P_s(t_k)^2 of the site populations after every
+    step: the P_s cotangent 2 c_i dL/dP_s of the adjoint against central
+    differences of the replayed map (extension; parity pinned by FD)."""
+    eps = W.seeded_normal(3, 11) * 0.3
+    base = (0.5, 0.9, 1.0, eps)
+    a = W.seeded_normal(12 * 3, 12).reshape(12, 3)
+    _, o, masks, _, _, Ps = _loss_run(base, record=True)
+    grad = o.backward(len(Ps), dL_dP=2.0 * a * Ps)
+    assert sum(m is not None and (~m).any() for m in masks) > 3
+
+    def loss(params):
+        Ps = _loss_run(params, keeps=masks)[5]
+        return float(np.sum(a * Ps * Ps))
+
+    J, g, w, e = base
+    for p in range(3 + 3):
+        h = 1e-5
+        vals = []
+        for sgn in (1, -1):
+            q = [J, g, w, e.copy()]
+            if p < 3:
+                q[p] += sgn * h
+            else:
+                q[3][p - 3] += sgn * h
+            vals.append(loss(tuple(q)))
+        fd = (vals[0] - vals[1]) / (2 * h)
         assert abs(grad[p] - fd) <= 1e-6 * max(1.0, abs(fd)), (p, grad[p], fd)
