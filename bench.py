@@ -115,6 +115,18 @@ def dist_setup():
     return ws, rank, local
 
 
+def reduce_over_ranks(dist, ms, units, t_host, all_units, device):
+    """Replicas: the slowest rank's times and the sum of all ranks' units."""
+    if dist is None:
+        return ms, units, t_host, all_units
+    import torch
+    tt = torch.tensor([ms, units, t_host, all_units], dtype=torch.float64, device=device)
+    mx = tt.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(tt, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(tt[1]), float(mx[2]), float(tt[3])
+
+
 def sol_precision(model):
     return {0: "dw", 1: "c128", 2: "c64"}[int(model.get("precision", 0))]
 
@@ -150,10 +162,17 @@ def traffic_from_profile(kernel_src, end_step):
         return None
 
 
+def oracle_model(cfg):
+    """The oracle's model: one realisation (the first) of an ensemble."""
+    if "realisations" in cfg:
+        return W.model_kwargs(cfg, eps=W.realisation_eps(cfg, 0))
+    return W.model_kwargs(cfg)
+
+
 def cpu_baseline(cfg, budget_s=15.0, max_steps=None):
     """The oracle as it stands on this host: steps from psi(0) until the budget."""
     from oracle.oracle import Oracle
-    o = Oracle(**W.model_kwargs(cfg))
+    o = Oracle(**oracle_model(cfg))
     o.set_state(*W.start_state(cfg))
     units = 0.0
     steps = 0
@@ -169,6 +188,107 @@ def cpu_baseline(cfg, budget_s=15.0, max_steps=None):
     return units / el, steps, el, int(st["rows"])
 
 
+def ensemble_model(cfg, realisations=None):
+    """Model keyword arguments; a disorder ensemble gets batch R and its eps table."""
+    model = W.model_kwargs(cfg)
+    if "realisations" in cfg:
+        R = int(realisations or cfg["realisations"])
+        model["batch"] = R
+        model["eps"] = np.stack([W.realisation_eps(cfg, r) for r in range(R)])
+    return model
+
+
+def run_trajectory(B, model, cfg, start_state, end, first_timed, K, barrier, clk=None):
+    """set_state, then `end` steps one at a time, each followed by the read-back
+    of its observables record; steps first_timed+1 .. first_timed+K are timed
+    with CUDA events on the solver's stream (stage timing on)."""
+    import torch
+    sol = B.Solver(**model)
+    stream = sol.stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    all_units = 0.0
+    barrier()
+    t_host0 = time.perf_counter()
+    sol.set_state(*start_state)
+    for k in range(end):
+        if k == first_timed:
+            barrier()
+            sol.profile(True)
+            sol.stage_stats(reset=True)
+            if clk is not None:
+                clk.__enter__()
+            e0.record(stream)
+        sol.step(cfg["dt"], 1, cfg["theta"])
+        r = sol.observables(sol.num_records() - 1, 1)[0]
+        all_units += r[9] * r[6]
+        if k + 1 == first_timed + K:
+            e1.record(stream)
+    barrier()
+    t_host = time.perf_counter() - t_host0
+    if clk is not None:
+        clk.__exit__(None, None, None)
+    sol.profile(False)
+    stage_ms, launches, stage_bytes = sol.stage_stats(reset=True)
+    return {"solver": sol, "ms": e0.elapsed_time(e1), "t_host": t_host, "all_units": all_units,
+            "rec": sol.observables(first_timed + 1, K), "stage_ms": stage_ms, "launches": launches,
+            "stage_bytes": stage_bytes}
+
+
+def observable_errors(B, rec, ref, N, R_rec=1, R_ref=1, r_rec=0, r_ref=0):
+    """Largest absolute differences of P_s, <n_j>, C, norm and energy between two
+    record blocks (realisation r of an ensemble block, or the single model)."""
+    a = B.records_dict(rec, N, R_rec)
+    b = B.records_dict(ref, N, R_ref)
+    pick = lambda d, key, R, r: d[key] if R == 1 else d[key][:, r]
+    Ca = a["C"] if R_rec == 1 else a["C_r"][:, r_rec]
+    Cb = b["C"] if R_ref == 1 else b["C_r"][:, r_ref]
+    out = {"P": float(np.max(np.abs(pick(a, "P", R_rec, r_rec) - pick(b, "P", R_ref, r_ref)))),
+           "nbar": float(np.max(np.abs(pick(a, "nbar", R_rec, r_rec) - pick(b, "nbar", R_ref, r_ref)))),
+           "C": float(np.max(np.abs(Ca - Cb)))}
+    if R_rec == 1 and R_ref == 1:
+        out["norm"] = float(np.max(np.abs(a["norm"] - b["norm"])))
+        out["energy"] = float(np.max(np.abs(a["energy"] - b["energy"])))
+    return out
+
+
+def compare_variants(B, args, cfg, model, start_state, end, first_timed, K, barrier, main):
+    """The plain FP64 single-instance form next to the measured one: throughput
+    over the same timed window and the largest observable differences."""
+    N = cfg["n_sites"]
+    units = lambda rec: float(np.sum(rec[:, 9] * rec[:, 6]))
+    out = {}
+    R = int(model.get("batch", 1))
+    if R == 1:
+        recs = {}
+        for name, p in (("c128", B.C128), ("c64", B.C64_SPMV), ("dw", B.DW)):
+            if p == model["precision"]:
+                recs[name] = main["rec"]
+                continue
+            run = run_trajectory(B, dict(model, precision=p), cfg, start_state, end, first_timed, K, barrier)
+            run["solver"].close()
+            recs[name] = run["rec"]
+            out[name] = {"value": units(run["rec"]) / (run["ms"] / 1e3), "ms_per_step": run["ms"] / K}
+        for name in ("dw", "c64"):
+            out.setdefault(name, {})["max_abs_err_vs_c128"] = observable_errors(B, recs[name], recs["c128"], N)
+        out["reference_form"] = "c128: plain FP64 single instance, same steps"
+        return out
+    # ensemble: single-instance FP64 runs of a sample of realisations
+    S = min(R, max(1, args.compare_sample))
+    tot_units, tot_ms, errs = 0.0, 0.0, []
+    for r in range(S):
+        m = dict(model, batch=1, eps=np.asarray(model["eps"])[r].copy(), precision=B.C128)
+        run = run_trajectory(B, m, cfg, start_state, end, first_timed, K, barrier)
+        run["solver"].close()
+        tot_units += units(run["rec"])
+        tot_ms += run["ms"]
+        errs.append(observable_errors(B, main["rec"], run["rec"], N, R_rec=R, R_ref=1, r_rec=r))
+    out["single_c128"] = {"value": tot_units / (tot_ms / 1e3), "ms_per_step_per_realisation": tot_ms / K / S,
+                          "sample": "realisations 0..%d, one solver each, run one after another" % (S - 1)}
+    out["max_abs_err_vs_single_c128"] = {k: max(e[k] for e in errs) for k in errs[0]}
+    out["reference_form"] = "c128: plain FP64 single instance per realisation"
+    return out
+
+
 def run_reference(args, cfg):
     ws, rank, _ = dist_setup()
     if rank != 0:
@@ -176,7 +296,7 @@ def run_reference(args, cfg):
     # W warm-up then K timed oracle steps, each a bounded sample: the trajectory
     # from psi(0) (the oracle cannot reach the GPU window in minutes)
     from oracle.oracle import Oracle
-    o = Oracle(**W.model_kwargs(cfg))
+    o = Oracle(**oracle_model(cfg))
     o.set_state(*W.start_state(cfg))
     for _ in range(args.warmup):
         o.step(cfg["dt"], cfg["theta"])
@@ -213,6 +333,10 @@ def main():
     ap.add_argument("--precision", default="dw", choices=["dw", "c128", "c64"])
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--realisations", type=int, default=0, help="ensemble size (0: the workload's)")
+    ap.add_argument("--compare", action="store_true",
+                    help="also time the plain FP64 single-instance form and report observable errors")
+    ap.add_argument("--compare-sample", type=int, default=4)
     args = ap.parse_args()
     cfg = W.CONFIGS[args.workload]
     if args.impl == "reference":
@@ -234,9 +358,10 @@ def main():
     K, Wm = args.steps, args.warmup
     end = args.end_step or cfg["nsteps"]
     start = max(0, end - K - Wm)
-    model = W.model_kwargs(cfg)
-    model["precision"] = {"dw": B.DW, "c128": B.C128, "c64": B.C64_SPMV}[args.precision]
-    sol = B.Solver(**model)
+    prec = {"dw": B.DW, "c128": B.C128, "c64": B.C64_SPMV}
+    model = ensemble_model(cfg, args.realisations)
+    model["precision"] = prec[args.precision]
+    R = int(model.get("batch", 1))
 
     def barrier():
         if dist is not None:
@@ -249,42 +374,14 @@ def main():
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
     site_p, occ_p = pin(site), pin(occ)
     amps_p = pin(np.stack([amps.real, amps.imag], 1).reshape(-1))
-    stream = sol.stream
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     first_timed = start + Wm
-    all_units = 0.0
-    barrier()
-    t_host0 = time.perf_counter()
-    sol.set_state(site_p, occ_p, amps_p[0::2] + 1j * amps_p[1::2])
     clk = ClockSampler(local)
-    for k in range(end):
-        if k == first_timed:
-            barrier()
-            sol.profile(True)
-            sol.stage_stats(reset=True)
-            clk.__enter__()
-            e0.record(stream)
-        sol.step(cfg["dt"], 1, cfg["theta"])
-        r = sol.observables(sol.num_records() - 1, 1)[0]
-        all_units += r[9] * r[6]
-    e1.record(stream)
-    barrier()
-    t_host = time.perf_counter() - t_host0
-    clk.__exit__(None, None, None)
-    sol.profile(False)
-    ms = e0.elapsed_time(e1)
-    stage_ms, launches, stage_bytes = sol.stage_stats(reset=True)
-    rec = sol.observables(first_timed + 1, K)
+    run = run_trajectory(B, model, cfg, (site_p, occ_p, amps_p[0::2] + 1j * amps_p[1::2]), end, first_timed, K,
+                         barrier, clk)
+    sol, ms, t_host, all_units, rec = run["solver"], run["ms"], run["t_host"], run["all_units"], run["rec"]
+    stage_ms, launches, stage_bytes = run["stage_ms"], run["launches"], run["stage_bytes"]
     units, tbytes, tflops = taylor_counts(rec, sol)
-    t_max = ms
-    total_units = units
-    if dist is not None:
-        tt = torch.tensor([ms, units, t_host, all_units], dtype=torch.float64, device="cuda")
-        mx = tt.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
-        t_max, total_units = float(mx[0]), float(tt[1])
-        t_host, all_units = float(mx[2]), float(tt[3])
+    t_max, total_units, t_host, all_units = reduce_over_ranks(dist, ms, units, t_host, all_units, "cuda")
     value = total_units / (t_max / 1e3)
 
     # roofline of the dominant kernel (the propagator), live CUDA events per launch
@@ -321,6 +418,11 @@ def main():
                "sample": "oracle steps 1..%d of %s from psi(0) (%.1f s, final rows %d)"
                          % (nst, args.workload, el, rows)}
 
+    variants = None
+    if args.compare:
+        sol.close()
+        variants = compare_variants(B, args, cfg, model, (site_p, occ_p, amps_p[0::2] + 1j * amps_p[1::2]), end,
+                                    first_timed, K, barrier, run)
     if rank == 0:
         q = rec[:, 6]
         line = {
@@ -347,6 +449,11 @@ def main():
                                       for n, b, m in zip(B.STAGES, stage_bytes, stage_ms)},
             "clocks": clk.summary(),
         }
+        if R > 1:
+            line["config"]["realisations"] = R
+            line["config"]["units"] = "rows of all realisations x Taylor terms"
+        if variants is not None:
+            line["variants"] = variants
         print(json.dumps(line))
     sol.close()
     if dist is not None:
