@@ -156,12 +156,13 @@ template <int W>
 __device__ __forceinline__ uint32_t insert_candidate(const DevModel* __restrict__ M, uint64_t* table, uint64_t slots,
                                                      const Key<W>& key, uint32_t c, const uint64_t* __restrict__ keys,
                                                      const uint32_t* __restrict__ meta, uint32_t lo, Counters* ctr,
-                                                     int step)
+                                                     int step, bool& resolved)
 {
     uint64_t h = key_hash<W>(key);
     uint64_t fp = fingerprint<W>(h);
     uint64_t mine = (fp << 32) | (uint64_t)(kCand | c);
     uint64_t pos = slot_home(h, slots);
+    resolved = false;
     for (uint32_t probe = 0; probe < kMaxProbe; ++probe) {
         uint64_t* sl = table + pos * Slot<W>::kWords;
         uint64_t tag = __ldcg(sl);
@@ -179,10 +180,9 @@ __device__ __forceinline__ uint32_t insert_candidate(const DevModel* __restrict_
                 int mv2 = (int)(c2 - p2 * (uint32_t)M->D);
                 Key<W> pk = load_key<W>(keys, lo + p2);
                 uint32_t pm = meta[lo + p2];
-                int s2 = meta_s(pm), ns2 = meta_ns(pm);
                 Key<W> k2;
                 int cid2;
-                if (apply_move<W>(M, pk, s2, ns2, mv2, k2, cid2) && key_eq<W>(k2, key)) {
+                if (apply_move<W>(M, pk, meta_s(pm), meta_ns(pm), mv2, k2, cid2) && key_eq<W>(k2, key)) {
                     atomicMin((unsigned long long*)sl, (unsigned long long)mine);
                     return (uint32_t)pos;
                 }
@@ -190,7 +190,10 @@ __device__ __forceinline__ uint32_t insert_candidate(const DevModel* __restrict_
                 bool eq = true;
 #pragma unroll
                 for (int i = 0; i < W; ++i) eq &= (__ldcg(sl + 1 + i) == key.w[i]);
-                if (eq) return (uint32_t)pos;
+                if (eq) {
+                    resolved = true;          // an existing row: return it
+                    return v;
+                }
             }
         }
         pos = slot_next(pos, slots);
@@ -232,9 +235,10 @@ __global__ void __launch_bounds__(kBlock) k_level_insert(const DevModel* __restr
         Key<W> child;
         int cid;
         uint32_t r = kNone;
+        bool res = false;
         if (apply_move<W>(M, k, meta_s(pm), meta_ns(pm), mv, child, cid))
-            r = insert_candidate<W>(M, table, slots, child, c, keys, meta, lo, ctr, step);
-        cand_slot[(uint64_t)p * D + mv] = r;
+            r = insert_candidate<W>(M, table, slots, child, c, keys, meta, lo, ctr, step, res);
+        cand_slot[(uint64_t)p * D + mv] = res ? (kCand | r) : r;
     }
 }
 
@@ -258,7 +262,8 @@ __global__ void __launch_bounds__(kBlock) k_level_flags(const DevModel* __restri
             int mv;
             cand_parent(M, c, lo0, p, mv);
             uint32_t sl = cand_slot[(uint64_t)p * D + mv];
-            if (sl != kNone) win = (uint32_t)table[(uint64_t)sl * Slot<W>::kWords] == (kCand | c);
+            // a candidate that met an existing row (kCand | row) is no winner: no probe
+            if (!(sl & kCand)) win = (uint32_t)table[(uint64_t)sl * Slot<W>::kWords] == (kCand | c);
         }
         unsigned bal = __ballot_sync(0xffffffffu, win);
         uint32_t w0 = base + (threadIdx.x & ~31u);
@@ -415,7 +420,7 @@ __global__ void __launch_bounds__(kBlock) k_csr_grp(const DevModel* __restrict__
                 if (row < lim) {
                     uint32_t sl = cand_slot[(uint64_t)row * D + mv];
                     if (sl != kNone) {
-                        colv = (uint32_t)table[(uint64_t)sl * Slot<W>::kWords];
+                        colv = (sl & kCand) ? (sl & ~kCand) : (uint32_t)table[(uint64_t)sl * Slot<W>::kWords];
                         found = true;
                     }
                 } else {
@@ -473,7 +478,7 @@ __global__ void __launch_bounds__(kBlock) k_csr(const DevModel* __restrict__ M, 
             int64_t r = -1;
             if (i < lim) {
                 uint32_t sl = cand_slot[(uint64_t)i * D + mv];
-                if (sl != kNone) r = (uint32_t)table[(uint64_t)sl * Slot<W>::kWords];
+                if (sl != kNone) r = (sl & kCand) ? (sl & ~kCand) : (uint32_t)table[(uint64_t)sl * Slot<W>::kWords];
             } else {
                 r = table_lookup<W>(table, slots, child);
             }
@@ -892,7 +897,8 @@ template <int W>
 static int csr_w(const Bufs& b, int gen, cudaStream_t st)
 {
 #define PACES_CSR_ARGS \
-    b.model, b.ctr, b.keys[gen], b.meta[gen], b.table[gen], b.table_slots, b.cand_slot, b.col, b.cid, b.cnt, b.diag
+    b.model, b.ctr, b.keys[gen], b.meta[gen], b.table[gen], b.table_slots, b.cand_slot, b.col, b.cid, b.cnt, \
+        b.diag
     if (b.D <= 4) k_csr_grp<W, 4><<<b.grid, kBlock, 0, st>>>(PACES_CSR_ARGS);
     else if (b.D <= 8) k_csr_grp<W, 8><<<b.grid, kBlock, 0, st>>>(PACES_CSR_ARGS);
     else if (b.D <= 16) k_csr_grp<W, 16><<<b.grid, kBlock, 0, st>>>(PACES_CSR_ARGS);

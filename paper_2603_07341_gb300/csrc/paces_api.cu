@@ -21,7 +21,7 @@ namespace {
 constexpr int kChunk = 8;                 // steps enqueued between error checks
 constexpr uint32_t kMinRows = 1u << 10;
 constexpr uint32_t kDefaultRows = 1u << 16;
-constexpr uint64_t kMaxRowsHard = (1ull << 31) - 1;
+constexpr uint64_t kMaxRowsHard = (1ull << 30) - 1;   // table slots (2 cap + 1) stay below 2^31
 
 struct Stage {
     enum { Trunc = 0, Expand = 1, Csr = 2, Taylor = 3, Obs = 4, Other = 5 };
@@ -374,7 +374,7 @@ void invalidate_graphs(paces_t h)
 paces_status grow(paces_t h, uint64_t want, uint32_t q, int vec)
 {
     uint64_t cur = h->cap_rows, base = std::max<uint64_t>(cur, kMinRows);
-    if (want > kMaxRowsHard) return fail(h, PACES_ERR_CAPACITY, "more rows than 32-bit row indices allow");
+    if (want > kMaxRowsHard) return fail(h, PACES_ERR_CAPACITY, "more than 2^30 - 1 rows (table slot indices use 31 bits)");
     uint64_t* sk = nullptr;
     double2* sv = nullptr;
     uint32_t* sm = nullptr;

@@ -27,7 +27,7 @@ struct Bufs {
     uint8_t* cid;                  // coefficient ids, row pitch P
     uint8_t* cnt;                  // entries per row
     double* diag;                  // diagonal per row
-    uint32_t* cand_slot;           // candidate -> table slot
+    uint32_t* cand_slot;           // candidate -> table slot, kCand | row (an existing row), or kNone
     uint32_t* from;                // adjoint re-runs: row -> row of the previous state (or kNone)
     void* terms;                   // adjoint re-runs: Taylor terms phi_1.. [n][row], 16 bytes each
     int term_max;                  // terms storable
