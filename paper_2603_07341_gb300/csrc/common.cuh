@@ -425,6 +425,24 @@ __device__ __forceinline__ uint32_t fingerprint(uint64_t h)
     return f == 0xFFFFFFFFu ? 0xFFFFFFFEu : f;
 }
 
+// 16-byte compare-and-swap (PTX atom.cas.b128, sm_90 and later) of an aligned
+// pair of words; returns the previous contents in old_lo, old_hi.
+__device__ __forceinline__ void cas128(uint64_t* p, uint64_t cmp_lo, uint64_t cmp_hi, uint64_t new_lo,
+                                       uint64_t new_hi, uint64_t& old_lo, uint64_t& old_hi)
+{
+    asm volatile(
+        "{\n\t"
+        ".reg .b128 d, b, c;\n\t"
+        "mov.b128 b, {%2, %3};\n\t"
+        "mov.b128 c, {%4, %5};\n\t"
+        "atom.global.cas.b128 d, [%6], b, c;\n\t"
+        "mov.b128 {%0, %1}, d;\n\t"
+        "}"
+        : "=l"(old_lo), "=l"(old_hi)
+        : "l"(cmp_lo), "l"(cmp_hi), "l"(new_lo), "l"(new_hi), "l"(p)
+        : "memory");
+}
+
 // Read-only lookup: row of key or -1.
 template <int W>
 __device__ __forceinline__ int64_t table_lookup(const uint64_t* __restrict__ table, uint64_t slots,

@@ -165,15 +165,36 @@ __device__ __forceinline__ uint32_t insert_candidate(const DevModel* __restrict_
     resolved = false;
     for (uint32_t probe = 0; probe < kMaxProbe; ++probe) {
         uint64_t* sl = table + pos * Slot<W>::kWords;
-        uint64_t tag = __ldcg(sl);
-        if (tag == kEmpty) {
-            unsigned long long old = atomicCAS((unsigned long long*)sl, kEmpty, mine);
-            if (old == kEmpty) return (uint32_t)pos;
-            tag = old;
+        uint64_t tag, kw = kEmpty;
+        if constexpr (W == 1) {
+            // a one-word slot is claimed with its key in one 16-byte atomic, so
+            // a later candidate of the same key compares the key in the slot
+            ulonglong2 s2 = __ldcg(reinterpret_cast<const ulonglong2*>(sl));
+            tag = s2.x;
+            kw = s2.y;
+            if (tag == kEmpty) {
+                uint64_t olo, ohi;
+                cas128(sl, kEmpty, kEmpty, mine, key.w[0], olo, ohi);
+                if (olo == kEmpty) return (uint32_t)pos;
+                tag = olo;
+                kw = ohi;
+            }
+        } else {
+            tag = __ldcg(sl);
+            if (tag == kEmpty) {
+                unsigned long long old = atomicCAS((unsigned long long*)sl, kEmpty, mine);
+                if (old == kEmpty) return (uint32_t)pos;
+                tag = old;
+            }
         }
         if ((tag >> 32) == fp) {
             uint32_t v = (uint32_t)tag;
-            if (v & kCand) {
+            if (W == 1 && (v & kCand) && kw != kEmpty) {
+                if (kw == key.w[0]) {
+                    atomicMin((unsigned long long*)sl, (unsigned long long)mine);
+                    return (uint32_t)pos;
+                }
+            } else if (v & kCand) {
                 // another candidate holds the slot: regenerate its key from its parent
                 uint32_t c2 = v & ~kCand;
                 uint32_t p2 = (uint32_t)udiv(c2, M->div_D);
@@ -312,9 +333,15 @@ __global__ void __launch_bounds__(kBlock) k_level_scatter(const DevModel* __rest
             store_key<W>(keys, row, child);
             meta[row] = child_meta<W>(M, k, pm, mv);
             uint64_t* sl = table + (uint64_t)cand_slot[(uint64_t)p * D + mv] * Slot<W>::kWords;
+            // the tag is rebuilt from the key's hash: a store, no read of the slot
+            const uint64_t tag = ((uint64_t)fingerprint<W>(key_hash<W>(child)) << 32) | (uint64_t)row;
+            if constexpr (W == 1) {
+                *reinterpret_cast<ulonglong2*>(sl) = make_ulonglong2(tag, child.w[0]);
+            } else {
 #pragma unroll
-            for (int w = 0; w < W; ++w) sl[1 + w] = child.w[w];
-            sl[0] = (sl[0] & 0xFFFFFFFF00000000ull) | (uint64_t)row;
+                for (int w = 0; w < W; ++w) sl[1 + w] = child.w[w];
+                sl[0] = tag;
+            }
             double2 a = make_double2(0.0, 0.0);
             int64_t orow = -1;
             if (old_table) {
