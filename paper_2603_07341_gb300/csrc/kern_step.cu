@@ -542,10 +542,22 @@ __device__ __forceinline__ void split_weight(double w, unsigned long long& hi, u
 }
 
 
+// Warp sum of x as limbs of 26, 26 and 12 bits through the integer warp-reduce
+// instruction (no limb sum can overflow 32 bits): three single-instruction
+// reductions instead of a ten-shuffle 64-bit tree, exact modulo 2^64.
+__device__ __forceinline__ unsigned long long warp_sum_limbs(unsigned long long x)
+{
+    const unsigned m26 = (1u << 26) - 1u;
+    unsigned long long s0 = __reduce_add_sync(0xffffffffu, (unsigned)(x & m26));
+    unsigned long long s1 = __reduce_add_sync(0xffffffffu, (unsigned)((x >> 26) & m26));
+    unsigned long long s2 = __reduce_add_sync(0xffffffffu, (unsigned)(x >> 52));
+    return s0 + (s1 << 26) + (s2 << 52);
+}
+
 // Rows are taken 32 at a time per warp.  P_s goes through atomics on the
 // warp's own shared row (contention only between lanes of one warp with the
-// same site); each <n_j> is a warp-wide integer shuffle sum, skipped when no
-// lane has phonons at site j.
+// same site); each <n_j> is a warp-wide integer sum (limb reductions),
+// skipped when no lane has phonons at site j.
 template <int W>
 __global__ void __launch_bounds__(kBlock) k_obs_accum(const DevModel* __restrict__ M, Counters* ctr,
                                                       const uint64_t* __restrict__ keys,
@@ -600,7 +612,7 @@ __global__ void __launch_bounds__(kBlock) k_obs_accum(const DevModel* __restrict
                 unsigned long long nj = x - xq * M->div_radix[j].d;
                 x = xq;
                 if (__any_sync(0xffffffffu, nj != 0ull)) {
-                    unsigned long long a = warp_sum_u64(hi * nj), c = warp_sum_u64(lo * nj);
+                    unsigned long long a = warp_sum_limbs(hi * nj), c = warp_sum_limbs(lo * nj);
                     if (lane == 0) {
                         sh[warp][N + j][0] += a;
                         sh[warp][N + j][1] += c;
