@@ -202,6 +202,7 @@ struct DevModel {
     dwf eps_dw[kMaxSites];
     dwf omega_dw[kMaxSites];
     int uniform_omega;         // all omega_j equal (diagonal = eps_s + omega sum_j n_j)
+    int uniform_radix;         // all site radices equal (one divisor decodes every digit)
     int batch;                 // realisations R of an ensemble (1: one model)
     int batch_word;            // realisation digit: word, place value, radix
     UDiv div_batch_stride;

@@ -572,6 +572,12 @@ __global__ void __launch_bounds__(kBlock) k_obs_accum(const DevModel* __restrict
     const int fmt = M->fmt;
     const uint32_t q = ctr->q;
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    const bool uni = M->uniform_radix != 0;
+    const UDiv rd0 = M->div_radix[0];
+    const UDiv dexc = M->div_exc;
+    int wf[W + 1];
+#pragma unroll
+    for (int i = 0; i <= W; ++i) wf[i] = M->word_first[i];
     unsigned long long nh = 0, nl = 0;
     for (uint64_t rb = (uint64_t)gw * 32; rb < q; rb += (uint64_t)nw * 32) {
         uint64_t row = rb + lane;
@@ -596,30 +602,37 @@ __global__ void __launch_bounds__(kBlock) k_obs_accum(const DevModel* __restrict
             if (hi | lo) k = load_key<W>(keys, row);
         }
         bool live = (hi | lo) != 0ull;
-        uint64_t q0 = udiv(k.w[0], M->div_exc);
-        int s = (int)(k.w[0] - q0 * M->div_exc.d);
+        uint64_t q0 = udiv(k.w[0], dexc);
+        int s = (int)(k.w[0] - q0 * dexc.d);
         if (live) {
             atomicAdd(&sh[warp][s][0], hi);
             atomicAdd(&sh[warp][s][1], lo);
         }
         nh += hi;
         nl += lo;
+        // every phonon digit, with the divisor held in registers when all
+        // sites share one radix
+        auto digits = [&](auto radix_of) {
 #pragma unroll
-        for (int wd = 0; wd < W; ++wd) {
-            uint64_t x = (wd == 0) ? q0 : k.w[wd];
-            for (int j = M->word_first[wd]; j < M->word_first[wd + 1]; ++j) {
-                uint64_t xq = udiv(x, M->div_radix[j]);
-                unsigned long long nj = x - xq * M->div_radix[j].d;
-                x = xq;
-                if (__any_sync(0xffffffffu, nj != 0ull)) {
-                    unsigned long long a = warp_sum_limbs(hi * nj), c = warp_sum_limbs(lo * nj);
-                    if (lane == 0) {
-                        sh[warp][N + j][0] += a;
-                        sh[warp][N + j][1] += c;
+            for (int wd = 0; wd < W; ++wd) {
+                uint64_t x = (wd == 0) ? q0 : k.w[wd];
+                for (int j = wf[wd]; j < wf[wd + 1]; ++j) {
+                    const UDiv& dv = radix_of(j);
+                    uint64_t xq = udiv(x, dv);
+                    unsigned long long nj = x - xq * dv.d;
+                    x = xq;
+                    if (__any_sync(0xffffffffu, nj != 0ull)) {
+                        unsigned long long a = warp_sum_limbs(hi * nj), c = warp_sum_limbs(lo * nj);
+                        if (lane == 0) {
+                            sh[warp][N + j][0] += a;
+                            sh[warp][N + j][1] += c;
+                        }
                     }
                 }
             }
-        }
+        };
+        if (uni) digits([&](int) -> const UDiv& { return rd0; });
+        else digits([&](int j) -> const UDiv& { return M->div_radix[j]; });
     }
     nh = warp_sum_u64(nh);
     nl = warp_sum_u64(nl);

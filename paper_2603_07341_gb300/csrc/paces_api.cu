@@ -702,6 +702,8 @@ paces_status paces::fill_model(const paces_params* params, const paces_layout& L
     }
     M->uniform_omega = 1;
     for (int j = 1; j < N; ++j) M->uniform_omega &= (M->omega[j] == M->omega[0]);
+    M->uniform_radix = 1;
+    for (int j = 1; j < N; ++j) M->uniform_radix &= (L.site_radix[j] == L.site_radix[0]);
     M->batch = params->batch > 1 ? params->batch : 1;
     M->batch_word = L.batch_word;
     M->div_batch_stride = make_udiv(L.batch_stride);
