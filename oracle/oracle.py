@@ -56,6 +56,10 @@ def _load():
         lib.or_get_hopping.argtypes = [P, dp]
         lib.or_set_state.argtypes = [P, C.c_int, ip, ip, dp]
         lib.or_step.argtypes = [P, C.c_double, C.c_double, C.POINTER(C.c_ubyte), C.c_int]
+        lib.or_step_nom.argtypes = [P, C.c_double, C.c_longlong, C.c_ulonglong]
+        lib.or_nom_keep.argtypes = [P, C.c_longlong, C.c_ulonglong, C.POINTER(C.c_ubyte)]
+        lib.or_tie_hash.restype = C.c_ulonglong
+        lib.or_tie_hash.argtypes = [C.c_ulonglong, C.c_longlong, C.POINTER(C.c_int), C.c_int]
         lib.or_nrows.argtypes = [P]
         lib.or_get_rows.argtypes = [P, ip, dp]
         lib.or_level_offsets.argtypes = [P, ip, C.c_int]
@@ -143,6 +147,25 @@ class Oracle:
         rc = self._lib.or_step(self._h, float(dt), float(theta), kp, kl)
         if rc:
             raise OracleError(rc, "or_step")
+
+    def step_nom(self, dt, q_nom, seed=0):
+        """One step with top-q_nom truncation (seeded tie-break of equal weights)."""
+        rc = self._lib.or_step_nom(self._h, float(dt), int(q_nom), int(seed) & ((1 << 64) - 1))
+        if rc:
+            raise OracleError(rc, "or_step_nom")
+
+    def nom_keep(self, q_nom, seed=0):
+        """Keep mask a top-q_nom step would apply to the current rows."""
+        out = np.zeros(max(self.nrows(), 1), dtype=np.uint8)
+        rc = self._lib.or_nom_keep(self._h, int(q_nom), int(seed) & ((1 << 64) - 1),
+                                   out.ctypes.data_as(C.POINTER(C.c_ubyte)))
+        if rc:
+            raise OracleError(rc, "or_nom_keep")
+        return out[: self.nrows()].astype(bool)
+
+    def tie_hash(self, seed, t, tuple_):
+        a = np.ascontiguousarray(tuple_, dtype=np.int32)
+        return int(self._lib.or_tie_hash(int(seed) & ((1 << 64) - 1), int(t), _ip(a), len(a)))
 
     def nrows(self):
         return self._lib.or_nrows(self._h)

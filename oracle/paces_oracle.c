@@ -154,6 +154,7 @@ struct oracle {
     cplx* c;             /* amplitudes on rows                    */
     int ccap;
     int fresh;           /* set_state done, first step not yet    */
+    int tstep;           /* steps taken since set_state           */
     int* lvl;            /* BFS level offsets                     */
     int nlvl, lvlcap;
     unsigned char* keep; /* last truncation mask                  */
@@ -412,6 +413,7 @@ int or_set_state(oracle_t* o, int n, const int* site, const int* occ, const doub
     if (ensure_c(o, o->rows.nrows)) return OR_NOMEM;
     for (int i = n; i < o->rows.nrows; ++i) o->c[i] = 0.0;
     o->fresh = 1;
+    o->tstep = 0;
     o->time = 0.0;
     free_recs(o);
     memset(o->st, 0, sizeof(o->st));
@@ -618,6 +620,7 @@ int or_step(oracle_t* o, double dt, double theta, const unsigned char* keep_over
     }
     o->time += dt;
     o->fresh = 0;
+    o->tstep += 1;
     observe(o);
     o->st[OR_ST_NORM_PHI0] = n0;
     o->st[OR_ST_ENERGY] = energy;
@@ -655,6 +658,90 @@ int or_last_keep(const oracle_t* o, unsigned char* keep, int max)
 }
 
 void or_stats(const oracle_t* o, double* st) { memcpy(st, o->st, sizeof(o->st)); }
+
+/* ------------------------------------------------------------------ top-q_nom
+ *
+ * Truncation to the q_nom basis states of largest weight w = re^2 + im^2 (the
+ * paper's scheme: Sec. "Truncation & post-adaptation detruncation"; App. "How
+ * to weight states for truncation").  The appendix warns that degenerate
+ * weights cut in a fixed order bias the result and recommends randomising the
+ * order of degenerate states at the cutoff.  Reading taken here: among equal
+ * weights, states are ordered by a key
+ *     tk = (u with its low 32 bits cleared) | (0xFFFFFFFF - row),
+ * u = a counter-based hash of (seed, t, s, n_0, .., n_{N-1}):
+ *     z = seed + G t,  z = mix(z xor v) for v = s, n_0, .., n_{N-1},  u = z,
+ * with G = 0x9E3779B97F4A7C15 and mix the output function of SplitMix64
+ * (Steele, Lea & Flood 2014), and t = 1 + the number of steps since
+ * set_state.  Larger (w, tk) is kept first; tk is unique (it holds the row),
+ * so exactly q_nom rows are kept whenever q > q_nom. */
+static unsigned long long mix64(unsigned long long x)
+{
+    x += 0x9E3779B97F4A7C15ULL;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBULL;
+    return x ^ (x >> 31);
+}
+
+unsigned long long or_tie_hash(unsigned long long seed, long long t, const int* tuple, int len)
+{
+    unsigned long long z = seed + 0x9E3779B97F4A7C15ULL * (unsigned long long)t;
+    for (int i = 0; i < len; ++i) z = mix64(z ^ (unsigned long long)(unsigned)tuple[i]);
+    return z;
+}
+
+typedef struct {
+    double w;
+    unsigned long long tk;
+    int row;
+} nom_item;
+
+static int nom_cmp(const void* a, const void* b)
+{
+    const nom_item* x = (const nom_item*)a;
+    const nom_item* y = (const nom_item*)b;
+    if (x->w != y->w) return x->w > y->w ? -1 : 1;
+    if (x->tk != y->tk) return x->tk > y->tk ? -1 : 1;
+    return 0;
+}
+
+int or_nom_keep(const oracle_t* o, long long q_nom, unsigned long long seed, unsigned char* keep)
+{
+    int q = o->rows.nrows;
+    if (q_nom < 0) return OR_INVALID;
+    if ((long long)q <= q_nom) {
+        for (int i = 0; i < q; ++i) keep[i] = 1;
+        return OR_OK;
+    }
+    nom_item* it = (nom_item*)malloc(sizeof(nom_item) * ((size_t)q + 1));
+    if (!it) return OR_NOMEM;
+    long long t = (long long)o->tstep + 1;
+    for (int i = 0; i < q; ++i) {
+        double re = creal(o->c[i]), im = cimag(o->c[i]);
+        unsigned long long u = or_tie_hash(seed, t, rs_row(&o->rows, i), o->len);
+        it[i].w = re * re + im * im;
+        it[i].tk = (u & 0xFFFFFFFF00000000ULL) | (0xFFFFFFFFULL - (unsigned long long)(unsigned)i);
+        it[i].row = i;
+    }
+    qsort(it, (size_t)q, sizeof(nom_item), nom_cmp);
+    for (int i = 0; i < q; ++i) keep[i] = 0;
+    for (long long i = 0; i < q_nom; ++i) keep[it[i].row] = 1;
+    free(it);
+    return OR_OK;
+}
+
+int or_step_nom(oracle_t* o, double dt, long long q_nom, unsigned long long seed)
+{
+    if (!o || (o->rows.nrows == 0 && !o->fresh)) return OR_STATE;
+    if (q_nom < 0) return OR_INVALID;
+    if (o->fresh) return or_step(o, dt, 0.0, NULL, 0);
+    int q = o->rows.nrows;
+    unsigned char* keep = (unsigned char*)malloc((size_t)q + 1);
+    if (!keep) return OR_NOMEM;
+    int rc = or_nom_keep(o, q_nom, seed, keep);
+    if (rc == OR_OK) rc = or_step(o, dt, 0.0, keep, q);
+    free(keep);
+    return rc;
+}
 
 /* ------------------------------------------------------------------ adjoint
  *

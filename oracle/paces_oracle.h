@@ -47,6 +47,15 @@ int or_set_state(oracle_t* o, int n, const int* site, const int* occ, const doub
 int or_step(oracle_t* o, double dt, double theta, const unsigned char* keep_override,
             int keep_len);
 
+/* One time step with top-q_nom truncation (the q_nom rows of largest weight,
+ * degenerate weights ordered by a seeded counter-based hash; see
+ * paces_oracle.c).  The first step after set_state does not truncate. */
+int or_step_nom(oracle_t* o, double dt, long long q_nom, unsigned long long seed);
+/* The keep mask that step would use on the current rows (keep[nrows]). */
+int or_nom_keep(const oracle_t* o, long long q_nom, unsigned long long seed, unsigned char* keep);
+/* The tie-break hash u of a tuple (s, n_0..n_{N-1}) at step index t. */
+unsigned long long or_tie_hash(unsigned long long seed, long long t, const int* tuple, int len);
+
 int or_nrows(const oracle_t* o);
 /* tuples[nrows*(N+1)] as (s, n_0..n_{N-1}); amps[2*nrows] */
 void or_get_rows(const oracle_t* o, int* tuples, double* amps);

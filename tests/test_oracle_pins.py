@@ -402,3 +402,81 @@ def test_adjoint_population_cotangents_match_finite_differences():
             vals.append(loss(tuple(q)))
         fd = (vals[0] - vals[1]) / (2 * h)
         assert abs(grad[p] - fd) <= 1e-6 * max(1.0, abs(fd)), (p, grad[p], fd)
+
+
+# ---------------------------------------------------------------- top-q_nom truncation
+def test_tie_hash_mixer_is_splitmix64():
+    """The tie-break hash folds the SplitMix64 output function (Steele, Lea &
+    Flood 2014): checked against the separately written generator of the
+    workload module."""
+    o = Oracle(2, W.RING, J=1.0, cap=1, m=1, m_init=0)
+    for seed in (0, 1, 12345, (1 << 64) - 7):
+        assert o.tie_hash(seed, 0, [0]) == W.SplitMix64(seed).next_u64()
+        a, b = 3, 11
+        inner = W.SplitMix64(seed ^ a).next_u64()
+        assert o.tie_hash(seed, 0, [a, b]) == W.SplitMix64(inner ^ b).next_u64()
+    g = 0x9E3779B97F4A7C15
+    assert o.tie_hash(5, 3, [2]) == W.SplitMix64(((5 + 3 * g) & ((1 << 64) - 1)) ^ 2).next_u64()
+
+
+def _basis(nstates, N=4, cap=3):
+    """The first nstates tuples of an enumeration of the ring basis."""
+    out = []
+    for s in range(N):
+        for occ in np.ndindex(*([cap + 1] * N)):
+            out.append((s,) + occ)
+            if len(out) == nstates:
+                return np.array(out, dtype=np.int32)
+    return np.array(out, dtype=np.int32)
+
+
+def test_top_q_keeps_the_heaviest_rows():
+    tup = _basis(40)
+    amp = W.seeded_normal(80, 91).reshape(40, 2) @ np.array([1.0, 1j])
+    o = Oracle(4, W.RING, J=1.0, g=1.0, cap=3, m=1, m_init=0)
+    o.set_state(tup[:, 0], tup[:, 1:], amp)
+    t, a = o.rows()
+    w = a.real * a.real + a.imag * a.imag
+    assert len(np.unique(w)) == len(w)
+    for q_nom in (1, 7, 25, 39):
+        keep = o.nom_keep(q_nom)
+        cut = np.sort(w)[::-1][q_nom - 1]
+        assert np.array_equal(keep, w >= cut), q_nom
+    assert o.nom_keep(40).all() and o.nom_keep(1000).all()
+
+
+def test_top_q_tie_break_is_unbiased():
+    """Eight states of exactly equal weight compete for two places: over 400
+    seeds each is kept about 100 times (App. D: randomise degenerate states at
+    the cutoff), and the four heavier states are always kept."""
+    tup = _basis(12)
+    amp = np.concatenate([np.full(4, 0.4), np.full(8, 0.1)]).astype(np.complex128)
+    o = Oracle(4, W.RING, J=1.0, g=1.0, cap=3, m=1, m_init=0)
+    o.set_state(tup[:, 0], tup[:, 1:], amp)
+    t, a = o.rows()
+    heavy = np.abs(a) > 0.2
+    counts = np.zeros(len(a))
+    for seed in range(400):
+        keep = o.nom_keep(6, seed)
+        assert keep.sum() == 6 and keep[heavy].all()
+        counts += keep
+    tied = counts[~heavy]
+    assert np.all((tied >= 60) & (tied <= 140)), tied
+    assert tied.sum() == 800
+
+
+def test_step_nom_equals_the_same_mask_as_override():
+    cfg = W.CONFIGS["ring4"]
+    mk = lambda: Oracle(**W.model_kwargs(cfg))
+    a, b = mk(), mk()
+    for o in (a, b):
+        o.set_state(*W.start_state(cfg))
+        o.step(0.1, 0.0)
+    for k in range(6):
+        keep = b.nom_keep(60, 77)
+        a.step_nom(0.1, 60, 77)
+        b.step(0.1, 0.0, keep=keep.astype(np.uint8))
+        ta, ca = a.rows()
+        tb, cb = b.rows()
+        assert np.array_equal(ta, tb) and np.array_equal(ca, cb)
+        assert a.stats()["kept"] == 60
