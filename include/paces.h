@@ -203,6 +203,25 @@ paces_status paces_load_state(paces_t h, int64_t n, const int32_t* site, const i
  * propagates it without truncating again), CAPACITY or CUDA. */
 paces_status paces_step(paces_t h, double dt, int64_t nsteps, double theta);
 
+/* As paces_step, with the paper's own truncation (Sec. "Truncation &
+ * post-adaptation detruncation"; App. "How to weight states for truncation"):
+ * keep the q_nom (>= 1) rows of largest weight w = re^2 + im^2 (all rows when
+ * q <= q_nom), then regrow and rescue as usual, so H_eff has q_true >= q_nom
+ * rows.  w is compared as FP64 (PACES_C128: products and sum rounded
+ * separately; double-word storage: the double-word |c|^2 rounded to FP64).
+ * Degenerate weights at the cutoff are ordered by
+ *   tk = (u & 0xFFFFFFFF00000000) | (0xFFFFFFFF - row),
+ * u = the hash of (seed, t, s, n_0 .. n_{N-1}): z = seed + G t, then
+ * z = mix(z ^ v) for each entry v in that order, with mix the SplitMix64
+ * output function (Steele, Lea & Flood 2014), G = 0x9E3779B97F4A7C15 and t
+ * the index of the observables record the step writes (1 for the first step
+ * after paces_set_state); larger (w, tk) is kept first, so exactly q_nom rows
+ * are kept when q > q_nom.  The selection runs on the device (radix select of
+ * the weight bits, then of the tie keys of the rows at the cut weight).  The
+ * record's KEPT field holds |M| and ROWS holds q_true.  Returns as paces_step,
+ * and UNSUPPORTED for ensembles (batch > 1). */
+paces_status paces_step_nom(paces_t h, double dt, int64_t nsteps, int64_t q_nom, uint64_t seed);
+
 /* Number of rows q = dim H_eff of the current state. */
 paces_status paces_num_rows(paces_t h, int64_t* rows);
 

@@ -30,6 +30,7 @@ EXPORTED = (
     "paces_get_levels", "paces_get_keep", "paces_get_hamiltonian", "paces_record_len",
     "paces_num_records", "paces_observables", "paces_profile", "paces_stage_stats",
     "paces_expand_noalloc", "paces_get_tuning", "paces_set_tuning", "paces_record", "paces_backward",
+    "paces_step_nom",
 )
 
 
@@ -106,6 +107,8 @@ def load():
         getattr(lib, fn).argtypes = [P, C.c_int64, ip, ip, dp]
     lib.paces_step.restype = S
     lib.paces_step.argtypes = [P, C.c_double, C.c_int64, C.c_double]
+    lib.paces_step_nom.restype = S
+    lib.paces_step_nom.argtypes = [P, C.c_double, C.c_int64, C.c_int64, C.c_uint64]
     lib.paces_num_rows.restype = S
     lib.paces_num_rows.argtypes = [P, i64p]
     lib.paces_get_state.restype = S
@@ -308,6 +311,11 @@ class Solver:
 
     def step(self, dt, nsteps=1, theta=0.0):
         self._check(self._lib.paces_step(self._h, float(dt), int(nsteps), float(theta)), "step")
+
+    def step_nom(self, dt, nsteps=1, q_nom=1, seed=0):
+        """Steps with top-q_nom truncation (the paper's scheme; seeded tie-break)."""
+        self._check(self._lib.paces_step_nom(self._h, float(dt), int(nsteps), int(q_nom),
+                                             int(seed) & ((1 << 64) - 1)), "step_nom")
 
     def num_rows(self):
         n = C.c_int64()

@@ -15,15 +15,6 @@ namespace paces {
 
 // Contiguous chunk of [0, n) for block b of G, aligned to the block size so
 // that 32-row bitmask words never straddle chunks.
-__device__ __forceinline__ void chunk_of(uint32_t n, uint32_t G, uint32_t b, uint32_t& lo, uint32_t& hi)
-{
-    uint32_t c = (n + G - 1) / G;
-    c = (c + kBlock - 1) / kBlock * kBlock;
-    uint64_t l = (uint64_t)b * c;
-    lo = (uint32_t)(l < n ? l : n);
-    uint64_t h = l + c;
-    hi = (uint32_t)(h < n ? h : n);
-}
 
 
 // ---------------------------------------------------------------- insert rows
@@ -918,9 +909,10 @@ __global__ void k_export_csr(const DevModel* __restrict__ M, uint32_t q, const u
 
 // ---------------------------------------------------------------- launchers
 template <int W>
-static int trunc_w(const Bufs& b, int gin, int gout, double th2, int step, cudaStream_t st)
+static int trunc_w(const Bufs& b, int gin, int gout, double th2, int step, cudaStream_t st, bool counted = false)
 {
-    k_trunc_count<<<b.G, kBlock, 0, st>>>(b.V[0], b.ctr, th2, dw_from_double(th2), b.fmt, b.keepw, b.blk_cnt);
+    if (!counted)
+        k_trunc_count<<<b.G, kBlock, 0, st>>>(b.V[0], b.ctr, th2, dw_from_double(th2), b.fmt, b.keepw, b.blk_cnt);
     k_scan<<<1, 1024, 0, st>>>(b.blk_cnt, b.blk_off, b.G, b.ctr, kScanTrunc, 0, b.cap_rows, step);
     k_trunc_scatter<W><<<b.G, kBlock, 0, st>>>(b.keys[gin], b.V[0], b.ctr, b.keepw, b.blk_off, b.keys[gout],
                                                b.V[1], b.table[gout], b.table_slots, b.meta[gin], b.meta[gout], b.from,
@@ -1006,6 +998,13 @@ int launch_insert_rows(const Bufs& b, int gen, uint32_t n, cudaStream_t st)
 int launch_truncate(const Bufs& b, int gin, int gout, double th2, int step, cudaStream_t st)
 {
     PACES_DISPATCH_W(b.W, trunc_w<KW>(b, gin, gout, th2, step, st))
+}
+
+int launch_truncate_nom(const Bufs& b, int gin, int gout, uint64_t q_nom, uint64_t seed, int step, cudaStream_t st)
+{
+    int n = launch_topq_select(b, gin, q_nom, seed, st);
+    if (n < 0) return n;
+    PACES_DISPATCH_W(b.W, n - 1 + trunc_w<KW>(b, gin, gout, 0.0, step, st, true))
 }
 
 int launch_level(const Bufs& b, int gen, int f, int rescue_gen, int step, cudaStream_t st)

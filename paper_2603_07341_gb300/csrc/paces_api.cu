@@ -87,6 +87,8 @@ struct paces_handle {
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     bool gvalid[2] = {false, false};
     double g_dt = 0.0, g_th2 = -1.0;
+    int64_t g_nom = 0;
+    uint64_t g_seed = 0;
     int64_t graph_launches[PACES_NUM_STAGES + 1] = {0};
 
     // recording for the reverse pass: a checkpoint of the state every
@@ -102,6 +104,8 @@ struct paces_handle {
     bool rec_valid = false;
     int64_t rec_steps = 0, rec_base = 0;   // rec_base: record written by recorded step 0
     std::vector<double> rec_dt, rec_th2;
+    std::vector<int64_t> rec_nom;            // top-q_nom truncation (0: threshold)
+    std::vector<uint64_t> rec_seed;
     std::vector<Ckpt> ckpts;
 
     bool profiling = false;
@@ -485,7 +489,8 @@ cudaEvent_t ev(paces_t h, size_t i)
 // (fresh: the state set by set_state, no truncation).  Touches no host state
 // except launch counts, so it can be captured into a CUDA graph.  Returns the
 // output generation.  ev_base: first of 6 events (profiling only).
-int enqueue_kernels(paces_t h, cudaStream_t st, int gin, bool fresh, double dt, double th2, int step,
+int enqueue_kernels(paces_t h, cudaStream_t st, int gin, bool fresh, double dt, double th2, int64_t q_nom,
+                    uint64_t seed, int step,
                     bool prof, size_t ev_base)
 {
     const Bufs& b = h->b;
@@ -497,7 +502,8 @@ int enqueue_kernels(paces_t h, cudaStream_t st, int gin, bool fresh, double dt, 
     if (!fresh) {
         int gout = 1 - gin;
         cudaMemsetAsync(b.table[gout], 0xFF, b.table_slots * slot_words(h->W) * 8, st);
-        count(h, Stage::Trunc, launch_truncate(b, gin, gout, th2, step, st));
+        if (q_nom > 0) count(h, Stage::Trunc, launch_truncate_nom(b, gin, gout, (uint64_t)q_nom, seed, step, st));
+        else count(h, Stage::Trunc, launch_truncate(b, gin, gout, th2, step, st));
         mark(1);
         for (int f = 0; f < h->prm.m; ++f) count(h, Stage::Expand, launch_level(b, gout, f, gin, step, st));
         gen = gout;
@@ -514,14 +520,14 @@ int enqueue_kernels(paces_t h, cudaStream_t st, int gin, bool fresh, double dt, 
     return gen;
 }
 
-void enqueue_step(paces_t h, double dt, double th2, size_t ev_base)
+void enqueue_step(paces_t h, double dt, double th2, int64_t q_nom, uint64_t seed, size_t ev_base)
 {
     int step = (int)(h->step_index & 0x7fffffff);
     bool fresh = h->fresh;
     int gen = -1;
     if (!fresh && h->use_graphs && !h->profiling) {
         int gin = h->gen;
-        if (!h->gvalid[gin] || h->g_dt != dt || h->g_th2 != th2) {
+        if (!h->gvalid[gin] || h->g_dt != dt || h->g_th2 != th2 || h->g_nom != q_nom || h->g_seed != seed) {
             if (h->gexec[gin]) cudaGraphExecDestroy(h->gexec[gin]);
             h->gexec[gin] = nullptr;
             h->gvalid[gin] = false;
@@ -530,7 +536,7 @@ void enqueue_step(paces_t h, double dt, double th2, size_t ev_base)
             int64_t saved[PACES_NUM_STAGES + 1];
             std::memcpy(saved, h->stage_launch, sizeof(saved));
             bool ok = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-            if (ok) enqueue_kernels(h, h->cap_stream, gin, false, dt, th2, step, false, 0);
+            if (ok) enqueue_kernels(h, h->cap_stream, gin, false, dt, th2, q_nom, seed, step, false, 0);
             ok = cudaStreamEndCapture(h->cap_stream, &g) == cudaSuccess && ok;
             std::memcpy(h->graph_launches, h->stage_launch, sizeof(saved));
             for (int i = 0; i <= PACES_NUM_STAGES; ++i) h->graph_launches[i] -= saved[i];
@@ -545,6 +551,8 @@ void enqueue_step(paces_t h, double dt, double th2, size_t ev_base)
                 h->gvalid[gin] = true;
                 h->g_dt = dt;
                 h->g_th2 = th2;
+                h->g_nom = q_nom;
+                h->g_seed = seed;
             }
         }
         if (h->gvalid[gin]) {
@@ -553,7 +561,7 @@ void enqueue_step(paces_t h, double dt, double th2, size_t ev_base)
             gen = 1 - gin;
         }
     }
-    if (gen < 0) gen = enqueue_kernels(h, h->st, h->gen, fresh, dt, th2, step, h->profiling, ev_base);
+    if (gen < 0) gen = enqueue_kernels(h, h->st, h->gen, fresh, dt, th2, q_nom, seed, step, h->profiling, ev_base);
     h->last_truncated = !fresh;
     h->gen = gen;
     h->fresh = false;
@@ -569,6 +577,8 @@ void drop_recording(paces_t h)
     h->ckpts.clear();
     h->rec_dt.clear();
     h->rec_th2.clear();
+    h->rec_nom.clear();
+    h->rec_seed.clear();
     h->rec_steps = 0;
     h->rec_valid = h->rec_every > 0;
     h->rec_base = h->n_records;
@@ -852,6 +862,7 @@ paces_status paces_create(const paces_params* params, const paces_allocator* all
 
     b.model = alloc_track<DevModel>(h, h->fixed_allocs, 1);
     b.ctr = alloc_track<Counters>(h, h->fixed_allocs, 1);
+    b.topq = alloc_track<TopqState>(h, h->fixed_allocs, 1);
     b.blk_cnt = alloc_track<uint32_t>(h, h->fixed_allocs, kMaxChunkBlocks);
     b.blk_off = alloc_track<uint32_t>(h, h->fixed_allocs, kMaxChunkBlocks);
     b.partials = alloc_track<double>(h, h->fixed_allocs, 8 * (size_t)h->sms * std::max(bps, bps_max) + 16);
@@ -1112,12 +1123,10 @@ paces_status paces_load_state(paces_t h, int64_t n, const int32_t* site, const i
     return PACES_OK;
 }
 
-paces_status paces_step(paces_t h, double dt, int64_t nsteps, double theta)
+// The step driver shared by threshold truncation (q_nom = 0) and top-q_nom
+// truncation.
+static paces_status step_impl(paces_t h, double dt, int64_t nsteps, double th2, int64_t q_nom, uint64_t seed)
 {
-    if (!h) return PACES_ERR_INVALID;
-    if (!(dt > 0.0) || nsteps < 0 || !(theta >= 0.0)) return fail(h, PACES_ERR_INVALID, "dt, nsteps or theta");
-    if (!h->has_state) return fail(h, PACES_ERR_STATE, "no state: call paces_set_state first");
-    double th2 = theta * theta;
     int64_t done = 0;
     std::vector<double> hrec;
     paces_status s = ensure_obs(h, h->n_records + nsteps);
@@ -1138,7 +1147,7 @@ paces_status paces_step(paces_t h, double dt, int64_t nsteps, double theta)
         int g0 = h->gen;
         bool fresh0 = h->fresh;
         int64_t rec0 = h->n_records, step0 = h->step_index;
-        for (int k = 0; k < chunk; ++k) enqueue_step(h, dt, th2, (size_t)k * 6);
+        for (int k = 0; k < chunk; ++k) enqueue_step(h, dt, th2, q_nom, seed, (size_t)k * 6);
         CUDA_TRY(h, cudaGetLastError());
         s = read_counters(h);
         if (s) return s;
@@ -1173,6 +1182,8 @@ paces_status paces_step(paces_t h, double dt, int64_t nsteps, double theta)
                 h->rec_steps += chunk;
                 h->rec_dt.insert(h->rec_dt.end(), (size_t)chunk, dt);
                 h->rec_th2.insert(h->rec_th2.end(), (size_t)chunk, th2);
+                h->rec_nom.insert(h->rec_nom.end(), (size_t)chunk, q_nom);
+                h->rec_seed.insert(h->rec_seed.end(), (size_t)chunk, seed);
             }
             continue;
         }
@@ -1190,6 +1201,8 @@ paces_status paces_step(paces_t h, double dt, int64_t nsteps, double theta)
             h->rec_steps += fs;
             h->rec_dt.insert(h->rec_dt.end(), (size_t)fs, dt);
             h->rec_th2.insert(h->rec_th2.end(), (size_t)fs, th2);
+            h->rec_nom.insert(h->rec_nom.end(), (size_t)fs, q_nom);
+            h->rec_seed.insert(h->rec_seed.end(), (size_t)fs, seed);
         }
         if (err == kErrRows || err == kErrProbe || err == kErrCand) {
             // the failing step's input (generation gen, vector V0) is intact
@@ -1231,6 +1244,23 @@ paces_status paces_step(paces_t h, double dt, int64_t nsteps, double theta)
         return fail(h, PACES_ERR_CUDA, "device error code " + std::to_string(err));
     }
     return PACES_OK;
+}
+
+paces_status paces_step(paces_t h, double dt, int64_t nsteps, double theta)
+{
+    if (!h) return PACES_ERR_INVALID;
+    if (!(dt > 0.0) || nsteps < 0 || !(theta >= 0.0)) return fail(h, PACES_ERR_INVALID, "dt, nsteps or theta");
+    if (!h->has_state) return fail(h, PACES_ERR_STATE, "no state: call paces_set_state first");
+    return step_impl(h, dt, nsteps, theta * theta, 0, 0);
+}
+
+paces_status paces_step_nom(paces_t h, double dt, int64_t nsteps, int64_t q_nom, uint64_t seed)
+{
+    if (!h) return PACES_ERR_INVALID;
+    if (!(dt > 0.0) || nsteps < 0 || q_nom < 1) return fail(h, PACES_ERR_INVALID, "dt, nsteps or q_nom");
+    if (h->R > 1) return fail(h, PACES_ERR_UNSUPPORTED, "top-q_nom truncation covers batch 1 only");
+    if (!h->has_state) return fail(h, PACES_ERR_STATE, "no state: call paces_set_state first");
+    return step_impl(h, dt, nsteps, 0.0, q_nom, seed);
 }
 
 paces_status paces_num_rows(paces_t h, int64_t* rows)
@@ -1572,7 +1602,8 @@ paces_status paces_backward(paces_t h, int64_t nsteps, const double* dL_dc_final
             h->b.terms = terms;
             h->b.term_max = std::max(ntk[k] - 1, 0);
         }
-        gen = enqueue_kernels(h, h->st, h->gen, h->fresh, h->rec_dt[k], h->rec_th2[k], (int)k, false, 0);
+        gen = enqueue_kernels(h, h->st, h->gen, h->fresh, h->rec_dt[k], h->rec_th2[k], h->rec_nom[k], h->rec_seed[k],
+                              (int)k, false, 0);
         h->gen = gen;
         h->b.from = nullptr;
         h->b.terms = nullptr;

@@ -13,6 +13,31 @@ namespace paces {
 constexpr int kBlock = 256;        // threads of the chunked (scan-based) kernels
 constexpr int kMaxChunkBlocks = 1024;
 
+// Chunk [lo, hi) of n items owned by block b of G (multiples of kBlock), the
+// split every scan-based kernel of one pass shares.
+__device__ __forceinline__ void chunk_of(uint32_t n, uint32_t G, uint32_t b, uint32_t& lo, uint32_t& hi)
+{
+    uint32_t c = (n + G - 1) / G;
+    c = (c + kBlock - 1) / kBlock * kBlock;
+    uint64_t l = (uint64_t)b * c;
+    lo = (uint32_t)(l < n ? l : n);
+    uint64_t h = l + c;
+    hi = (uint32_t)(h < n ? h : n);
+}
+
+// Selection state of top-q_nom truncation (kern_topq.cu).
+struct TopqState {
+    unsigned long long prefix;     // bits chosen so far in the current phase
+    unsigned long long krem;       // rank still to place within the prefix
+    unsigned long long w_cut;      // weight bits of the cut
+    unsigned long long tk_cut;     // tie key of the cut (phase 1)
+    uint32_t all;                  // q <= q_nom: every row is kept
+    uint32_t phase;                // 0 weights, 1 tie keys, 2 done
+    uint32_t ties_all;             // every row of the cut weight is kept
+    uint32_t pad;
+    uint32_t hist[4096];
+};
+
 // Device buffers of one handle (all device pointers).
 struct Bufs {
     const DevModel* model;
@@ -36,6 +61,7 @@ struct Bufs {
     uint32_t* blk_cnt;             // chunk counts
     uint32_t* blk_off;             // chunk offsets
     double* partials;              // Taylor reduction partials [2][G][4]
+    TopqState* topq;               // top-q_nom selection state
     double* obs;                   // observables records
     unsigned long long* obs_part;  // observables partials [grid][2*kMaxSites+1][2]
     uint64_t* psi0_keys;
@@ -67,6 +93,11 @@ struct TaylorParams {
 // launch error, which the caller reads with cudaGetLastError).
 int launch_insert_rows(const Bufs& b, int gen, uint32_t n, cudaStream_t st);
 int launch_truncate(const Bufs& b, int gin, int gout, double th2, int step, cudaStream_t st);
+// Top-q_nom truncation: the selection writes the keep bits (kern_topq.cu), then
+// the compaction shared with threshold truncation.
+int launch_truncate_nom(const Bufs& b, int gin, int gout, uint64_t q_nom, uint64_t seed, int step,
+                        cudaStream_t st);
+int launch_topq_select(const Bufs& b, int gin, uint64_t q_nom, uint64_t seed, cudaStream_t st);
 int launch_level(const Bufs& b, int gen, int f, int rescue_gen, int step, cudaStream_t st);
 int launch_csr(const Bufs& b, int gen, cudaStream_t st);
 int launch_taylor(const Bufs& b, const TaylorParams& p, cudaStream_t st);
