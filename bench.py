@@ -38,6 +38,7 @@ sys.path.insert(0, ROOT)
 from paper_2603_07341_gb300 import workloads as W  # noqa: E402
 
 METRIC = "H-applied amplitudes/s"
+TIE_SEED = 2603073410                 # seed of the top-q_nom tie hash (workloads with q_nom)
 UNIT = "amplitudes/s"
 FALLBACK_HBM_GBS = 6800.0
 FP64_PEAK_TFLOPS = 1.25          # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal table)
@@ -169,6 +170,13 @@ def oracle_model(cfg):
     return W.model_kwargs(cfg)
 
 
+def oracle_step(o, cfg):
+    if "q_nom" in cfg:
+        o.step_nom(cfg["dt"], cfg["q_nom"], TIE_SEED)
+    else:
+        o.step(cfg["dt"], cfg["theta"])
+
+
 def cpu_baseline(cfg, budget_s=15.0, max_steps=None):
     """The oracle as it stands on this host: steps from psi(0) until the budget."""
     from oracle.oracle import Oracle
@@ -178,7 +186,7 @@ def cpu_baseline(cfg, budget_s=15.0, max_steps=None):
     steps = 0
     t0 = time.perf_counter()
     while True:
-        o.step(cfg["dt"], cfg["theta"])
+        oracle_step(o, cfg)
         st = o.stats()
         units += st["terms"] * st["rows"]
         steps += 1
@@ -218,7 +226,10 @@ def run_trajectory(B, model, cfg, start_state, end, first_timed, K, barrier, clk
             if clk is not None:
                 clk.__enter__()
             e0.record(stream)
-        sol.step(cfg["dt"], 1, cfg["theta"])
+        if "q_nom" in cfg:
+            sol.step_nom(cfg["dt"], 1, cfg["q_nom"], TIE_SEED)
+        else:
+            sol.step(cfg["dt"], 1, cfg["theta"])
         r = sol.observables(sol.num_records() - 1, 1)[0]
         all_units += r[9] * r[6]
         if k + 1 == first_timed + K:
@@ -299,11 +310,11 @@ def run_reference(args, cfg):
     o = Oracle(**oracle_model(cfg))
     o.set_state(*W.start_state(cfg))
     for _ in range(args.warmup):
-        o.step(cfg["dt"], cfg["theta"])
+        oracle_step(o, cfg)
     units = 0.0
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        o.step(cfg["dt"], cfg["theta"])
+        oracle_step(o, cfg)
         st = o.stats()
         units += st["terms"] * st["rows"]
     el = time.perf_counter() - t0

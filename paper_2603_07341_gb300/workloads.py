@@ -42,6 +42,13 @@ CONFIGS = {
                        J=1.0, omega=1.0, g=1.0, eps=0.0, cap=6, m=2, m_init=10,
                        dt=0.05, nsteps=2048, theta=1e-4, start="bright",
                        realisations=256, eps_sigma=0.5, seed0=1000),
+    # the paper's 1D Holstein benchmark at g = 4 (1D parameter table): open chain
+    # N = 25, d_pho = 64 (K = 63), J = omega = 1, m_init = 10, m = 2, dt = 0.05 to
+    # t = 50, top-q_nom truncation with q_nom = 32e6, a Franck-Condon excitation on
+    # the centre site
+    "chain25": dict(n_sites=25, lattice_kind=CHAIN, dims=(25, 1, 1), coupling_kind=NEAREST,
+                    J=1.0, omega=1.0, g=4.0, eps=0.0, cap=63, m=2, m_init=10,
+                    dt=0.05, nsteps=1000, theta=0.0, q_nom=32_000_000, start="center"),
     # 3D 4x4x4 open cube, nearest-neighbour J = 1, K = 4 -- the gradient workload.
     # theta = 1e-4 (1e-5 and 1e-6 outgrow one GPU before step 80)
     "cube4": dict(n_sites=64, lattice_kind=OPEN3D, dims=(4, 4, 4), coupling_kind=NEAREST,
@@ -69,9 +76,10 @@ def describe(cfg):
     geo = "x".join(str(d) for d in cfg["dims"] if d > 1) if cfg["lattice_kind"] in (OPEN2D, OPEN3D) \
         else "N=%d" % cfg["n_sites"]
     coup = "J0/r^3 all pairs" if cfg["coupling_kind"] == DIPOLAR else "nearest-neighbour"
-    return ("Holstein %s %s, %s J=%g omega=%g g=%g K=%d, dt=%g theta=%g, start %s"
+    trunc = ("q_nom=%d" % cfg["q_nom"]) if "q_nom" in cfg else ("theta=%g" % cfg["theta"])
+    return ("Holstein %s %s, %s J=%g omega=%g g=%g K=%d, dt=%g %s, start %s"
             % (kinds[cfg["lattice_kind"]], geo, coup, cfg["J"], cfg["omega"], cfg["g"], cfg["cap"],
-               cfg["dt"], cfg["theta"], cfg["start"]))
+               cfg["dt"], trunc, cfg["start"]))
 
 
 def start_state(cfg):
@@ -80,6 +88,9 @@ def start_state(cfg):
     kind = cfg["start"]
     if kind == "site0":
         return (np.zeros(1, dtype=np.int32), np.zeros((1, N), dtype=np.int32),
+                np.ones(1, dtype=np.complex128))
+    if kind == "center":        # |N // 2, vac>: a localised Franck-Condon excitation
+        return (np.array([N // 2], dtype=np.int32), np.zeros((1, N), dtype=np.int32),
                 np.ones(1, dtype=np.complex128))
     if kind == "bright":        # sum_s |s, vac> / sqrt(N)  (Eq. init_state_spec)
         return (np.arange(N, dtype=np.int32), np.zeros((N, N), dtype=np.int32),

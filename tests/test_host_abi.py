@@ -29,7 +29,7 @@ def test_library_exports_every_declared_symbol(libpaces):
 
 
 @pytest.mark.parametrize("name,words,pow2", [("ring4", 1, 1), ("ring16", 1, 0), ("dipolar6x6", 2, 1),
-                                             ("disorder12", 1, 1), ("cube4", 3, 0)])
+                                             ("disorder12", 1, 1), ("cube4", 3, 0), ("chain25", 3, 1)])
 def test_layout_word_counts(libpaces, name, words, pow2):
     """Dense mixed radix where a power-of-two field would cost an extra word
     (ring16: 16 log2 9 + 4 = 54.7 bits in one word; cube4: 154.6 bits in 3)."""

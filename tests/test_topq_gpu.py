@@ -155,3 +155,16 @@ def test_topq_invalid_arguments(libpaces):
     with pytest.raises(B.PacesError) as e:
         s.step_nom(0.02, 1, 100, 1)
     assert e.value.code == B.ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("precision", [B.C128, B.DW])
+def test_topq_paper_benchmark_chain_prefix(libpaces, precision):
+    """The paper's g = 4 benchmark shape (open chain N = 25, K = 63, three-word
+    keys) at a small q_nom: lockstep with the oracle over the first steps."""
+    cfg = W.CONFIGS["chain25"]
+    model = W.model_kwargs(cfg, m_init=4)
+    gpu = B.Solver(**model, precision=precision)
+    ora = Oracle(**model)
+    gpu.set_state(*W.start_state(cfg))
+    ora.set_state(*W.start_state(cfg))
+    _lockstep_nom(gpu, ora, cfg["dt"], 1500, 2603073410, 10)
