@@ -21,8 +21,10 @@
  *     no contraction (this file is compiled with -ffp-contract=off);
  *   - no truncation before the first propagation after set_state;
  *   - Taylor stops at the first n >= 2 with ||phi_n||^2 <= tol^2 ||r||^2;
- *   - move order (which fixes row order): hops to t = 0..N-1 ascending, then
- *     a_s^dag, then a_s; new states are appended in first-occurrence order.
+ *   - row order: the kept set M in ascending basis order (n_{N-1} most
+ *     significant, down to n_0, then s: the order of the paper's sorted key
+ *     array), then every BFS level in first-occurrence order under the move
+ *     order hops to t = 0..N-1 ascending, a_s^dag, a_s.
  *
  * Representation: a basis state is the int tuple (s, n_0, ..., n_{N-1}); rows
  * of H_eff are stored in order in a growable array with a linear-probing index.
@@ -546,6 +548,26 @@ void or_populations(const oracle_t* o, double* P, double* nbar)
     }
 }
 
+/* Sort row indices by basis state: n_{N-1} first, down to n_0, then s. */
+static const rowset* g_sort_rows;
+static int basis_cmp(const void* a, const void* b)
+{
+    const int* x = rs_row(g_sort_rows, *(const int*)a);
+    const int* y = rs_row(g_sort_rows, *(const int*)b);
+    int len = g_sort_rows->len;
+    for (int j = len - 1; j >= 1; --j)
+        if (x[j] != y[j]) return x[j] < y[j] ? -1 : 1;
+    if (x[0] != y[0]) return x[0] < y[0] ? -1 : 1;
+    return 0;
+}
+
+static void sort_rows_by_basis(const rowset* rows, int* idx, int n)
+{
+    g_sort_rows = rows;
+    qsort(idx, (size_t)n, sizeof(int), basis_cmp);     /* states are distinct: no ties */
+    g_sort_rows = NULL;
+}
+
 int or_step(oracle_t* o, double dt, double theta, const unsigned char* keep_override,
             int keep_len)
 {
@@ -568,15 +590,22 @@ int or_step(oracle_t* o, double dt, double theta, const unsigned char* keep_over
             double w = re * re + im * im;
             o->keep[i] = keep_override ? (keep_override[i] != 0) : (w >= th2);
         }
-        /* 2. M in row order, then regrow H_eff by m BFS levels */
+        /* 2. M in ascending basis order -- the tuple compared from n_{N-1}
+         *    down to n_0, then s -- the order of the paper's sorted key array;
+         *    then regrow H_eff by m BFS levels */
         rowset old = o->rows;
         cplx* cold = o->c;
         o->c = NULL;
         o->ccap = 0;
         rs_init(&o->rows, len);
         kept = 0;
+        int* mi = (int*)malloc(sizeof(int) * ((size_t)q_old + 1));
+        if (!mi) return OR_NOMEM;
         for (int i = 0; i < q_old; ++i)
-            if (o->keep[i]) { rs_add(&o->rows, rs_row(&old, i)); ++kept; }
+            if (o->keep[i]) mi[kept++] = i;
+        sort_rows_by_basis(&old, mi, kept);
+        for (int i = 0; i < kept; ++i) rs_add(&o->rows, rs_row(&old, mi[i]));
+        free(mi);
         int rc = expand(o, o->m);
         if (rc) return rc;
         /* 3. rescue: amplitudes of re-admitted states come back (detruncation) */

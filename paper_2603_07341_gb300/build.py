@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libpaces.so")
-SOURCES = ["paces_api.cu", "kern_step.cu", "kern_taylor.cu", "noalloc.cu", "kern_adjoint.cu", "kern_topq.cu"]
+SOURCES = ["paces_api.cu", "kern_step.cu", "kern_taylor.cu", "noalloc.cu", "kern_adjoint.cu", "kern_topq.cu", "kern_sort.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

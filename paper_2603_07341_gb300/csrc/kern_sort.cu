@@ -1,0 +1,201 @@
+// kern_sort.cu -- the kept set M in ascending basis order.
+//
+// After truncation the kept rows are compacted as (key, source row) pairs,
+// sorted by key with a stable least-significant-digit radix sort (8-bit
+// digits, only over the bits the key layout uses), and placed: keys, row
+// descriptors and amplitudes gathered from their source rows, and each row
+// inserted into the fresh table.  Ascending key order is ascending basis
+// order -- n_{N-1} most significant, down to n_0, then the exciton site --
+// which is the order of the paper's sorted key array (Sec. "Truncation &
+// post-adaptation detruncation" with the sort-and-search of its
+// implementation).  States that differ by an exciton hop are then neighbours
+// in M, and the regrown levels inherit that grouping from their parents, so
+// the propagator's gathers of neighbour amplitudes hit cache lines that are
+// already loaded.
+#include "runtime.h"
+
+namespace paces {
+
+namespace {
+constexpr int kDigits = 256;
+}
+
+// Kept rows as (key, source row) in row order (the scan of the keep bits).
+template <int W>
+__global__ void __launch_bounds__(kBlock) k_trunc_compact(const uint64_t* __restrict__ keys_in, Counters* ctr,
+                                                          const uint32_t* __restrict__ keepw,
+                                                          const uint32_t* __restrict__ blk_off,
+                                                          uint64_t* __restrict__ sk, uint32_t* __restrict__ si)
+{
+    if (ctr->err) return;
+    uint32_t q = ctr->q_in, lo, hi;
+    chunk_of(q, gridDim.x, blockIdx.x, lo, hi);
+    uint32_t run = blk_off[blockIdx.x];
+    for (uint32_t base = lo; base < hi; base += kBlock) {
+        uint32_t i = base + threadIdx.x;
+        uint32_t w0 = base + (threadIdx.x & ~31u);
+        uint32_t bal = (w0 < hi) ? keepw[w0 >> 5] : 0u;
+        bool keep = (i < hi) && ((bal >> (threadIdx.x & 31)) & 1u);
+        uint32_t tot;
+        uint32_t r = block_excl_scan<kBlock>(keep ? 1u : 0u, &tot);
+        if (keep) {
+            store_key<W>(sk, run + r, load_key<W>(keys_in, i));
+            si[run + r] = i;
+        }
+        run += tot;
+    }
+}
+
+// Digit counts of each block's chunk: hist[d * G + block].
+template <int W>
+__global__ void __launch_bounds__(kBlock) k_rs_hist(const Counters* __restrict__ ctr, const uint64_t* __restrict__ sk,
+                                                    int word, int shift, uint32_t* __restrict__ hist)
+{
+    __shared__ uint32_t h[kDigits];
+    if (ctr->err) return;
+    for (int d = threadIdx.x; d < kDigits; d += blockDim.x) h[d] = 0u;
+    __syncthreads();
+    uint32_t n = ctr->kept, lo, hi;
+    chunk_of(n, gridDim.x, blockIdx.x, lo, hi);
+    for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x)
+        atomicAdd(&h[(sk[(uint64_t)i * W + word] >> shift) & (kDigits - 1)], 1u);
+    __syncthreads();
+    for (int d = threadIdx.x; d < kDigits; d += blockDim.x) hist[(size_t)d * gridDim.x + blockIdx.x] = h[d];
+}
+
+// Exclusive scan of hist[0 .. kDigits * G) in place (digit-major, block-minor):
+// the first output position of every (digit, block).
+__global__ void __launch_bounds__(1024) k_rs_scan(const Counters* __restrict__ ctr, uint32_t* __restrict__ hist, int G)
+{
+    if (ctr->err) return;
+    const uint32_t n = (uint32_t)kDigits * (uint32_t)G;
+    const uint32_t per = (n + blockDim.x - 1) / blockDim.x;
+    const uint32_t a = threadIdx.x * per, b = min(n, a + per);
+    uint32_t s = 0;
+    for (uint32_t i = a; i < b; ++i) s += hist[i];
+    uint32_t tot;
+    uint32_t run = block_excl_scan<1024>(s, &tot);
+    for (uint32_t i = a; i < b; ++i) {
+        uint32_t v = hist[i];
+        hist[i] = run;
+        run += v;
+    }
+}
+
+// Stable scatter of one digit: each block walks its chunk in tiles of kBlock
+// items; the rank of an item among the equal digits before it is its rank in
+// its warp (match) plus the counts of the earlier warps of the tile plus the
+// items of the earlier tiles of the block.
+template <int W>
+__global__ void __launch_bounds__(kBlock) k_rs_scatter(const Counters* __restrict__ ctr,
+                                                       const uint64_t* __restrict__ kin, const uint32_t* __restrict__ iin,
+                                                       uint64_t* __restrict__ kout, uint32_t* __restrict__ iout,
+                                                       int word, int shift, const uint32_t* __restrict__ offs)
+{
+    static_assert(kBlock == kDigits, "one thread per digit in the per-tile prefix");
+    __shared__ uint32_t base[kDigits];
+    __shared__ uint32_t wc[kBlock / 32][kDigits];
+    if (ctr->err) return;
+    uint32_t n = ctr->kept, lo, hi;
+    chunk_of(n, gridDim.x, blockIdx.x, lo, hi);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    base[threadIdx.x] = offs[(size_t)threadIdx.x * gridDim.x + blockIdx.x];
+    for (uint32_t t0 = lo; t0 < hi; t0 += kBlock) {
+#pragma unroll
+        for (int w = 0; w < kBlock / 32; ++w) wc[w][threadIdx.x] = 0u;
+        __syncthreads();
+        const uint32_t i = t0 + threadIdx.x;
+        const bool valid = i < hi;
+        Key<W> k;
+#pragma unroll
+        for (int x = 0; x < W; ++x) k.w[x] = 0;
+        uint32_t idx = 0;
+        int d = kDigits;                          // invalid lanes match only each other
+        if (valid) {
+            k = load_key<W>(kin, i);
+            idx = iin[i];
+            d = (int)((kin[(uint64_t)i * W + word] >> shift) & (kDigits - 1));
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int wrank = __popc(peers & ((1u << lane) - 1u));
+        if (valid && wrank == 0) wc[warp][d] = (uint32_t)__popc(peers);
+        __syncthreads();
+        uint32_t tile_total = 0;
+        {
+            const int dd = threadIdx.x;
+#pragma unroll
+            for (int w = 0; w < kBlock / 32; ++w) {
+                uint32_t c = wc[w][dd];
+                wc[w][dd] = tile_total;
+                tile_total += c;
+            }
+        }
+        __syncthreads();
+        if (valid) {
+            uint32_t pos = base[d] + wc[warp][d] + (uint32_t)wrank;
+            store_key<W>(kout, pos, k);
+            iout[pos] = idx;
+        }
+        __syncthreads();
+        base[threadIdx.x] += tile_total;
+    }
+}
+
+// Sorted M in place: keys, descriptors and amplitudes from the source rows,
+// rescue map, and the fresh table.
+template <int W>
+__global__ void __launch_bounds__(kBlock) k_trunc_place(Counters* ctr, const uint64_t* __restrict__ sk,
+                                                        const uint32_t* __restrict__ si,
+                                                        const double2* __restrict__ c_in,
+                                                        const uint32_t* __restrict__ meta_in,
+                                                        uint64_t* __restrict__ keys_out, double2* __restrict__ c_out,
+                                                        uint32_t* __restrict__ meta_out, uint64_t* table_out,
+                                                        uint64_t slots, uint32_t* __restrict__ from, int step)
+{
+    if (ctr->err) return;
+    const uint32_t n = ctr->kept;
+    for (uint32_t dst = blockIdx.x * blockDim.x + threadIdx.x; dst < n; dst += gridDim.x * blockDim.x) {
+        const uint32_t src = si[dst];
+        Key<W> k = load_key<W>(sk, dst);
+        store_key<W>(keys_out, dst, k);
+        c_out[dst] = c_in[src];
+        meta_out[dst] = meta_in[src];
+        if (from) from[dst] = src;
+        if (!table_insert_unique<W>(table_out, slots, k, dst)) set_err(ctr, kErrProbe, step, 1);
+    }
+}
+
+template <int W>
+static int sorted_m(const Bufs& b, int gin, int gout, int step, cudaStream_t st)
+{
+    int n = 0;
+    k_trunc_compact<W><<<b.G, kBlock, 0, st>>>(b.keys[gin], b.ctr, b.keepw, b.blk_off, b.sortk[0], b.sorti[0]);
+    ++n;
+    int cur = 0;
+    for (int w = 0; w < W; ++w) {
+        for (int s = 0; s < b.key_bits[w]; s += 8) {
+            k_rs_hist<W><<<b.G, kBlock, 0, st>>>(b.ctr, b.sortk[cur], w, s, b.rs_hist);
+            k_rs_scan<<<1, 1024, 0, st>>>(b.ctr, b.rs_hist, b.G);
+            k_rs_scatter<W><<<b.G, kBlock, 0, st>>>(b.ctr, b.sortk[cur], b.sorti[cur], b.sortk[1 - cur],
+                                                     b.sorti[1 - cur], w, s, b.rs_hist);
+            cur = 1 - cur;
+            n += 3;
+        }
+    }
+    k_trunc_place<W><<<b.grid, kBlock, 0, st>>>(b.ctr, b.sortk[cur], b.sorti[cur], b.V[0], b.meta[gin], b.keys[gout],
+                                                 b.V[1], b.meta[gout], b.table[gout], b.table_slots, b.from, step);
+    return n + 1;
+}
+
+int launch_sorted_m(const Bufs& b, int gin, int gout, int step, cudaStream_t st)
+{
+    switch (b.W) {
+    case 1: return sorted_m<1>(b, gin, gout, step, st);
+    case 2: return sorted_m<2>(b, gin, gout, step, st);
+    case 3: return sorted_m<3>(b, gin, gout, step, st);
+    case 4: return sorted_m<4>(b, gin, gout, step, st);
+    default: return -1;
+    }
+}
+
+}  // namespace paces

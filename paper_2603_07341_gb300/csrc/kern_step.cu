@@ -97,41 +97,6 @@ __global__ void __launch_bounds__(1024) k_scan(const uint32_t* __restrict__ blk_
     }
 }
 
-template <int W>
-__global__ void __launch_bounds__(kBlock) k_trunc_scatter(const uint64_t* __restrict__ keys_in,
-                                                          const double2* __restrict__ c_in, Counters* ctr,
-                                                          const uint32_t* __restrict__ keepw,
-                                                          const uint32_t* __restrict__ blk_off,
-                                                          uint64_t* __restrict__ keys_out, double2* __restrict__ c_out,
-                                                          uint64_t* table_out, uint64_t slots,
-                                                          const uint32_t* __restrict__ meta_in,
-                                                          uint32_t* __restrict__ meta_out,
-                                                          uint32_t* __restrict__ from, int step)
-{
-    if (ctr->err) return;
-    uint32_t q = ctr->q_in, lo, hi;
-    chunk_of(q, gridDim.x, blockIdx.x, lo, hi);
-    uint32_t run = blk_off[blockIdx.x];
-    for (uint32_t base = lo; base < hi; base += kBlock) {
-        uint32_t i = base + threadIdx.x;
-        uint32_t w0 = base + (threadIdx.x & ~31u);
-        uint32_t bal = (w0 < hi) ? keepw[w0 >> 5] : 0u;
-        bool keep = (i < hi) && ((bal >> (threadIdx.x & 31)) & 1u);
-        uint32_t tot;
-        uint32_t r = block_excl_scan<kBlock>(keep ? 1u : 0u, &tot);
-        if (keep) {
-            uint32_t dst = run + r;
-            Key<W> k = load_key<W>(keys_in, i);
-            store_key<W>(keys_out, dst, k);
-            c_out[dst] = c_in[i];
-            meta_out[dst] = meta_in[i];
-            if (from) from[dst] = i;
-            if (!table_insert_unique<W>(table_out, slots, k, dst)) set_err(ctr, kErrProbe, step, 1);
-        }
-        run += tot;
-    }
-}
-
 // ---------------------------------------------------------------- a2/a3 one level
 // One thread per candidate c = (parent p - lo) * D + move: the parents of a
 // level are the frontier rows [lo, hi); every candidate is inserted
@@ -914,10 +879,8 @@ static int trunc_w(const Bufs& b, int gin, int gout, double th2, int step, cudaS
     if (!counted)
         k_trunc_count<<<b.G, kBlock, 0, st>>>(b.V[0], b.ctr, th2, dw_from_double(th2), b.fmt, b.keepw, b.blk_cnt);
     k_scan<<<1, 1024, 0, st>>>(b.blk_cnt, b.blk_off, b.G, b.ctr, kScanTrunc, 0, b.cap_rows, step);
-    k_trunc_scatter<W><<<b.G, kBlock, 0, st>>>(b.keys[gin], b.V[0], b.ctr, b.keepw, b.blk_off, b.keys[gout],
-                                               b.V[1], b.table[gout], b.table_slots, b.meta[gin], b.meta[gout], b.from,
-                                               step);
-    return 3;
+    int n = launch_sorted_m(b, gin, gout, step, st);
+    return n < 0 ? n : n + (counted ? 1 : 2);
 }
 
 template <int W>

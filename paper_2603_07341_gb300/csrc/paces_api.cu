@@ -321,7 +321,17 @@ paces_status alloc_rows(paces_t h, uint32_t cap, std::vector<DevAlloc>& out, Buf
     chk(b.cnt = alloc_track<uint8_t>(h, h->row_allocs, cap));
     chk(b.diag = alloc_track<double>(h, h->row_allocs, cap));
     chk(b.cand_slot = alloc_track<uint32_t>(h, h->row_allocs, (size_t)cap * h->D));
+    // sort of the kept set: indices in the winner-mask buffer (free during
+    // truncation); keys in the two term buffers when a key fits in 16 bytes
+    if (h->W <= 2) {
+        b.sortk[0] = reinterpret_cast<uint64_t*>(b.V[2]);
+        b.sortk[1] = reinterpret_cast<uint64_t*>(b.V[3]);
+    } else {
+        for (int s = 0; s < 2; ++s) chk(b.sortk[s] = alloc_track<uint64_t>(h, h->row_allocs, (size_t)cap * h->W));
+    }
     chk(b.masks = alloc_track<uint64_t>(h, h->row_allocs, cap));
+    b.sorti[0] = reinterpret_cast<uint32_t*>(b.masks);
+    b.sorti[1] = reinterpret_cast<uint32_t*>(b.masks) + cap;
     chk(b.keepw = alloc_track<uint32_t>(h, h->row_allocs, cap / 32 + 64));
     out.swap(h->row_allocs);
     h->row_allocs.swap(saved);
@@ -859,10 +869,23 @@ paces_status paces_create(const paces_params* params, const paces_allocator* all
     int bps_max = std::max(std::max(taylor_blocks_per_sm(1, 0), taylor_blocks_per_sm(4, 0)),
                            taylor_blocks_per_sm(8, 0));
     b.rec_len = PACES_OBS_FIXED + 2 * N * h->R + (h->R > 1 ? 2 * h->R : 0);
+    {   // bits each key word uses: the product of the radices packed into it
+        unsigned __int128 prod[PACES_MAX_WORDS];
+        for (int w = 0; w < PACES_MAX_WORDS; ++w) prod[w] = 1;
+        prod[0] = h->lay.exciton_radix;
+        for (int j = 0; j < N; ++j) prod[h->lay.site_word[j]] *= h->lay.site_radix[j];
+        prod[h->lay.batch_word] *= h->lay.batch_radix;
+        for (int w = 0; w < PACES_MAX_WORDS; ++w) {
+            int bits = 0;
+            while (w < h->W && bits < 64 && (((unsigned __int128)1) << bits) < prod[w]) ++bits;
+            b.key_bits[w] = bits;
+        }
+    }
 
     b.model = alloc_track<DevModel>(h, h->fixed_allocs, 1);
     b.ctr = alloc_track<Counters>(h, h->fixed_allocs, 1);
     b.topq = alloc_track<TopqState>(h, h->fixed_allocs, 1);
+    b.rs_hist = alloc_track<uint32_t>(h, h->fixed_allocs, 256 * (size_t)kMaxChunkBlocks);
     b.blk_cnt = alloc_track<uint32_t>(h, h->fixed_allocs, kMaxChunkBlocks);
     b.blk_off = alloc_track<uint32_t>(h, h->fixed_allocs, kMaxChunkBlocks);
     b.partials = alloc_track<double>(h, h->fixed_allocs, 8 * (size_t)h->sms * std::max(bps, bps_max) + 16);

@@ -54,6 +54,10 @@ struct Bufs {
     double* diag;                  // diagonal per row
     uint32_t* cand_slot;           // candidate -> table slot, kCand | row (an existing row), or kNone
     uint32_t* from;                // adjoint re-runs: row -> row of the previous state (or kNone)
+    uint64_t* sortk[2];            // sort of the kept set: keys (ping-pong)
+    uint32_t* sorti[2];            // and their source rows
+    uint32_t* rs_hist;             // digit counts per block [256][G]
+    int key_bits[kMaxWords];       // bits used by each key word (radix passes)
     void* terms;                   // adjoint re-runs: Taylor terms phi_1.. [n][row], 16 bytes each
     int term_max;                  // terms storable
     uint64_t* masks;               // winner bits per frontier row
@@ -98,6 +102,9 @@ int launch_truncate(const Bufs& b, int gin, int gout, double th2, int step, cuda
 int launch_truncate_nom(const Bufs& b, int gin, int gout, uint64_t q_nom, uint64_t seed, int step,
                         cudaStream_t st);
 int launch_topq_select(const Bufs& b, int gin, uint64_t q_nom, uint64_t seed, cudaStream_t st);
+// The kept rows (keep bits and chunk offsets ready) compacted, sorted by key
+// and placed in generation gout with their table (kern_sort.cu).
+int launch_sorted_m(const Bufs& b, int gin, int gout, int step, cudaStream_t st);
 int launch_level(const Bufs& b, int gen, int f, int rescue_gen, int step, cudaStream_t st);
 int launch_csr(const Bufs& b, int gen, cudaStream_t st);
 int launch_taylor(const Bufs& b, const TaylorParams& p, cudaStream_t st);

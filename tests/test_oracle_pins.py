@@ -480,3 +480,26 @@ def test_step_nom_equals_the_same_mask_as_override():
         tb, cb = b.rows()
         assert np.array_equal(ta, tb) and np.array_equal(ca, cb)
         assert a.stats()["kept"] == 60
+
+
+def test_kept_set_is_in_ascending_basis_order():
+    """After a truncating step the first |M| rows are the kept states in
+    ascending basis order (n_{N-1} most significant, then down to n_0, then
+    s), and they are exactly the states of the previous step that reached
+    theta (Sec. 3.3: truncation, then regrowth appended after M)."""
+    cfg = W.CONFIGS["ring4"]
+    o = Oracle(**W.model_kwargs(cfg))
+    o.set_state(*W.start_state(cfg))
+    for k in range(6):
+        t_prev, a_prev = o.rows()
+        o.step(0.1, 2e-3)
+        if k == 0:
+            continue
+        kept = int(o.stats()["kept"])
+        t, _ = o.rows()
+        M = t[:kept]
+        order = np.lexsort([M[:, c] for c in range(M.shape[1])])   # last column is primary
+        assert np.array_equal(order, np.arange(kept))
+        w = np.abs(a_prev) ** 2
+        want = {tuple(r) for r in t_prev[w >= 2e-3 ** 2]}
+        assert {tuple(r) for r in M} == want
