@@ -82,62 +82,105 @@ __global__ void __launch_bounds__(1024) k_rs_scan(const Counters* __restrict__ c
     }
 }
 
-// Stable scatter of one digit: each block walks its chunk in tiles of kBlock
-// items; the rank of an item among the equal digits before it is its rank in
-// its warp (match) plus the counts of the earlier warps of the tile plus the
-// items of the earlier tiles of the block.
+// Stable scatter of one digit.  Each block walks its chunk in tiles of
+// kBlock * IPT items (IPT rounds of one item per thread, in index order).  The
+// rank of an item among the equal digits of its tile is its rank in its warp
+// (match) plus the counts of the earlier warps of its round plus those of the
+// earlier rounds.  The tile is then staged in shared memory in digit order and
+// written out so that consecutive threads write consecutive positions of one
+// digit's run (coalesced), at the block's running offset of that digit.
+template <int W>
+struct ScatterTile {
+    static constexpr int kIPT = W <= 2 ? 4 : 2;
+    static constexpr int kItems = kBlock * kIPT;
+};
+
 template <int W>
 __global__ void __launch_bounds__(kBlock) k_rs_scatter(const Counters* __restrict__ ctr,
                                                        const uint64_t* __restrict__ kin, const uint32_t* __restrict__ iin,
                                                        uint64_t* __restrict__ kout, uint32_t* __restrict__ iout,
                                                        int word, int shift, const uint32_t* __restrict__ offs)
 {
-    static_assert(kBlock == kDigits, "one thread per digit in the per-tile prefix");
-    __shared__ uint32_t base[kDigits];
+    static_assert(kBlock == kDigits, "one thread per digit in the per-tile scans");
+    constexpr int IPT = ScatterTile<W>::kIPT, T = ScatterTile<W>::kItems;
+    __shared__ uint32_t base[kDigits];            // block's next output position per digit
+    __shared__ uint32_t run[kDigits];             // items of the current tile per digit so far
+    __shared__ uint32_t tstart[kDigits];          // first staged slot of each digit in the tile
     __shared__ uint32_t wc[kBlock / 32][kDigits];
+    __shared__ uint64_t skey[T * W];
+    __shared__ uint32_t sidx[T];
+    __shared__ uint16_t sdig[T];
     if (ctr->err) return;
     uint32_t n = ctr->kept, lo, hi;
     chunk_of(n, gridDim.x, blockIdx.x, lo, hi);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     base[threadIdx.x] = offs[(size_t)threadIdx.x * gridDim.x + blockIdx.x];
-    for (uint32_t t0 = lo; t0 < hi; t0 += kBlock) {
+    for (uint32_t t0 = lo; t0 < hi; t0 += T) {
+        run[threadIdx.x] = 0u;
+        int dg[IPT];
+        uint32_t rk[IPT];
+        Key<W> ks[IPT];
+        uint32_t is[IPT];
 #pragma unroll
-        for (int w = 0; w < kBlock / 32; ++w) wc[w][threadIdx.x] = 0u;
-        __syncthreads();
-        const uint32_t i = t0 + threadIdx.x;
-        const bool valid = i < hi;
-        Key<W> k;
+        for (int r = 0; r < IPT; ++r) {
 #pragma unroll
-        for (int x = 0; x < W; ++x) k.w[x] = 0;
-        uint32_t idx = 0;
-        int d = kDigits;                          // invalid lanes match only each other
-        if (valid) {
-            k = load_key<W>(kin, i);
-            idx = iin[i];
-            d = (int)((kin[(uint64_t)i * W + word] >> shift) & (kDigits - 1));
+            for (int w = 0; w < kBlock / 32; ++w) wc[w][threadIdx.x] = 0u;
+            __syncthreads();
+            const uint32_t i = t0 + (uint32_t)r * kBlock + threadIdx.x;
+            const bool valid = i < hi;
+#pragma unroll
+            for (int x = 0; x < W; ++x) ks[r].w[x] = 0;
+            is[r] = 0u;
+            int d = kDigits;                      // invalid lanes match only each other
+            if (valid) {
+                ks[r] = load_key<W>(kin, i);
+                is[r] = iin[i];
+                d = (int)((kin[(uint64_t)i * W + word] >> shift) & (kDigits - 1));
+            }
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            const uint32_t wrank = (uint32_t)__popc(peers & ((1u << lane) - 1u));
+            if (valid && wrank == 0) wc[warp][d] = (uint32_t)__popc(peers);
+            __syncthreads();
+            {   // exclusive prefix over the warps of this round, after the earlier rounds
+                const int dd = threadIdx.x;
+                uint32_t acc = run[dd];
+#pragma unroll
+                for (int w = 0; w < kBlock / 32; ++w) {
+                    uint32_t c = wc[w][dd];
+                    wc[w][dd] = acc;
+                    acc += c;
+                }
+                run[dd] = acc;
+            }
+            __syncthreads();
+            dg[r] = d;
+            rk[r] = valid ? wc[warp][d] + wrank : 0u;
+            __syncthreads();                      // wc is cleared for the next round
         }
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
-        const int wrank = __popc(peers & ((1u << lane) - 1u));
-        if (valid && wrank == 0) wc[warp][d] = (uint32_t)__popc(peers);
+        // first staged slot of every digit: exclusive scan of the tile counts
+        uint32_t tot;
+        const uint32_t st = block_excl_scan<kBlock>(run[threadIdx.x], &tot);
+        tstart[threadIdx.x] = st;
         __syncthreads();
-        uint32_t tile_total = 0;
-        {
-            const int dd = threadIdx.x;
 #pragma unroll
-            for (int w = 0; w < kBlock / 32; ++w) {
-                uint32_t c = wc[w][dd];
-                wc[w][dd] = tile_total;
-                tile_total += c;
+        for (int r = 0; r < IPT; ++r) {
+            if (dg[r] < kDigits) {
+                const uint32_t l = tstart[dg[r]] + rk[r];
+                store_key<W>(skey, l, ks[r]);
+                sidx[l] = is[r];
+                sdig[l] = (uint16_t)dg[r];
             }
         }
         __syncthreads();
-        if (valid) {
-            uint32_t pos = base[d] + wc[warp][d] + (uint32_t)wrank;
-            store_key<W>(kout, pos, k);
-            iout[pos] = idx;
+        for (uint32_t j = threadIdx.x; j < tot; j += kBlock) {
+            const int d = sdig[j];
+            const uint32_t pos = base[d] + (j - tstart[d]);
+            store_key<W>(kout, pos, load_key<W>(skey, j));
+            iout[pos] = sidx[j];
         }
         __syncthreads();
-        base[threadIdx.x] += tile_total;
+        base[threadIdx.x] += run[threadIdx.x];
+        __syncthreads();
     }
 }
 
