@@ -143,19 +143,31 @@ def taylor_counts(rec, h_words):
     return units, bytes_, flops
 
 
-def traffic_from_profile(kernel_src, end_step):
+def library_source_hash():
+    """sha256[:16] over the library's CUDA sources: the propagator's traffic also
+    depends on the row order the other stages produce."""
+    d = os.path.join(ROOT, "paper_2603_07341_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            h.update(name.encode())
+            h.update(open(os.path.join(d, name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profile(end_step):
     """ncu DRAM bytes per launch of the propagator at this window, if the
-    summary in profiles/ was taken on the current kernel source."""
+    summary in profiles/ was taken on the current library source."""
     path = os.path.join(ROOT, "profiles", "k_taylor_dw_ring16_traffic.md")
     if not os.path.exists(path):
         return None
     fields = {}
     for line in open(path):
         if ":" in line and line.startswith("- "):
-            k, v = line[2:].split(":", 1)
+            k, v = line[2:].rsplit(":", 1)
             fields[k.strip()] = v.strip()
-    h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
-    if fields.get("kernel source sha256[:16]") != h or fields.get("window end step") != str(end_step):
+    if fields.get("library source sha256[:16]") != library_source_hash() or \
+            fields.get("window end step") != str(end_step):
         return None
     try:
         return float(fields["dram bytes per launch"])
@@ -402,8 +414,7 @@ def main():
     achieved_tf = tflops / K / (tay_ms / 1e3) / 1e12
     frac_hbm = achieved_gbs / peak_gbs
     frac_fp64 = achieved_tf / FP64_PEAK_TFLOPS
-    src = os.path.join(ROOT, "paper_2603_07341_gb300", "csrc", "kern_taylor.cu")
-    traffic = traffic_from_profile(src, end)
+    traffic = traffic_from_profile(end) if args.workload == "ring16" and sol_precision(model) == "dw" else None
     if sol_precision(model) == "c128" and frac_fp64 > frac_hbm:
         roof = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s (FP64)",
                 "frac": frac_fp64, "traffic": traffic, "peak_kind": "nominal FP64 (derived)",
