@@ -350,7 +350,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ring16", choices=sorted(W.CONFIGS))
+    ap.add_argument("--workload", default="ring16", choices=sorted(W.WORKLOADS))
     ap.add_argument("--end-step", type=int, default=500,
                     help="last timed step (the ring16 trajectory has 1000; 0 = the whole trajectory)")
     ap.add_argument("--precision", default="dw", choices=["dw", "c128", "c64"])
@@ -361,7 +361,7 @@ def main():
                     help="also time the plain FP64 single-instance form and report observable errors")
     ap.add_argument("--compare-sample", type=int, default=4)
     args = ap.parse_args()
-    cfg = W.CONFIGS[args.workload]
+    cfg = W.WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, cfg)
 

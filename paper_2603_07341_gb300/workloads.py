@@ -22,7 +22,7 @@ import numpy as np
 RING, CHAIN, OPEN2D, OPEN3D, EXPLICIT = 0, 1, 2, 3, 4
 NEAREST, DIPOLAR = 0, 1
 
-CONFIGS = {
+WORKLOADS = {
     # 1D Holstein ring N=4, K=4 (full space 4*5^4 = 2500), checked against expm
     "ring4": dict(n_sites=4, lattice_kind=RING, dims=(4, 1, 1), coupling_kind=NEAREST,
                   J=1.0, omega=1.0, g=1.0, eps=0.0, cap=4, m=2, m_init=-1,

@@ -66,7 +66,7 @@ def _case(model, start, dt, theta, nsteps, every, precision, seed):
 
 def _ring_model():
     eps = W.seeded_normal(4, 21) * 0.3
-    cfg = dict(W.CONFIGS["ring4"], cap=3, g=0.8, J=0.6)
+    cfg = dict(W.WORKLOADS["ring4"], cap=3, g=0.8, J=0.6)
     return W.model_kwargs(cfg, eps=eps, m_init=2)
 
 
@@ -83,7 +83,7 @@ def test_ring_gradient_matches_oracle(libpaces, precision):
 def test_cube_gradient_matches_oracle(libpaces):
     """2x2x2 open cube, per-site energies: every eps_s bin and several segments."""
     eps = W.seeded_normal(8, 41) * 0.2
-    cfg = dict(W.CONFIGS["cube4"], n_sites=8, dims=(2, 2, 2), cap=2)
+    cfg = dict(W.WORKLOADS["cube4"], n_sites=8, dims=(2, 2, 2), cap=2)
     model = W.model_kwargs(cfg, eps=eps, m_init=2)
     _case(model, W.start_state(cfg), 0.05, 1e-3, 16, 4, B.DW, 51)
 
@@ -184,7 +184,7 @@ def test_cube4_directional_derivative_at_scale(libpaces):
     20): grad . v against central differences of the GPU forward along a
     seeded direction v, with the row and kept counts of every step unchanged
     by the perturbation (so the subspace sequence is the recorded one)."""
-    cfg = W.CONFIGS["cube4"]
+    cfg = W.WORKLOADS["cube4"]
     nsteps, dt, theta = 40, cfg["dt"], cfg["theta"]
     N = cfg["n_sites"]
     base = W.model_kwargs(cfg)

@@ -14,7 +14,7 @@ AMP_TOL = 1e-10
 
 
 def ensemble(R, **over):
-    cfg = W.CONFIGS["disorder12"]
+    cfg = W.WORKLOADS["disorder12"]
     eps = np.stack([W.realisation_eps(cfg, r) for r in range(R)])
     model = W.model_kwargs(cfg, **over)
     gb = B.Solver(**dict(model, eps=eps, batch=R))

@@ -26,7 +26,7 @@ def run(cfg, precision, nsteps, theta, **over):
     ("cube4", {"m_init": 2}, 20, 1e-5),
 ])
 def test_c64_observables_within_1e6_of_double_word(libpaces, name, over, nsteps, theta):
-    cfg = W.CONFIGS[name]
+    cfg = W.WORKLOADS[name]
     a = run(cfg, B.DW, nsteps, theta, **over)
     b = run(cfg, B.C64_SPMV, nsteps, theta, **over)
     ra = B.records_dict(a.observables(), cfg["n_sites"])
@@ -38,7 +38,7 @@ def test_c64_observables_within_1e6_of_double_word(libpaces, name, over, nsteps,
 
 
 def test_c64_amplitudes_against_oracle(libpaces):
-    cfg = W.CONFIGS["ring16"]
+    cfg = W.WORKLOADS["ring16"]
     model = W.model_kwargs(cfg)
     g = B.Solver(**model, precision=B.C64_SPMV)
     o = Oracle(**model)

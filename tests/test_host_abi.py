@@ -33,7 +33,7 @@ def test_library_exports_every_declared_symbol(libpaces):
 def test_layout_word_counts(libpaces, name, words, pow2):
     """Dense mixed radix where a power-of-two field would cost an extra word
     (ring16: 16 log2 9 + 4 = 54.7 bits in one word; cube4: 154.6 bits in 3)."""
-    L = B.plan_layout(**W.model_kwargs(W.CONFIGS[name]))
+    L = B.plan_layout(**W.model_kwargs(W.WORKLOADS[name]))
     assert (L.words, L.pow2) == (words, pow2)
 
 
@@ -71,7 +71,7 @@ def test_layout_rejects_too_wide_basis(libpaces):
 def test_encode_roundtrip_and_ranges(libpaces):
     rng = np.random.default_rng(3)
     for name in ("ring16", "dipolar6x6", "cube4"):
-        cfg = W.CONFIGS[name]
+        cfg = W.WORKLOADS[name]
         L = B.plan_layout(**W.model_kwargs(cfg))
         N, K = cfg["n_sites"], cfg["cap"]
         site = rng.integers(0, N, 50).astype(np.int32)

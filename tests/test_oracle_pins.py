@@ -43,7 +43,7 @@ def test_ring4_full_space_matches_dense_expm():
     space, so the trajectory is exp(-iHt) psi0 to the series tolerance (Sec. 3.5:
     the only error sources are Q, P_m and the series cutoff).  At the workload's
     theta = 1e-8 the early steps truncate; the end state stays within 1e-6."""
-    cfg = W.CONFIGS["ring4"]
+    cfg = W.WORKLOADS["ring4"]
     N = cfg["n_sites"]
     H, D, strides = dense_holstein(ring_hop(N, cfg["J"]), [0.0] * N, [1.0] * N, [1.0] * N, [4] * N)
     U = propagator(H)
@@ -65,7 +65,7 @@ def test_threshold_to_zero_converges():
     """Starting from the full space (m_init = closure), the error against the exact
     evolution falls steadily as the threshold goes to zero and reaches the series
     tolerance (Sec. 4.2: fidelity grows with the kept set; Sec. 3.5 error sources)."""
-    cfg = W.CONFIGS["ring4"]
+    cfg = W.WORKLOADS["ring4"]
     N = cfg["n_sites"]
     H, D, strides = dense_holstein(ring_hop(N, 1.0), [0.0] * N, [1.0] * N, [1.0] * N, [4] * N)
     U = propagator(H)
@@ -240,7 +240,7 @@ def test_norm_and_energy_conservation_inside_steps():
     """Sec. 3.5 / Fig. error_sources: the propagator is unitary to machine precision
     inside H_eff (norm to 1e-13) and conserves c^dag H_P c; with the full space kept
     the energy is constant across steps."""
-    cfg = W.CONFIGS["ring4"]
+    cfg = W.WORKLOADS["ring4"]
     o = oracle_for(cfg, eps=np.array([0.1, -0.2, 0.3, 0.0]))
     o.set_state(np.arange(4), np.zeros((4, 4), dtype=np.int32), [0.5] * 4)
     E0 = None
@@ -254,7 +254,7 @@ def test_norm_and_energy_conservation_inside_steps():
 
 
 def test_truncation_never_increases_norm():
-    cfg = W.CONFIGS["ring16"]
+    cfg = W.WORKLOADS["ring16"]
     o = oracle_for(cfg, m_init=4)
     o.set_state(*W.start_state(cfg))
     for _ in range(15):
@@ -267,7 +267,7 @@ def test_truncation_never_increases_norm():
 def test_sign_of_J_invariance_on_bipartite_ring():
     """J -> -J leaves populations and phonon numbers unchanged for a localised
     start on a bipartite lattice (App. H; gauge |s> -> (-1)^s |s>)."""
-    cfg = W.CONFIGS["ring4"]
+    cfg = W.WORKLOADS["ring4"]
     res = []
     for J in (1.0, -1.0):
         o = oracle_for(cfg, J=J, m_init=3)
@@ -281,7 +281,7 @@ def test_sign_of_J_invariance_on_bipartite_ring():
 
 def test_second_order_taylor_breaks_unitarity():
     """App. C.2: cutting the series at N_series = m = 2 makes the norm grow."""
-    cfg = W.CONFIGS["ring4"]
+    cfg = W.WORKLOADS["ring4"]
     good = oracle_for(cfg)
     bad = oracle_for(cfg, fixed_terms=2)
     for o in (good, bad):
@@ -294,7 +294,7 @@ def test_second_order_taylor_breaks_unitarity():
 
 def test_taylor_nonconvergence_is_reported():
     """App. I: a step too large for the series is an error, not a silent result."""
-    cfg = W.CONFIGS["ring4"]
+    cfg = W.WORKLOADS["ring4"]
     o = oracle_for(cfg, nmax=6)
     o.set_state(*W.start_state(cfg))
     with pytest.raises(OracleError) as e:
@@ -466,7 +466,7 @@ def test_top_q_tie_break_is_unbiased():
 
 
 def test_step_nom_equals_the_same_mask_as_override():
-    cfg = W.CONFIGS["ring4"]
+    cfg = W.WORKLOADS["ring4"]
     mk = lambda: Oracle(**W.model_kwargs(cfg))
     a, b = mk(), mk()
     for o in (a, b):
@@ -487,7 +487,7 @@ def test_kept_set_is_in_ascending_basis_order():
     ascending basis order (n_{N-1} most significant, then down to n_0, then
     s), and they are exactly the states of the previous step that reached
     theta (Sec. 3.3: truncation, then regrowth appended after M)."""
-    cfg = W.CONFIGS["ring4"]
+    cfg = W.WORKLOADS["ring4"]
     o = Oracle(**W.model_kwargs(cfg))
     o.set_state(*W.start_state(cfg))
     for k in range(6):

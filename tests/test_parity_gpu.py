@@ -84,7 +84,7 @@ def lockstep(gpu, ora, dt, theta, nsteps, check_every=1):
 
 # smaller initial balls where the oracle would otherwise need minutes
 SET_STATE_CASES = [("ring4", {}), ("ring16", {}), ("dipolar6x6", {"m_init": 2}),
-                   ("disorder12", {"eps": W.realisation_eps(W.CONFIGS["disorder12"], 0)}),
+                   ("disorder12", {"eps": W.realisation_eps(W.WORKLOADS["disorder12"], 0)}),
                    ("cube4", {"m_init": 3})]
 
 
@@ -92,7 +92,7 @@ SET_STATE_CASES = [("ring4", {}), ("ring16", {}), ("dipolar6x6", {"m_init": 2}),
 def test_initial_expansion_keys_bitexact(libpaces, name, over):
     """H_eff(0) = ball of radius m_init (Eq. H_eff): same states, same BFS order,
     same level boundaries."""
-    cfg = W.CONFIGS[name]
+    cfg = W.WORKLOADS[name]
     gpu, ora = make_pair(cfg, **over)
     st = W.start_state(cfg)
     gpu.set_state(*st)
@@ -109,7 +109,7 @@ def test_hamiltonian_parity(libpaces, name, over, precision):
     """P_m H P_m: per-row counts, columns and values in move order, diagonal
     (bit-exact in FP64; within the double-word rounding, 2^-47 relative,
     when the diagonal is held as a double-word)."""
-    cfg = W.CONFIGS[name]
+    cfg = W.WORKLOADS[name]
     gpu, ora = make_pair(cfg, gpu_extra=dict(precision=precision), **over)
     st = W.start_state(cfg)
     gpu.set_state(*st)
@@ -128,7 +128,7 @@ def test_hamiltonian_parity(libpaces, name, over, precision):
 @pytest.mark.parametrize("precision", [B.DW, B.C128], ids=["dw", "c128"])
 def test_ring4_full_trajectory(libpaces, precision):
     """Config ring4: 200 steps of dt = 0.05 at theta = 1e-8 in lockstep."""
-    cfg = W.CONFIGS["ring4"]
+    cfg = W.WORKLOADS["ring4"]
     gpu, ora = make_pair(cfg, gpu_extra=dict(precision=precision))
     gpu.set_state(*W.start_state(cfg))
     ora.set_state(*W.start_state(cfg))
@@ -139,7 +139,7 @@ def test_ring4_full_trajectory(libpaces, precision):
 @pytest.mark.parametrize("precision", [B.DW, B.C128], ids=["dw", "c128"])
 def test_ring16_trajectory_prefix(libpaces, precision):
     """Config ring16 (the throughput workload): the first 40 steps in lockstep."""
-    cfg = W.CONFIGS["ring16"]
+    cfg = W.WORKLOADS["ring16"]
     gpu, ora = make_pair(cfg, gpu_extra=dict(precision=precision))
     gpu.set_state(*W.start_state(cfg))
     ora.set_state(*W.start_state(cfg))
@@ -147,7 +147,7 @@ def test_ring16_trajectory_prefix(libpaces, precision):
 
 
 def test_dipolar_trajectory_prefix(libpaces):
-    cfg = W.CONFIGS["dipolar6x6"]
+    cfg = W.WORKLOADS["dipolar6x6"]
     gpu, ora = make_pair(cfg, m_init=2)
     gpu.set_state(*W.start_state(cfg))
     ora.set_state(*W.start_state(cfg))
@@ -156,7 +156,7 @@ def test_dipolar_trajectory_prefix(libpaces):
 
 @pytest.mark.parametrize("r", [0, 1])
 def test_disorder_realisation_trajectory(libpaces, r):
-    cfg = W.CONFIGS["disorder12"]
+    cfg = W.WORKLOADS["disorder12"]
     eps = W.realisation_eps(cfg, r)
     gpu, ora = make_pair(cfg, eps=eps, m_init=4)
     gpu.set_state(*W.start_state(cfg))
@@ -165,7 +165,7 @@ def test_disorder_realisation_trajectory(libpaces, r):
 
 
 def test_cube_trajectory_prefix(libpaces):
-    cfg = W.CONFIGS["cube4"]
+    cfg = W.WORKLOADS["cube4"]
     gpu, ora = make_pair(cfg, m_init=2)
     gpu.set_state(*W.start_state(cfg))
     ora.set_state(*W.start_state(cfg))
@@ -221,7 +221,7 @@ def test_frozen_single_state(libpaces):
 
 def test_capacity_grows_and_matches(libpaces):
     """Start with the minimum capacity; the library grows and redoes the step."""
-    cfg = W.CONFIGS["ring16"]
+    cfg = W.WORKLOADS["ring16"]
     gpu, ora = make_pair(cfg, gpu_extra=dict(max_rows=16), m_init=6)
     gpu.set_state(*W.start_state(cfg))
     ora.set_state(*W.start_state(cfg))
@@ -230,7 +230,7 @@ def test_capacity_grows_and_matches(libpaces):
 
 
 def test_noconvergence_reported_and_recoverable(libpaces):
-    cfg = W.CONFIGS["ring4"]
+    cfg = W.WORKLOADS["ring4"]
     gpu = B.Solver(**W.model_kwargs(cfg), nmax=14)
     gpu.set_state(*W.start_state(cfg))
     gpu.step(0.05, 3, 1e-8)
@@ -244,7 +244,7 @@ def test_noconvergence_reported_and_recoverable(libpaces):
 
 def test_second_order_series_breaks_unitarity(libpaces):
     """App. C.2 negative control on the GPU path: two terms only, norm grows."""
-    cfg = W.CONFIGS["ring4"]
+    cfg = W.WORKLOADS["ring4"]
     gpu = B.Solver(**W.model_kwargs(cfg), fixed_terms=2)
     gpu.set_state(*W.start_state(cfg))
     gpu.step(0.05, 100, 1e-8)
@@ -254,7 +254,7 @@ def test_second_order_series_breaks_unitarity(libpaces):
 
 def test_load_state_continues_bitwise(libpaces):
     """A state exported and loaded again continues exactly like the original."""
-    cfg = W.CONFIGS["ring16"]
+    cfg = W.WORKLOADS["ring16"]
     a = B.Solver(**W.model_kwargs(cfg, m_init=4))
     b = B.Solver(**W.model_kwargs(cfg, m_init=4))
     a.set_state(*W.start_state(cfg))

@@ -18,7 +18,7 @@ def solver(cfg, **kw):
 
 @pytest.mark.parametrize("max_rows", [0, 16])
 def test_graph_replay_is_bitwise_identical(libpaces, max_rows):
-    cfg = W.CONFIGS["ring16"]
+    cfg = W.WORKLOADS["ring16"]
     a = solver(cfg, max_rows=max_rows)
     b = solver(cfg, max_rows=max_rows)
     b.set_tuning(use_graphs=1)
@@ -34,7 +34,7 @@ def test_graph_replay_is_bitwise_identical(libpaces, max_rows):
 
 
 def test_tuning_knobs_keep_results(libpaces):
-    cfg = W.CONFIGS["ring16"]
+    cfg = W.WORKLOADS["ring16"]
     a = solver(cfg)
     b = solver(cfg)
     t = b.tuning()
@@ -53,7 +53,7 @@ def test_tuning_knobs_keep_results(libpaces):
 
 
 def test_autotuner_picks_valid_settings(libpaces, tmp_path):
-    cfg = W.CONFIGS["ring16"]
+    cfg = W.WORKLOADS["ring16"]
     model = W.model_kwargs(cfg)
     s = solver(cfg)
     ref = solver(cfg)

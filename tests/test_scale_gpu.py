@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 
 
 def test_ring16_full_size_invariants(libpaces):
-    cfg = W.CONFIGS["ring16"]
+    cfg = W.WORKLOADS["ring16"]
     s = B.Solver(**W.model_kwargs(cfg))
     s.set_state(*W.start_state(cfg))
     for _ in range(500):

@@ -18,7 +18,7 @@ AMP_TOL = 1e-10
 
 
 def _ring16(**over):
-    cfg = W.CONFIGS["ring16"]
+    cfg = W.WORKLOADS["ring16"]
     return cfg, W.model_kwargs(cfg, **over)
 
 
@@ -83,7 +83,7 @@ def test_topq_degenerate_weights_follow_the_tie_hash(libpaces, precision):
     """load_state (a mid-trajectory state; the next step truncates) with
     sixteen states of identical weight competing for places: the kept rows
     are the ones the published tie hash orders first."""
-    cfg = dict(W.CONFIGS["ring4"], cap=3)
+    cfg = dict(W.WORKLOADS["ring4"], cap=3)
     model = W.model_kwargs(cfg, m_init=1)
     tup, amp = _degenerate_state()
     helper = Oracle(**model)
@@ -126,7 +126,7 @@ def test_topq_graph_replay_is_bitwise(libpaces):
 
 
 def test_topq_gradient_replays_its_masks(libpaces):
-    cfg = dict(W.CONFIGS["ring4"], cap=3, g=0.8, J=0.6)
+    cfg = dict(W.WORKLOADS["ring4"], cap=3, g=0.8, J=0.6)
     model = W.model_kwargs(cfg, eps=W.seeded_normal(4, 21) * 0.3, m_init=2)
     gpu = B.Solver(**model, precision=B.C128)
     ora = Oracle(**model)
@@ -161,7 +161,7 @@ def test_topq_invalid_arguments(libpaces):
 def test_topq_paper_benchmark_chain_prefix(libpaces, precision):
     """The paper's g = 4 benchmark shape (open chain N = 25, K = 63, three-word
     keys) at a small q_nom: lockstep with the oracle over the first steps."""
-    cfg = W.CONFIGS["chain25"]
+    cfg = W.WORKLOADS["chain25"]
     model = W.model_kwargs(cfg, m_init=4)
     gpu = B.Solver(**model, precision=precision)
     ora = Oracle(**model)

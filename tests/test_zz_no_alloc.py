@@ -44,19 +44,19 @@ def check_case(model, site, occ, amps, base_radius):
 
 
 def test_noalloc_expansion_matches_regular_path_on_consecutive_calls(libpaces):
-    ring = W.model_kwargs(W.CONFIGS["ring16"])
-    dip = W.model_kwargs(W.CONFIGS["dipolar6x6"])
-    cube = W.model_kwargs(W.CONFIGS["cube4"])
-    n1 = check_case(ring, *W.start_state(W.CONFIGS["ring16"]), base_radius=4)
-    n2 = check_case(dip, *W.start_state(W.CONFIGS["dipolar6x6"]), base_radius=1)
-    n3 = check_case(cube, *W.start_state(W.CONFIGS["cube4"]), base_radius=1)
-    n4 = check_case(ring, *W.start_state(W.CONFIGS["ring16"]), base_radius=4)
+    ring = W.model_kwargs(W.WORKLOADS["ring16"])
+    dip = W.model_kwargs(W.WORKLOADS["dipolar6x6"])
+    cube = W.model_kwargs(W.WORKLOADS["cube4"])
+    n1 = check_case(ring, *W.start_state(W.WORKLOADS["ring16"]), base_radius=4)
+    n2 = check_case(dip, *W.start_state(W.WORKLOADS["dipolar6x6"]), base_radius=1)
+    n3 = check_case(cube, *W.start_state(W.WORKLOADS["cube4"]), base_radius=1)
+    n4 = check_case(ring, *W.start_state(W.WORKLOADS["ring16"]), base_radius=4)
     assert n1 == n4 and min(n1, n2, n3) > 100
 
 
 def test_noalloc_rejects_requests_beyond_its_array(libpaces):
     import torch
-    ring = W.model_kwargs(W.CONFIGS["ring16"])
+    ring = W.model_kwargs(W.WORKLOADS["ring16"])
     big = torch.zeros((3_000_000, 1), dtype=torch.int64, device="cuda")
     with pytest.raises(B.PacesError) as e:
         B.expand_noalloc(big, max_out=4_000_000, **ring)
