@@ -196,8 +196,12 @@ paces_status paces_load_state(paces_t h, int64_t n, const int32_t* site, const i
 /* Advance nsteps time steps of length dt (> 0) with amplitude threshold theta
  * (>= 0): keep a row iff re^2 + im^2 >= theta^2 (PACES_C128: in FP64 without
  * contraction; double-word storage: in double-word arithmetic, relative error
- * below 2^-46).  Appends one observables record per step.  Capacity grows
- * automatically and the failing step is redone.  Returns INVALID, STATE (no
+ * below 2^-46).  Row order after a step: the kept set M in ascending basis
+ * order (n_{N-1} most significant, down to n_0, then s; the realisation first
+ * in an ensemble), then each regrown BFS level in first-occurrence order
+ * (parents in row order, moves in canonical order).  Appends one observables
+ * record per step.  Capacity grows automatically (up to 2^30 - 1 rows) and the
+ * failing step is redone.  Returns INVALID, STATE (no
  * state set), NOCONVERGE (series did not reach taylor_tol: the state stays as
  * the failed step truncated and regrew it, unpropagated, and the next call
  * propagates it without truncating again), CAPACITY or CUDA. */
