@@ -144,14 +144,19 @@ def taylor_counts(rec, h_words):
 
 
 def library_source_hash():
-    """sha256[:16] over the library's CUDA sources: the propagator's traffic also
-    depends on the row order the other stages produce."""
+    """sha256[:16] over the code of the library's CUDA sources, comments and
+    whitespace removed: the propagator's traffic also depends on the row order
+    the other stages produce, but not on how the code is commented."""
+    import re
     d = os.path.join(ROOT, "paper_2603_07341_gb300", "csrc")
     h = hashlib.sha256()
     for name in sorted(os.listdir(d)):
         if name.endswith((".cu", ".cuh", ".h")):
+            src = open(os.path.join(d, name)).read()
+            src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+            src = re.sub(r"//[^\n]*", " ", src)
             h.update(name.encode())
-            h.update(open(os.path.join(d, name), "rb").read())
+            h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 

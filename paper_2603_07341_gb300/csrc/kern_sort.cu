@@ -6,9 +6,10 @@
 // descriptors and amplitudes gathered from their source rows, and each row
 // inserted into the fresh table.  Ascending key order is ascending basis
 // order -- n_{N-1} most significant, down to n_0, then the exciton site --
-// which is the order of the paper's sorted key array (Sec. "Truncation &
-// post-adaptation detruncation" with the sort-and-search of its
-// implementation).  States that differ by an exciton hop are then neighbours
+// the order of a sorted key array, which the paper's index matching between
+// successive effective spaces by sorting and searching works on (Sec. "Formal
+// operator representation and notes on parallelization").  States that
+// differ by an exciton hop are then neighbours
 // in M, and the regrown levels inherit that grouping from their parents, so
 // the propagator's gathers of neighbour amplitudes hit cache lines that are
 // already loaded.
