@@ -8,6 +8,8 @@
 // Paper: Sec. 3.3 (neighbour sets, Eqs. def_neighbor/def_neighbor_k/H_eff;
 // truncation and post-adaptation detruncation; generating the effective
 // Hamiltonian) and Sec. 3.4 (the step map).
+#include <type_traits>
+
 #include "runtime.h"
 #include "paces.h"
 
@@ -568,12 +570,14 @@ __global__ void __launch_bounds__(kBlock) k_obs_accum(const DevModel* __restrict
         nl += lo;
         // every phonon digit, with the divisor held in registers when all
         // sites share one radix
-        auto digits = [&](auto radix_of) {
+        auto digits = [&](auto uniform) {
 #pragma unroll
             for (int wd = 0; wd < W; ++wd) {
                 uint64_t x = (wd == 0) ? q0 : k.w[wd];
                 for (int j = wf[wd]; j < wf[wd + 1]; ++j) {
-                    const UDiv& dv = radix_of(j);
+                    UDiv dv;
+                    if constexpr (decltype(uniform)::value) dv = rd0;
+                    else dv = M->div_radix[j];
                     uint64_t xq = udiv(x, dv);
                     unsigned long long nj = x - xq * dv.d;
                     x = xq;
@@ -587,8 +591,8 @@ __global__ void __launch_bounds__(kBlock) k_obs_accum(const DevModel* __restrict
                 }
             }
         };
-        if (uni) digits([&](int) -> const UDiv& { return rd0; });
-        else digits([&](int j) -> const UDiv& { return M->div_radix[j]; });
+        if (uni) digits(std::true_type{});
+        else digits(std::false_type{});
     }
     nh = warp_sum_u64(nh);
     nl = warp_sum_u64(nl);

@@ -1519,7 +1519,6 @@ paces_status paces_backward(paces_t h, int64_t nsteps, const double* dL_dc_final
     if (s) return s;
     const Counters live_ctr = *h->hctr;
     const uint32_t q_live = live_ctr.q;
-    const int live_gen = h->gen;
     const double live_time = h->time;
 
     // forward records of the recorded steps (restored unchanged at the end)
@@ -1597,7 +1596,6 @@ paces_status paces_backward(paces_t h, int64_t nsteps, const double* dL_dc_final
         if (e_ != cudaSuccess) return finish(cuda_fail(h, e_, #call));            \
     } while (0)
     if (!ok) return finish(fail(h, PACES_ERR_CAPACITY, "reverse-pass buffers"));
-    (void)live_gen;
     s = copy_state_out(h, h->gen, 0, q_live, live);
     if (s) return finish(s);
     saved_live = true;

@@ -168,3 +168,19 @@ def test_topq_paper_benchmark_chain_prefix(libpaces, precision):
     gpu.set_state(*W.start_state(cfg))
     ora.set_state(*W.start_state(cfg))
     _lockstep_nom(gpu, ora, cfg["dt"], 1500, 2603073410, 10)
+
+
+def test_qtrue_over_qnom_matches_the_papers_1d_estimate(libpaces):
+    """For the 1D Holstein chain the paper finds q_true ~ 2^(m-1) 2.5 q_nom
+    (Sec. 3.3, after Eq. qtrue: about 170e6 rows at q_nom = 32e6, m = 2).  The
+    chain25 model at a smaller q_nom, once truncation is active: the ratio of
+    regrown to kept rows stays near 5."""
+    cfg = W.WORKLOADS["chain25"]
+    s = B.Solver(**W.model_kwargs(cfg))
+    s.set_state(*W.start_state(cfg))
+    s.step_nom(cfg["dt"], 150, 2_000_000, 1)
+    rec = s.observables(131, 20)
+    rows, kept = rec[:, 6], rec[:, 7]
+    assert np.all(kept == 2_000_000)
+    ratio = rows / kept
+    assert np.all((ratio > 4.0) & (ratio < 7.0)), ratio
