@@ -178,8 +178,8 @@ def test_qtrue_over_qnom_matches_the_papers_1d_estimate(libpaces):
     cfg = W.WORKLOADS["chain25"]
     s = B.Solver(**W.model_kwargs(cfg))
     s.set_state(*W.start_state(cfg))
-    s.step_nom(cfg["dt"], 150, 2_000_000, 1)
-    rec = s.observables(131, 20)
+    s.step_nom(cfg["dt"], 250, 2_000_000, 1)
+    rec = s.observables(231, 20)
     rows, kept = rec[:, 6], rec[:, 7]
     assert np.all(kept == 2_000_000)
     ratio = rows / kept
