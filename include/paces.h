@@ -108,7 +108,8 @@ typedef struct {
     int32_t fixed_terms;        /* > 0: exactly this many series terms, no test         */
     double taylor_tol;          /* stop at n >= 2 with ||phi_n|| <= tol ||r||; 0 = 1e-15 */
     int32_t taylor_nmax;        /* series terms allowed before NOCONVERGE; 0 = 200      */
-    uint64_t max_rows;          /* initial row capacity hint; 0 = automatic (it grows)  */
+    uint64_t max_rows;          /* initial row capacity hint; 0 = automatic (it grows); */
+                                /* at most 2^30 - 1 (paces_create: CAPACITY beyond)     */
     int32_t batch;              /* realisations R of a static-disorder ensemble (0 or 1 */
                                 /* = one model); for R > 1 eps holds R*N site energies, */
                                 /* realisation r in eps[r*N .. r*N + N)                 */
