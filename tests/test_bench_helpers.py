@@ -7,10 +7,21 @@ import shutil
 import bench
 
 
-def test_stored_traffic_matches_this_library_and_window():
-    v = bench.traffic_from_profile(500)
-    assert v is not None and 3e11 < v < 2e12
+def test_stored_traffic_is_keyed_on_code_and_window(tmp_path, monkeypatch):
+    """A summary in the committed format is read back only for the library
+    code it names and the window it was taken at."""
+    src = os.path.join(bench.ROOT, "paper_2603_07341_gb300", "csrc")
+    shutil.copytree(src, tmp_path / "paper_2603_07341_gb300" / "csrc")
+    (tmp_path / "profiles").mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h = bench.library_source_hash()
+    prof = tmp_path / "profiles" / "k_taylor_dw_ring16_traffic.md"
+    prof.write_text("# summary\n\n- library source sha256[:16]: %s\n- window end step: 500\n"
+                    "- dram bytes per launch: 699490000000\n" % h)
+    assert bench.traffic_from_profile(500) == 699490000000.0
     assert bench.traffic_from_profile(499) is None
+    prof.write_text(prof.read_text().replace(h, "0" * 16))
+    assert bench.traffic_from_profile(500) is None
 
 
 def test_source_hash_ignores_comments_but_not_code(tmp_path, monkeypatch):
