@@ -1,5 +1,6 @@
 // kern_step.cu -- the integer/gather stages of one time step (sm_103a):
-//   a1 truncation Q (threshold, stable compaction, insertion of M into a fresh table),
+//   a1 truncation Q (threshold keep bits and their scan; the kept set is then
+//      sorted and placed by kern_sort.cu),
 //   a2/a3 one BFS level of H_eff: expansion of the frontier through H's moves,
 //         hash de-duplication with first-occurrence winners, compaction,
 //   a4 rescue of re-admitted amplitudes from the previous step's table,
