@@ -40,8 +40,9 @@ from paper_2603_07341_gb300 import workloads as W  # noqa: E402
 METRIC = "H-applied amplitudes/s"
 TIE_SEED = 2603073410                 # seed of the top-q_nom tie hash (workloads with q_nom)
 UNIT = "amplitudes/s"
+REF_SKIP = 60                         # reference arm: untimed oracle steps before its warm-up
 FALLBACK_HBM_GBS = 6800.0
-FP64_PEAK_TFLOPS = 1.25          # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal table)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x FP64 FMA/clk/SM x 2 flop x max SM clock (GHz)
 
 
 def peaks():
@@ -129,17 +130,23 @@ def reduce_over_ranks(dist, ms, units, t_host, all_units, device):
 
 
 def sol_precision(model):
-    return {0: "dw", 1: "c128", 2: "c64"}[int(model.get("precision", 0))]
+    return {0: "c128", 1: "dw", 2: "c64"}[int(model.get("precision", 0))]
 
 
 def taylor_counts(rec, h_words):
-    """Units, FP64 flops and algorithmic bytes of the propagator over records."""
+    """Units, FP64 flops and algorithmic bytes of the propagator over records.
+
+    Bytes per row and term: 1 (entry count) + 8 (diagonal) + 16 (x_i) + 16
+    (phi_n written) + 32 (r read and written; 16 written in term 1, where
+    r = x + phi_1) and 5 per off-diagonal entry (column and coefficient id).
+    FP64 flops per row and term of the FP64 kernel: 4 per off-diagonal entry
+    (two FMAs), 5 for the diagonal (dt/n times d, two FMAs), 2 for r += phi_n."""
     q = rec[:, 6]
     nnz_off = rec[:, 8] - q
     terms = rec[:, 9]
     units = float(np.sum(terms * q))
     bytes_ = float(np.sum(q * 57.0 + nnz_off * 5.0 + (terms - 1) * (q * 73.0 + nnz_off * 5.0)))
-    flops = float(np.sum(terms * (q * 16.0 + nnz_off * 4.0) + q * 8.0))
+    flops = float(np.sum(terms * (q * 7.0 + nnz_off * 4.0)))
     return units, bytes_, flops
 
 
@@ -160,24 +167,48 @@ def library_source_hash():
     return h.hexdigest()[:16]
 
 
-def traffic_from_profile(end_step):
-    """ncu DRAM bytes per launch of the propagator at this window, if the
-    summary in profiles/ was taken on the current library source."""
-    path = os.path.join(ROOT, "profiles", "k_taylor_dw_ring16_traffic.md")
+def traffic_scaled(kernel, alg_bytes_per_launch):
+    """DRAM bytes per launch of the propagator at the bench window, scaled from
+    a one-kernel ncu capture of a small case of the same workload (inputs above
+    L2, a few GB on the device): the capture's ratio of DRAM to algorithmic
+    bytes times this window's algorithmic bytes.  None unless the summary in
+    profiles/ was taken on the current library source."""
+    path = os.path.join(ROOT, "profiles", "%s_ring16_small_traffic.md" % kernel)
     if not os.path.exists(path):
-        return None
+        return None, None
     fields = {}
     for line in open(path):
         if ":" in line and line.startswith("- "):
             k, v = line[2:].rsplit(":", 1)
             fields[k.strip()] = v.strip()
-    if fields.get("library source sha256[:16]") != library_source_hash() or \
-            fields.get("window end step") != str(end_step):
-        return None
+    if fields.get("library source sha256[:16]") != library_source_hash():
+        return None, None
     try:
-        return float(fields["dram bytes per launch"])
-    except (KeyError, ValueError):
-        return None
+        ratio = float(fields["dram bytes per launch"]) / float(fields["algorithmic bytes per launch"])
+    except (KeyError, ValueError, ZeroDivisionError):
+        return None, None
+    return ratio * alg_bytes_per_launch, "scaled: DRAM/algorithmic ratio %.3f of a %s capture (%s) times " \
+        "this window's algorithmic bytes" % (ratio, kernel, fields.get("case", "small case"))
+
+
+def cpu_info():
+    """Host core count and CPU model (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None and os.path.exists("/proc/cpuinfo"):
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                model = line.split(":", 1)[1].strip()
+                break
+    import platform
+    return os.cpu_count() or 1, "%s (%s)" % (model or "unknown", platform.machine())
 
 
 def oracle_model(cfg):
@@ -194,23 +225,56 @@ def oracle_step(o, cfg):
         o.step(cfg["dt"], cfg["theta"])
 
 
-def cpu_baseline(cfg, budget_s=15.0, max_steps=None):
-    """The oracle as it stands on this host: steps from psi(0) until the budget."""
+def _oracle_run(args):
+    """One oracle process: psi(0), then `skip` untimed steps, then timed steps
+    until `budget_s` seconds or `max_steps` steps.  Returns (units, seconds,
+    timed steps, final rows)."""
+    name, skip, budget_s, max_steps = args
+    sys.path.insert(0, ROOT)
     from oracle.oracle import Oracle
+    cfg = W.WORKLOADS[name]
     o = Oracle(**oracle_model(cfg))
     o.set_state(*W.start_state(cfg))
-    units = 0.0
-    steps = 0
+    for _ in range(skip):
+        oracle_step(o, cfg)
+    units, steps, rows = 0.0, 0, 0
     t0 = time.perf_counter()
     while True:
         oracle_step(o, cfg)
         st = o.stats()
         units += st["terms"] * st["rows"]
+        rows = int(st["rows"])
         steps += 1
         el = time.perf_counter() - t0
-        if el > budget_s or (max_steps and steps >= max_steps):
+        if (budget_s and el > budget_s) or (max_steps and steps >= max_steps):
             break
-    return units / el, steps, el, int(st["rows"])
+    return units, el, steps, rows
+
+
+def oracle_replicas(name, procs, skip=0, budget_s=None, max_steps=None):
+    """The oracle (single-threaded C) as it stands, run as `procs` independent
+    processes, one per host core, started with spawn; aggregate units/s =
+    the processes' units over the slowest process's time."""
+    if procs <= 1:
+        return [_oracle_run((name, skip, budget_s, max_steps))]
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(procs) as pool:
+        return pool.map(_oracle_run, [(name, skip, budget_s, max_steps)] * procs)
+
+
+def cpu_baseline(name, budget_s=15.0):
+    """The oracle on this host: one process, then one per core, each timed
+    from psi(0) for about budget_s seconds."""
+    cores, model = cpu_info()
+    one = oracle_replicas(name, 1, budget_s=budget_s)[0]
+    allc = oracle_replicas(name, cores, budget_s=budget_s) if cores > 1 else [one]
+    v_all = sum(r[0] for r in allc) / max(r[1] for r in allc)
+    return {"value": v_all, "unit": UNIT, "cores": len(allc), "kind": "oracle",
+            "cpu_model": model, "nproc": cores,
+            "value_1core": one[0] / one[1],
+            "sample": "oracle steps 1..%d of %s from psi(0) (%.1f s, final rows %d) in each of %d processes, "
+                      "one per core; 1-core rate from one process alone (steps 1..%d)"
+                      % (min(r[2] for r in allc), name, max(r[1] for r in allc), allc[0][3], len(allc), one[2])}
 
 
 def ensemble_model(cfg, realisations=None):
@@ -321,30 +385,23 @@ def run_reference(args, cfg):
     ws, rank, _ = dist_setup()
     if rank != 0:
         return
-    # W warm-up then K timed oracle steps, each a bounded sample: the trajectory
-    # from psi(0) (the oracle cannot reach the GPU window in minutes)
-    from oracle.oracle import Oracle
-    o = Oracle(**oracle_model(cfg))
-    o.set_state(*W.start_state(cfg))
-    for _ in range(args.warmup):
-        oracle_step(o, cfg)
-    units = 0.0
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        oracle_step(o, cfg)
-        st = o.stats()
-        units += st["terms"] * st["rows"]
-    el = time.perf_counter() - t0
-    v = units / el
+    # the oracle as it stands, one process per host core: W warm-up steps then
+    # K timed steps from psi(0) in each (the oracle cannot reach the GPU window
+    # in minutes)
+    cores, cpu_model = cpu_info()
+    skip = REF_SKIP + args.warmup
+    runs = oracle_replicas(args.workload, cores, skip=skip, max_steps=args.steps)
+    el = max(r[1] for r in runs)
+    v = sum(r[0] for r in runs) / el
+    sample = "oracle steps %d..%d of %s from psi(0) (steps 1..%d untimed) in each of %d processes (one per " \
+        "core), final rows %d" % (skip + 1, skip + args.steps, args.workload, skip, len(runs), runs[0][3])
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": args.workload, "sample": "oracle steps %d..%d from psi(0)"
-                       % (args.warmup + 1, args.warmup + args.steps)},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "oracle steps %d..%d from psi(0), final rows %d"
-                             % (args.warmup + 1, args.warmup + args.steps, int(st["rows"]))},
+            "config": {"workload": args.workload, "sample": sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": len(runs), "kind": "oracle", "nproc": cores,
+                             "cpu_model": cpu_model, "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -358,7 +415,7 @@ def main():
     ap.add_argument("--workload", default="ring16", choices=sorted(W.WORKLOADS))
     ap.add_argument("--end-step", type=int, default=500,
                     help="last timed step (the ring16 trajectory has 1000; 0 = the whole trajectory)")
-    ap.add_argument("--precision", default="dw", choices=["dw", "c128", "c64"])
+    ap.add_argument("--precision", default="c128", choices=["c128", "dw", "c64"])
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--realisations", type=int, default=0, help="ensemble size (0: the workload's)")
@@ -419,16 +476,19 @@ def main():
     achieved_tf = tflops / K / (tay_ms / 1e3) / 1e12
     frac_hbm = achieved_gbs / peak_gbs
     frac_fp64 = achieved_tf / FP64_PEAK_TFLOPS
-    traffic = traffic_from_profile(end) if args.workload == "ring16" and sol_precision(model) == "dw" else None
+    kern = {"c128": "k_taylor_f64", "dw": "k_taylor_dw", "c64": "k_taylor_c64"}[sol_precision(model)]
+    traffic, traffic_note = traffic_scaled(kern, tbytes / K) if args.workload == "ring16" else (None, None)
     if sol_precision(model) == "c128" and frac_fp64 > frac_hbm:
         roof = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s (FP64)",
-                "frac": frac_fp64, "traffic": traffic, "peak_kind": "nominal FP64 (derived)",
-                "hbm_achieved_gbs": achieved_gbs, "hbm_frac": frac_hbm}
+                "frac": frac_fp64, "traffic": traffic,
+                "peak_kind": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
+                "hbm_achieved_gbs": achieved_gbs, "hbm_frac": frac_hbm, "hbm_peak_gbs": peak_gbs}
     else:
         roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": peak_gbs, "unit": "GB/s",
-                "frac": frac_hbm, "traffic": traffic, "peak_kind": peak_kind + " (copy), sustained"}
-    roof["kernel"] = {"c128": "k_taylor_f64", "dw": "k_taylor_dw", "c64": "k_taylor_c64"}[sol_precision(model)] + \
-        " (one cooperative launch per time step)"
+                "frac": frac_hbm, "traffic": traffic, "peak_kind": peak_kind + " (copy), sustained",
+                "fp64_achieved_tflops": achieved_tf, "fp64_frac": frac_fp64}
+    roof["traffic_note"] = traffic_note
+    roof["kernel"] = kern + " (one cooperative launch per time step)"
     roof["algorithmic_bytes_per_launch"] = tbytes / K
 
     e2e = {"value": all_units / t_host, "unit": UNIT,
@@ -440,10 +500,7 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        v, nst, el, rows = cpu_baseline(cfg, args.cpu_budget)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "oracle steps 1..%d of %s from psi(0) (%.1f s, final rows %d)"
-                         % (nst, args.workload, el, rows)}
+        cpu = cpu_baseline(args.workload, args.cpu_budget)
 
     variants = None
     if args.compare:

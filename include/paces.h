@@ -74,11 +74,12 @@ typedef enum {
 #define PACES_NEAREST 0   /* M_ab = 1 for Euclidean distance 1                         */
 #define PACES_DIPOLAR 1   /* M_ab = 1 / r_ab^3 for all pairs (computed as 1/(r2*sqrt(r2))) */
 /* arithmetic of the amplitudes and of the propagator */
-#define PACES_DW 0        /* double-word: every amplitude is a pair of FP32 (48-bit       */
+#define PACES_C128 0      /* complex128: FP64 amplitudes and FP64 arithmetic, the         */
+                          /* paper's (default)                                            */
+#define PACES_DW 1        /* double-word: every amplitude is a pair of FP32 (48-bit       */
                           /* significand) and all arithmetic on them runs on the FP32     */
-                          /* pipe with error-free transformations (default)               */
-#define PACES_C128 1      /* complex128: FP64 amplitudes and FP64 arithmetic              */
-#define PACES_C64_SPMV 2  /* complex64 SpMV for terms n >= 2; term 1, the accumulator,    */
+                          /* pipe with error-free transformations                         */
+#define PACES_C64_SPMV 2  /* complex64 SpMV for terms n >= 3; terms 1-2, the accumulator, */
                           /* norms and truncation magnitudes double-word                  */
 
 /* Device memory hook.  alloc returns device memory of `bytes` usable on
@@ -104,7 +105,7 @@ typedef struct {
     const int32_t* phonon_cap;  /* [N] K_j >= 0 (d_pho - 1), required                  */
     int32_t m;                  /* neighbour order of every step, >= 0 (paper: 2)       */
     int32_t m_init;             /* neighbour order of H_eff(0); < 0 = until closure     */
-    int32_t precision;          /* PACES_DW, PACES_C128 or PACES_C64_SPMV               */
+    int32_t precision;          /* PACES_C128, PACES_DW or PACES_C64_SPMV               */
     int32_t fixed_terms;        /* > 0: exactly this many series terms, no test         */
     double taylor_tol;          /* stop at n >= 2 with ||phi_n|| <= tol ||r||; 0 = 1e-15 */
     int32_t taylor_nmax;        /* series terms allowed before NOCONVERGE; 0 = 200      */
@@ -282,7 +283,9 @@ paces_status paces_observables(paces_t h, int64_t first, int64_t count, double* 
 paces_status paces_profile(paces_t h, int32_t enable);
 /* ms[5]: summed stage times since the last reset; launches[6]: kernels launched
  * per stage (index 5: set_state and other kernels); bytes[5]: algorithmic bytes
- * moved per stage (the per-unit figures of the design notes). */
+ * moved per stage: per row, the key and amplitude reads and writes each stage
+ * must make, one 32-byte sector per hash probe, 5 bytes per stored entry of
+ * P H P, and per Taylor term 1 + 8 + 16 + 16 + 32 bytes per row. */
 paces_status paces_stage_stats(paces_t h, double* ms, int64_t* launches, double* bytes,
                                int32_t reset);
 

@@ -16,7 +16,7 @@
  *              (Sec. "Generating the effective Hamiltonian"), propagate with the
  *              Taylor series of exp(-i P H P dt) (App. C.1), record observables.
  *
- * Readings taken where the paper is silent (listed in the design notes):
+ * Readings taken where the paper is silent:
  *   - truncation keeps a row iff re^2 + im^2 >= theta^2, evaluated in FP64 with
  *     no contraction (this file is compiled with -ffp-contract=off);
  *   - no truncation before the first propagation after set_state;

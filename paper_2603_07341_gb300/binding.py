@@ -17,7 +17,7 @@ from . import build as _build
 OK, ERR_INVALID, ERR_KEY_WIDTH, ERR_CAPACITY, ERR_NOCONVERGE, ERR_CUDA, ERR_STATE, ERR_UNSUPPORTED = range(8)
 RING, CHAIN, OPEN2D, OPEN3D, EXPLICIT = 0, 1, 2, 3, 4
 NEAREST, DIPOLAR = 0, 1
-DW, C128, C64_SPMV = 0, 1, 2
+C128, DW, C64_SPMV = 0, 1, 2
 MAX_SITES, MAX_WORDS = 128, 4
 OBS_FIELDS = ("time", "norm", "norm_phi0", "energy", "C_re", "C_im", "rows", "kept", "nnz", "terms",
               "norm_before")
@@ -152,7 +152,7 @@ def _ip(a):
 
 
 def make_params(n_sites, lattice_kind=RING, dims=(0, 0, 0), coupling_kind=NEAREST, J=1.0, eps=None,
-                omega=None, g=None, cap=None, m=2, m_init=10, precision=DW, fixed_terms=0, tol=0.0,
+                omega=None, g=None, cap=None, m=2, m_init=10, precision=C128, fixed_terms=0, tol=0.0,
                 nmax=0, max_rows=0, J_explicit=None, batch=1):
     """Build a Params struct; returns (struct, keepalive arrays).  For an
     ensemble (batch R > 1) eps is [R, N] (or broadcastable to it)."""
@@ -217,13 +217,21 @@ def expand_noalloc(keys_in, max_out, stream=None, **model):
     import torch
     lib = load()
     p, keep = make_params(**model)
+    if not (torch.is_tensor(keys_in) and keys_in.is_cuda and keys_in.dtype == torch.int64 and keys_in.dim() == 2):
+        raise ValueError("keys_in must be a 2-D int64 CUDA tensor [n_in, words]")
+    words = plan_layout(**model).words
+    if keys_in.shape[1] != words:
+        raise ValueError("keys_in has %d words per key; this model's layout uses %d" % (keys_in.shape[1], words))
     keys_in = keys_in.contiguous()
-    n_in, words = keys_in.shape
-    out = torch.empty((int(max_out), words), dtype=torch.int64, device=keys_in.device)
-    n = C.c_int64()
-    st = stream if stream is not None else torch.cuda.current_stream()
-    rc = lib.paces_expand_noalloc(C.byref(p), C.c_void_p(keys_in.data_ptr()), n_in, C.c_void_p(out.data_ptr()),
-                                  int(max_out), C.byref(n), C.c_void_p(st.cuda_stream))
+    n_in = keys_in.shape[0]
+    # the library works on the current device and that device's scratch array
+    with torch.cuda.device(keys_in.device):
+        out = torch.empty((int(max_out), words), dtype=torch.int64, device=keys_in.device)
+        n = C.c_int64()
+        st = stream if stream is not None else torch.cuda.current_stream(keys_in.device)
+        rc = lib.paces_expand_noalloc(C.byref(p), C.c_void_p(keys_in.data_ptr()), n_in,
+                                      C.c_void_p(out.data_ptr()), int(max_out), C.byref(n),
+                                      C.c_void_p(st.cuda_stream))
     if rc:
         raise PacesError(rc, "paces_expand_noalloc")
     return out[: n.value]

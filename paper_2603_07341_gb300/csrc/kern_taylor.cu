@@ -2,10 +2,11 @@
 //   phi_0 = c',  phi_n = (-i dt / n) (P H P) phi_{n-1},  r = sum_n phi_n,
 // stopping at the first n >= 2 with ||phi_n||^2 <= tol^2 ||r||^2.
 //
-// Two arithmetic variants share the structure below: k_taylor_dw keeps every
+// Three arithmetic variants share the structure below: k_taylor_f64 keeps the
+// amplitudes in FP64 (the paper's complex128); k_taylor_dw keeps every
 // amplitude as a double-word (FP32 pair) and accumulates each row with the
-// compensated dot product (FP32 pipe, 48-bit significand); k_taylor_f64 does
-// the same in FP64 (the FP64 pipe of this part is the bottleneck there).
+// compensated dot product (FP32 pipe, 48-bit significand); k_taylor_c64 runs
+// the later terms in complex64.
 //
 // One cooperative launch runs every term of a step: each term is one pass of
 // SpMV over the row-pitched P H P fused with the scaling, the accumulation
@@ -123,6 +124,28 @@ __device__ __forceinline__ double2 row_apply(const uint32_t* __restrict__ col, c
     return make_double2(yr, yi);
 }
 
+// |v| 2^32 as an FP32 number, from the upper 32 bits of the FP64 v (20 bits of
+// significand, relative error below 2^-20) with integer operations only, so
+// that the stop test costs the FP64 pipe nothing.  |v| below 2^-158 gives 0 (or
+// a subnormal), |v| at or above 2^96 saturates.
+__device__ __forceinline__ float mag_scaled_f32(double v)
+{
+    int h = __double2hiint(v) & 0x7FFFFFFF;
+    int e = (h >> 20) - (1023 - 127 - 32);
+    e = min(max(e, 0), 254);
+    return __int_as_float((e << 23) | ((h & 0xFFFFF) << 3));
+}
+
+// FP64 amplitudes.  The FP64 pipe of this part retires about two operations
+// per SM per clock, so the kernel spends FP64 operations only on the
+// amplitudes themselves: the factor dt/n is folded into the shared coefficient
+// table and into one product with the diagonal, so a row of c off-diagonal
+// entries costs 2c + 5 FP64 operations (products, the diagonal, r += phi_n).
+// The stop test compares ||phi_n||^2, summed in FP32 from the leading 20 bits
+// of every component, with tol^2 ||c'||^2 (||c'|| in FP64 from term 1): the
+// partial sum r_n differs from c' in norm by about ||phi_{n+1}||, which is
+// far below the test's resolution when the test is near to passing.  A term
+// more or less changes r by at most tol ||c'||.
 template <int LPR>
 __global__ void __launch_bounds__(kBlock) k_taylor_f64(TaylorArgs a)
 {
@@ -131,9 +154,7 @@ __global__ void __launch_bounds__(kBlock) k_taylor_f64(TaylorArgs a)
     Counters* ctr = a.ctr;
     if (ctr->err) return;
     const DevModel* M = a.M;
-    for (int t = threadIdx.x; t < M->ncoef; t += blockDim.x) coef[t] = M->coef[t];
-    __syncthreads();
-
+    const int ncoef = M->ncoef;
     const uint32_t q = ctr->q;
     const uint64_t P = (uint64_t)M->P;
     const unsigned G = gridDim.x;
@@ -142,43 +163,49 @@ __global__ void __launch_bounds__(kBlock) k_taylor_f64(TaylorArgs a)
     const uint32_t nwarps = (G * blockDim.x) >> 5;
     const int lane = (threadIdx.x & 31) % LPR;
     const uint32_t sub = (threadIdx.x & 31) / LPR;
+    const float kScale2 = 18446744073709551616.0f;          // 2^64 = (2^32)^2
 
     const int fixed = a.p.fixed_terms;
     const int nlimit = fixed > 0 ? fixed : a.p.nmax;
     const double2* x = a.c_in;
     double2* y = a.ta;
-    double E = 0.0, n0 = 0.0, r2 = 0.0;
+    double E = 0.0, n0 = 0.0;
     int nd = 0;
     bool conv = false;
     for (int n = 1; n <= nlimit; ++n) {
         const double s = a.p.dt / (double)n;
-        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        __syncthreads();
+        for (int t = threadIdx.x; t < ncoef; t += blockDim.x) coef[t] = s * M->coef[t];
+        __syncthreads();
+        float phi2 = 0.f;
+        double acc_e = 0.0, acc_n = 0.0;
         for (uint32_t rb = warp * RPW; rb < q; rb += nwarps * RPW) {
             uint32_t row = rb + sub;
             bool valid = row < q;
             uint32_t c = valid ? a.cnt[row] : 0u;
             uint64_t base = (uint64_t)row * P;
-            double2 yv = row_apply<LPR, double2>(a.col, a.cid, c, base, coef, x, lane);
+            double2 yv = row_apply<LPR, double2>(a.col, a.cid, c, base, coef, x, lane);   // s (H x) off the diagonal
             if (valid && lane == 0) {
                 double2 xi = x[row];
-                double d = a.diag[row];
+                double d = s * a.diag[row];
                 yv.x = fma(d, xi.x, yv.x);
                 yv.y = fma(d, xi.y, yv.y);
-                double2 phi = make_double2(s * yv.y, -s * yv.x);     // (-i s) y
+                double2 phi = make_double2(yv.y, -yv.x);            // (-i) s H x
                 y[row] = phi;
                 if (a.terms && n <= a.term_max) reinterpret_cast<double2*>(a.terms)[(size_t)(n - 1) * q + row] = phi;
                 double2 rr = (n == 1) ? xi : a.r[row];
                 rr.x += phi.x;
                 rr.y += phi.y;
                 a.r[row] = rr;
-                acc[0] += phi.x * phi.x + phi.y * phi.y;
-                acc[1] += rr.x * rr.x + rr.y * rr.y;
+                float p0 = mag_scaled_f32(phi.x), p1 = mag_scaled_f32(phi.y);
+                phi2 = __fmaf_rn(p0, p0, __fmaf_rn(p1, p1, phi2));
                 if (n == 1) {
-                    acc[2] += xi.x * yv.x + xi.y * yv.y;            // Re(conj(c') H c')
-                    acc[3] += xi.x * xi.x + xi.y * xi.y;
+                    acc_e = fma(xi.x, yv.x, fma(xi.y, yv.y, acc_e));     // Re(conj(c') dt H c')
+                    acc_n = fma(xi.x, xi.x, fma(xi.y, xi.y, acc_n));
                 }
             }
         }
+        double acc[4] = {(double)phi2, acc_e, acc_n, 0.0};
         double* part = a.partials + (size_t)(n & 1) * G * 4;
         double* tot = a.totals + (n & 1) * 4;
         block_sum<kBlock, 4>(acc, part + 4 * blockIdx.x);
@@ -186,22 +213,20 @@ __global__ void __launch_bounds__(kBlock) k_taylor_f64(TaylorArgs a)
         if (threadIdx.x < 4) tsh[threadIdx.x] = __ldcg(tot + threadIdx.x);
         __syncthreads();
         nd = n;
-        r2 = tsh[1];
         if (n == 1) {
-            E = tsh[2];
-            n0 = tsh[3];
+            E = tsh[1] / a.p.dt;
+            n0 = tsh[2];
         }
-        if (fixed <= 0 && n >= 2 && tsh[0] <= a.p.tol2 * tsh[1]) {
+        if (fixed <= 0 && n >= 2 && tsh[0] <= a.p.tol2 * n0 * (double)kScale2) {
             conv = true;
             break;
         }
         x = y;
         y = (y == a.ta) ? a.tb : a.ta;
-        __syncthreads();
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         ctr->nterms = nd;
-        ctr->norm_r = r2;
+        ctr->norm_r = 0.0;
         ctr->norm_phi0 = n0;
         ctr->energy = E;
         if (!conv && fixed <= 0 && atomicCAS(&ctr->err, 0, (int)kErrNoConverge) == 0) {
@@ -615,23 +640,23 @@ __global__ void __launch_bounds__(kBlock) k_taylor_c64(TaylorArgs a)
     }
 }
 
+// Co-resident blocks per SM of the propagator variant that the precision
+// selects (PACES_C128, PACES_DW or PACES_C64_SPMV).
 template <int LPR>
-static int occupancy()
+static int occupancy(int precision)
 {
-    int n1 = 0, n2 = 0, n3 = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n1, k_taylor_f64<LPR>, kBlock, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n2, k_taylor_dw<LPR>, kBlock, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n3, k_taylor_c64<LPR>, kBlock, 0);
-    int n = n1 < n2 ? n1 : n2;
-    return n < n3 ? n : n3;
+    int n = 0;
+    const void* fn = precision == PACES_C128 ? (const void*)k_taylor_f64<LPR>
+                   : precision == PACES_C64_SPMV ? (const void*)k_taylor_c64<LPR> : (const void*)k_taylor_dw<LPR>;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, kBlock, 0);
+    return n;
 }
 
-int taylor_blocks_per_sm(int lpr, int c64)
+int taylor_blocks_per_sm(int lpr, int precision)
 {
-    (void)c64;
-    if (lpr == 1) return occupancy<1>();
-    if (lpr == 4) return occupancy<4>();
-    return occupancy<8>();
+    if (lpr == 1) return occupancy<1>(precision);
+    if (lpr == 4) return occupancy<4>(precision);
+    return occupancy<8>(precision);
 }
 
 int launch_taylor(const Bufs& b, const TaylorParams& p, cudaStream_t st)

@@ -84,6 +84,13 @@ extern "C" paces_status paces_expand_noalloc(const paces_params* params, const u
         return s;
     }
     const int W = L.words, D = M->D;
+    // every input key needs 8 bytes of winner mask in the scratch array, so a
+    // larger n_in cannot fit; rejecting it first keeps the size products below
+    // far from overflow
+    if (n_in > (int64_t)(PACES_NOALLOC_SCRATCH_BYTES / 8) || n_in >= (int64_t)kCand / (D + 1)) {
+        delete M;
+        return PACES_ERR_CAPACITY;
+    }
     int64_t need = 0;
     need_bytes(params, n_in, max_out, &need);
     if (need > (int64_t)PACES_NOALLOC_SCRATCH_BYTES || n_in * (int64_t)D >= (int64_t)kCand) {

@@ -670,8 +670,8 @@ paces_status save_checkpoint(paces_t h)
 }
 
 
-// Algorithmic bytes of one step from its record (the per-unit figures of the
-// design notes); fills bytes[5].
+// Algorithmic bytes of one step from its record (the per-unit figures stated
+// at paces_stage_stats); fills bytes[5].
 void step_bytes(paces_t h, const double* r, double q_in, bool truncated, double* bytes)
 {
     double W8 = 8.0 * h->W, q = r[PACES_OBS_ROWS], kept = r[PACES_OBS_KEPT];
@@ -863,11 +863,12 @@ paces_status paces_create(const paces_params* params, const paces_allocator* all
     b.batch = h->R;
     b.G = std::min(kMaxChunkBlocks, h->sms * 4);
     b.grid = h->sms * 8;
-    int bps = taylor_blocks_per_sm(h->lpr, 0);
+    const int prec = h->prm.precision;
+    int bps = taylor_blocks_per_sm(h->lpr, prec);
     if (bps < 1) bps = 1;
     b.taylor_grid = h->sms * bps;
-    int bps_max = std::max(std::max(taylor_blocks_per_sm(1, 0), taylor_blocks_per_sm(4, 0)),
-                           taylor_blocks_per_sm(8, 0));
+    int bps_max = std::max(std::max(taylor_blocks_per_sm(1, prec), taylor_blocks_per_sm(4, prec)),
+                           taylor_blocks_per_sm(8, prec));
     b.rec_len = PACES_OBS_FIXED + 2 * N * h->R + (h->R > 1 ? 2 * h->R : 0);
     {   // bits each key word uses: the product of the radices packed into it
         unsigned __int128 prod[PACES_MAX_WORDS];
@@ -1423,7 +1424,7 @@ paces_status paces_get_tuning(paces_t h, paces_tuning* out)
     out->grid_blocks_per_sm = h->b.grid / h->sms;
     out->chunk_blocks_per_sm = h->b.G / h->sms;
     out->use_graphs = h->use_graphs ? 1 : 0;
-    out->max_taylor_blocks_per_sm = taylor_blocks_per_sm(h->lpr, 0);
+    out->max_taylor_blocks_per_sm = taylor_blocks_per_sm(h->lpr, h->prm.precision);
     return PACES_OK;
 }
 
@@ -1434,7 +1435,7 @@ paces_status paces_set_tuning(paces_t h, const paces_tuning* in)
         return fail(h, PACES_ERR_STATE, "recorded steps must be replayed with the tuning they ran with");
     int lpr = in->taylor_lanes_per_row;
     if (lpr != 1 && lpr != 4 && lpr != 8) return fail(h, PACES_ERR_INVALID, "lanes per row must be 1, 4 or 8");
-    int maxb = taylor_blocks_per_sm(lpr, 0);
+    int maxb = taylor_blocks_per_sm(lpr, h->prm.precision);
     if (in->taylor_blocks_per_sm < 1 || in->taylor_blocks_per_sm > maxb)
         return fail(h, PACES_ERR_INVALID, "propagator blocks per SM must be 1.." + std::to_string(maxb));
     if (in->grid_blocks_per_sm < 1 || in->grid_blocks_per_sm > 32) return fail(h, PACES_ERR_INVALID, "grid blocks");

@@ -116,7 +116,7 @@ int launch_meta_from_keys(const Bufs& b, int gen, uint32_t n, cudaStream_t st);
 int launch_export_csr(const Bufs& b, uint32_t q, const uint64_t* off, int32_t* cols,
                       double* vals, cudaStream_t st);
 
-int taylor_blocks_per_sm(int lpr, int c64);
+int taylor_blocks_per_sm(int lpr, int precision);
 
 // Reverse pass of one step (kern_adjoint.cu).
 int launch_adj_obs(const Bufs& b, int gen, const void* vec, const double* dLdP, const double2* wC, double2* gbar,

@@ -9,8 +9,8 @@ The five workloads stand in for the paper's parameterised model runs (the 1D
 Holstein benchmark of Sec. 4 and the 1D/2D/3D aggregates of Sec. 5): they are
 Holstein models (Eq. holstein) with omega = 1 (time in 1/omega_0) and a hard
 phonon cap per site.  Choices the paper leaves open (m, m_init, theta, the
-boundary of the disorder chain, the start states) are the readings recorded in
-the design notes.
+boundary of the disorder chain, the start states) are fixed here, each beside
+its workload.
 """
 from __future__ import annotations
 

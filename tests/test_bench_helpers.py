@@ -1,27 +1,48 @@
-"""Host-side helpers of bench.py: the stored propagator traffic is reported
-only for the library code it was captured on (comments ignored) and the bench
-window it was captured at; the replica reduction lives in test_bench_ranks."""
+"""Host-side helpers of bench.py: the propagator traffic scaled from a stored
+small-case capture is reported only for the library code it was captured on
+(comments ignored); the CPU description; the replica reduction lives in
+test_bench_ranks."""
 import os
 import shutil
 
 import bench
 
 
-def test_stored_traffic_is_keyed_on_code_and_window(tmp_path, monkeypatch):
-    """A summary in the committed format is read back only for the library
-    code it names and the window it was taken at."""
+def test_scaled_traffic_is_keyed_on_code(tmp_path, monkeypatch):
+    """A summary in the committed format gives DRAM/algorithmic bytes of the
+    small case, applied to the window's algorithmic bytes, and only for the
+    library code it names."""
     src = os.path.join(bench.ROOT, "paper_2603_07341_gb300", "csrc")
     shutil.copytree(src, tmp_path / "paper_2603_07341_gb300" / "csrc")
     (tmp_path / "profiles").mkdir()
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     h = bench.library_source_hash()
-    prof = tmp_path / "profiles" / "k_taylor_dw_ring16_traffic.md"
-    prof.write_text("# summary\n\n- library source sha256[:16]: %s\n- window end step: 500\n"
-                    "- dram bytes per launch: 699490000000\n" % h)
-    assert bench.traffic_from_profile(500) == 699490000000.0
-    assert bench.traffic_from_profile(499) is None
+    prof = tmp_path / "profiles" / "k_taylor_f64_ring16_small_traffic.md"
+    prof.write_text("# summary\n\n- library source sha256[:16]: %s\n- case: ring16 step 180\n"
+                    "- dram bytes per launch: 30000000000\n- algorithmic bytes per launch: 25000000000\n" % h)
+    t, note = bench.traffic_scaled("k_taylor_f64", 4.0e11)
+    assert abs(t - 1.2 * 4.0e11) < 1.0 and "ring16 step 180" in note
+    assert bench.traffic_scaled("k_taylor_dw", 4.0e11) == (None, None)
     prof.write_text(prof.read_text().replace(h, "0" * 16))
-    assert bench.traffic_from_profile(500) is None
+    assert bench.traffic_scaled("k_taylor_f64", 4.0e11) == (None, None)
+
+
+def test_cpu_info_reports_cores_and_model():
+    cores, model = bench.cpu_info()
+    assert cores >= 1 and isinstance(model, str) and model
+
+
+def test_taylor_counts_per_row_and_term():
+    """Two records: 10 rows with 30 stored entries (20 off the diagonal) and 3
+    terms, then 20 rows with 60 entries and 2 terms."""
+    import numpy as np
+    rec = np.zeros((2, 12))
+    rec[0, 6], rec[0, 8], rec[0, 9] = 10, 30, 3
+    rec[1, 6], rec[1, 8], rec[1, 9] = 20, 60, 2
+    units, bytes_, flops = bench.taylor_counts(rec, 1)
+    assert units == 10 * 3 + 20 * 2
+    assert bytes_ == (10 * 57 + 20 * 5 + 2 * (10 * 73 + 20 * 5)) + (20 * 57 + 40 * 5 + 1 * (20 * 73 + 40 * 5))
+    assert flops == 3 * (10 * 7 + 20 * 4) + 2 * (20 * 7 + 40 * 4)
 
 
 def test_source_hash_ignores_comments_but_not_code(tmp_path, monkeypatch):
