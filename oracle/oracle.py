@@ -26,27 +26,36 @@ ST_NAMES = ("norm", "norm_phi0", "energy", "C_re", "C_im", "rows", "kept", "nnz"
             "terms", "norm_before", "time")
 
 
-def build_oracle(force: bool = False) -> str:
-    """Compile the oracle with gcc (-ffp-contract=off: no FMA contraction)."""
-    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
-    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= max(
+MUTANTS = ("NO_RESCUE", "OPEN3D_AXES", "ENERGY_CONJ")
+
+
+def build_oracle(force: bool = False, mutant: str | None = None) -> str:
+    """Compile the oracle with gcc (-ffp-contract=off: no FMA contraction).
+
+    mutant: one of MUTANTS, for the pin tests only -- a second library with
+    that planted mistake compiled in (the default build has none)."""
+    lib = _LIB if mutant is None else _LIB.replace("liboracle.so", "liboracle_%s.so" % mutant.lower())
+    if mutant is not None and mutant not in MUTANTS:
+        raise ValueError(mutant)
+    os.makedirs(os.path.dirname(lib), exist_ok=True)
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= max(
             os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "paces_oracle.h"))):
-        return _LIB
-    tmp = _LIB + ".%d.tmp" % os.getpid()
-    cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared",
-           "-o", tmp, _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB)
-    return _LIB
+        return lib
+    tmp = lib + ".%d.tmp" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared"]
+    if mutant is not None:
+        cmd.append("-DOR_MUTANT_%s" % mutant)
+    subprocess.run(cmd + ["-o", tmp, _SRC, "-lm"], check=True)
+    os.replace(tmp, lib)
+    return lib
 
 
-_lib = None
+_libs = {}
 
 
-def _load():
-    global _lib
-    if _lib is None:
-        lib = C.CDLL(build_oracle())
+def _load(mutant=None):
+    if mutant not in _libs:
+        lib = C.CDLL(build_oracle(mutant=mutant))
         P = C.c_void_p
         dp, ip = C.POINTER(C.c_double), C.POINTER(C.c_int)
         lib.or_create.restype = P
@@ -70,8 +79,8 @@ def _load():
         lib.or_populations.argtypes = [P, dp, dp]
         lib.or_record.argtypes = [P, C.c_int]
         lib.or_backward.argtypes = [P, C.c_int, dp, dp, dp, dp]
-        _lib = lib
-    return _lib
+        _libs[mutant] = lib
+    return _libs[mutant]
 
 
 def _dp(a):
@@ -95,13 +104,14 @@ class Oracle:
     caps ``cap`` (K_j = d_pho - 1), hopping ``J`` times the lattice pattern
     (ring / open chain / open 2D / open 3D nearest neighbour, or all pairs
     J / r^3).  ``m`` and ``m_init`` are the neighbour orders of Eq. H_eff
-    (``m_init < 0``: closure).
+    (``m_init < 0``: closure).  ``mutant`` (pin tests only) selects a build
+    with one planted mistake, see ``MUTANTS``.
     """
 
     def __init__(self, n_sites, lattice_kind=0, dims=(0, 0, 0), coupling_kind=0, J=1.0,
                  eps=None, omega=None, g=None, cap=None, m=2, m_init=10, tol=1e-15,
-                 nmax=200, fixed_terms=0, J_explicit=None):
-        lib = _load()
+                 nmax=200, fixed_terms=0, J_explicit=None, mutant=None):
+        lib = _load(mutant)
         self.N = int(n_sites)
         N = self.N
         f = lambda v, d: np.ascontiguousarray(np.broadcast_to(

@@ -28,6 +28,11 @@
  *
  * Representation: a basis state is the int tuple (s, n_0, ..., n_{N-1}); rows
  * of H_eff are stored in order in a growable array with a linear-probing index.
+ *
+ * Planted mistakes: the pin tests compile this file a second time with one of
+ * the macros OR_MUTANT_NO_RESCUE, OR_MUTANT_OPEN3D_AXES or OR_MUTANT_ENERGY_CONJ
+ * defined, each a plausible slip in one function, and check that the pin of
+ * that function fails.  The default build defines none of them.
  */
 #include "paces_oracle.h"
 
@@ -198,6 +203,9 @@ static double hop_pattern(int lattice_kind, int coupling_kind, const int* dims, 
     if (lattice_kind == 1) { d0 = N; d1 = 1; }
     if (lattice_kind == 2) { d0 = dims[0]; d1 = dims[1]; }
     if (lattice_kind == 3) { d0 = dims[0]; d1 = dims[1]; }
+#ifdef OR_MUTANT_OPEN3D_AXES
+    int t0 = d0; d0 = d1; d1 = t0;   /* planted: the two inner extents exchanged */
+#endif
     int ax = a % d0, ay = (a / d0) % d1, az = a / (d0 * d1);
     int bx = b % d0, by = (b / d0) % d1, bz = b / (d0 * d1);
     double dx = ax - bx, dy = ay - by, dz = az - bz;
@@ -503,7 +511,11 @@ static int taylor(oracle_t* o, double dt, cplx* c, int* nterms_out, double* ener
         apply_h(o, phi, y);
         if (n == 1) {
             double e = 0.0;
+#ifdef OR_MUTANT_ENERGY_CONJ
+            for (int i = 0; i < q; ++i) e += creal(c[i] * y[i]);        /* planted: conj dropped */
+#else
             for (int i = 0; i < q; ++i) e += creal(conj(c[i]) * y[i]);
+#endif
             *energy = e;
         }
         cplx f = -I * dt / (double)n;
@@ -615,6 +627,9 @@ int or_step(oracle_t* o, double dt, double theta, const unsigned char* keep_over
         for (int i = 0; i < q; ++i) {
             int j = rs_find(&old, rs_row(&o->rows, i));
             o->last_from[i] = j;
+#ifdef OR_MUTANT_NO_RESCUE
+            if (i >= kept) j = -1;          /* planted: re-admitted rows restart at 0 */
+#endif
             o->c[i] = (j >= 0) ? cold[j] : 0.0;
         }
         rs_free(&old);

@@ -503,3 +503,126 @@ def test_kept_set_is_in_ascending_basis_order():
         w = np.abs(a_prev) ** 2
         want = {tuple(r) for r in t_prev[w >= 2e-3 ** 2]}
         assert {tuple(r) for r in M} == want
+
+
+# ---------------------------------------------------------------- rescue, 3D geometry, energy value
+def _ring4_dense():
+    N = 4
+    eps = np.array([0.1, -0.2, 0.3, 0.0])
+    H, D, strides = dense_holstein(ring_hop(N, 1.0), eps, [1.0] * N, [1.0] * N, [4] * N)
+    return eps, H, D, strides
+
+
+def _rescue_run(mutant=None, nsteps=60):
+    """ring4 with m = 30, a radius from which every kept set reaches the whole
+    2500-state space, truncated hard (theta = 1e-2).  Rescue (Sec. 3.3,
+    post-adaptation detruncation) gives every dropped amplitude back, so the
+    trajectory is exp(-iHt) psi0 although most rows fall below theta."""
+    eps, H, D, strides = _ring4_dense()
+    U = propagator(H)
+    o = Oracle(4, W.RING, J=1.0, eps=eps, omega=1.0, g=1.0, cap=4, m=30, m_init=-1, mutant=mutant)
+    o.set_state([0], [[0] * 4], [1.0])
+    psi0 = state_vector(o, D, strides, H.shape[0])
+    kept = []
+    for k in range(1, nsteps + 1):
+        o.step(0.05, 1e-2)
+        st = o.stats()
+        assert st["rows"] == 2500
+        kept.append(st["kept"])
+    err = np.linalg.norm(state_vector(o, D, strides, H.shape[0]) - U(nsteps * 0.05, psi0))
+    return err, kept
+
+
+def test_rescue_restores_every_dropped_amplitude():
+    err, kept = _rescue_run()
+    assert max(kept[1:]) < 2500 and min(kept[1:]) < 500, kept      # truncation really dropped rows
+    assert err <= 1e-11, err
+
+
+def test_rescue_pin_fails_without_rescue():
+    err, _ = _rescue_run(mutant="NO_RESCUE")
+    assert err > 1e-3, err
+
+
+def _cubic_adjacency(dims):
+    """Open simple-cubic nearest neighbours from the coordinates, built here:
+    site j = x + d0 (y + d1 z)."""
+    d0, d1, d2 = dims
+    coords = [(x, y, z) for z in range(d2) for y in range(d1) for x in range(d0)]
+    N = len(coords)
+    A = np.zeros((N, N))
+    for a, ca in enumerate(coords):
+        for b, cb in enumerate(coords):
+            if sum(abs(u - v) for u, v in zip(ca, cb)) == 1:
+                A[a, b] = 1.0
+    assert coords[1] == (1, 0, 0) and coords[d0] == (0, 1, 0) and coords[d0 * d1] == (0, 0, 1)
+    return A
+
+
+@pytest.mark.parametrize("dims", [(2, 2, 2), (3, 2, 2), (2, 3, 4)])
+def test_open3d_hopping_matches_hand_built_lattice(dims):
+    """Eq. holstein on the open simple-cubic aggregates of Sec. 5: J_ab = J
+    for nearest neighbours.  Every site of the 2x2x2 cube is a corner with
+    three neighbours."""
+    N = int(np.prod(dims))
+    o = Oracle(N, W.OPEN3D, dims=dims, J=0.7, omega=1.0, g=0.0, cap=1, m=1, m_init=1)
+    A = _cubic_adjacency(dims)
+    assert np.array_equal(o.hopping(), 0.7 * A)
+    if dims == (2, 2, 2):
+        assert np.all(A.sum(1) == 3)
+
+
+def test_open3d_pin_fails_on_exchanged_axes():
+    o = Oracle(12, W.OPEN3D, dims=(3, 2, 2), J=1.0, omega=1.0, g=0.0, cap=1, m=1, m_init=1,
+               mutant="OPEN3D_AXES")
+    assert not np.array_equal(o.hopping(), _cubic_adjacency((3, 2, 2)))
+
+
+def test_open3d_g0_autocorrelation_matches_eigh():
+    """g = 0 on the 3x2x2 aggregate: the phonons stay in vacuum and
+    C(t) = sum_k |<k|mu>|^2 exp(-i E_k t) from eigh of the exciton matrix built
+    from the hand-made lattice (bright state mu = sum_s |s>/sqrt(N))."""
+    dims = (3, 2, 2)
+    N = 12
+    A = _cubic_adjacency(dims)
+    E, V = np.linalg.eigh(-1.0 * A)
+    mu = np.ones(N) / np.sqrt(N)
+    w = (V.T @ mu) ** 2
+    o = Oracle(N, W.OPEN3D, dims=dims, J=-1.0, omega=1.0, g=0.0, cap=2, m=2, m_init=2)
+    o.set_state(np.arange(N), np.zeros((N, N), dtype=np.int32), mu)
+    dt = 0.05
+    for k in range(1, 81):
+        o.step(dt, 1e-12)
+        st = o.stats()
+        C = st["C_re"] + 1j * st["C_im"]
+        assert abs(C - np.sum(w * np.exp(-1j * E * k * dt))) < 1e-12
+
+
+def _energy_run(mutant=None):
+    """The energy record of a step is <c'|P H P|c'> with c' the rescued state
+    entering the propagator (Sec. 3.5).  c' is rebuilt here from the previous
+    step's rows restricted to the new H_eff, and E compared with c'^dag H c'
+    for the dense Kronecker-product H (P c' = c', so P H P gives the same)."""
+    eps, H, D, strides = _ring4_dense()
+    o = Oracle(4, W.RING, J=1.0, eps=eps, omega=1.0, g=1.0, cap=4, m=2, m_init=2, mutant=mutant)
+    o.set_state([0, 1], [[0] * 4, [1, 0, 0, 0]], [0.6, 0.8j])
+    worst = 0.0
+    prev = state_vector(o, D, strides, H.shape[0])
+    for _ in range(25):
+        o.step(0.05, 2e-3)
+        t, _ = o.rows()
+        cp = np.zeros_like(prev)
+        idx = dense_index(t, D, strides)
+        cp[idx] = prev[idx]
+        E_ref = float(np.real(np.vdot(cp, H @ cp)))
+        worst = max(worst, abs(o.stats()["energy"] - E_ref) / max(1.0, abs(E_ref)))
+        prev = state_vector(o, D, strides, H.shape[0])
+    return worst
+
+
+def test_energy_value_is_the_expectation_in_the_rescued_state():
+    assert _energy_run() < 1e-13
+
+
+def test_energy_pin_fails_on_a_dropped_conjugate():
+    assert _energy_run(mutant="ENERGY_CONJ") > 1e-3
