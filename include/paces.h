@@ -115,6 +115,11 @@ typedef struct {
                                 /* = one model); for R > 1 eps holds R*N site energies, */
                                 /* realisation r in eps[r*N .. r*N + N)                 */
     int32_t reserved0;
+    double taylor_xmax;         /* substepping (App. C.1): a step runs as               */
+                                /* s = ceil(rho dt / xmax) Taylor series of dt / s,     */
+                                /* rho = the largest absolute row sum of H over H_eff   */
+                                /* (each term rounded up to 2^-20); 0 = 8; < 0 = always */
+                                /* one series.  More than 1024 series: NOCONVERGE.      */
 } paces_params;
 
 /* Ensembles (batch = R > 1).  The R realisations share every parameter except
@@ -269,7 +274,9 @@ paces_status paces_get_hamiltonian(paces_t h, int32_t* cnt, int32_t* cols, doubl
 #define PACES_OBS_NNZ 8          /* stored entries of P H P incl. the diagonal  */
 #define PACES_OBS_TERMS 9        /* Taylor terms used                           */
 #define PACES_OBS_NORM_BEFORE 10 /* ||c||^2 before truncation                   */
-#define PACES_OBS_FIXED 12       /* fields before P_s                           */
+#define PACES_OBS_SUBSTEPS 11    /* Taylor series the step ran (substeps)       */
+#define PACES_OBS_HBOUND 12      /* rho, the bound on ||P H P|| that set them    */
+#define PACES_OBS_FIXED 14       /* fields before P_s                           */
 int32_t paces_record_len(paces_t h);
 /* Number of records held. */
 paces_status paces_num_records(paces_t h, int64_t* n);

@@ -23,7 +23,7 @@ _LIB = os.path.join(_HERE, "_build", "liboracle.so")
 
 OR_OK, OR_INVALID, OR_NOMEM, OR_NOCONVERGE, OR_STATE = 0, 1, 3, 4, 6
 ST_NAMES = ("norm", "norm_phi0", "energy", "C_re", "C_im", "rows", "kept", "nnz",
-            "terms", "norm_before", "time")
+            "terms", "norm_before", "time", "substeps", "hbound")
 
 
 MUTANTS = ("NO_RESCUE", "OPEN3D_AXES", "ENERGY_CONJ")
@@ -62,6 +62,7 @@ def _load(mutant=None):
         lib.or_create.argtypes = [C.c_int, C.c_int, ip, C.c_int, C.c_double, dp, dp, dp, dp,
                                   ip, C.c_int, C.c_int, C.c_double, C.c_int, C.c_int]
         lib.or_destroy.argtypes = [P]
+        lib.or_set_xmax.argtypes = [P, C.c_double]
         lib.or_get_hopping.argtypes = [P, dp]
         lib.or_set_state.argtypes = [P, C.c_int, ip, ip, dp]
         lib.or_step.argtypes = [P, C.c_double, C.c_double, C.POINTER(C.c_ubyte), C.c_int]
@@ -104,13 +105,15 @@ class Oracle:
     caps ``cap`` (K_j = d_pho - 1), hopping ``J`` times the lattice pattern
     (ring / open chain / open 2D / open 3D nearest neighbour, or all pairs
     J / r^3).  ``m`` and ``m_init`` are the neighbour orders of Eq. H_eff
-    (``m_init < 0``: closure).  ``mutant`` (pin tests only) selects a build
+    (``m_init < 0``: closure).  ``xmax`` bounds rho dt / s, the length of each
+    of the s Taylor series a step is split into (rho: largest absolute row sum
+    of H over H_eff; ``xmax <= 0``: one series).  ``mutant`` (pin tests only) selects a build
     with one planted mistake, see ``MUTANTS``.
     """
 
     def __init__(self, n_sites, lattice_kind=0, dims=(0, 0, 0), coupling_kind=0, J=1.0,
                  eps=None, omega=None, g=None, cap=None, m=2, m_init=10, tol=1e-15,
-                 nmax=200, fixed_terms=0, J_explicit=None, mutant=None):
+                 nmax=200, fixed_terms=0, J_explicit=None, xmax=8.0, mutant=None):
         lib = _load(mutant)
         self.N = int(n_sites)
         N = self.N
@@ -128,6 +131,7 @@ class Oracle:
         if not self._h:
             raise OracleError(OR_INVALID, "or_create")
         self._lib = lib
+        lib.or_set_xmax(self._h, float(xmax))
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -210,7 +214,7 @@ class Oracle:
         return cnt, cols[:nnz], vals[:nnz], diag[:q]
 
     def stats(self):
-        st = np.zeros(12)
+        st = np.zeros(len(ST_NAMES))
         self._lib.or_stats(self._h, _dp(st))
         return dict(zip(ST_NAMES, st))
 

@@ -143,7 +143,9 @@ typedef struct {         /* one recorded step, for the adjoint */
     int* from;           /* rescue map: new row -> previous row or -1 */
     int nprev;
     cplx* cprime;        /* amplitudes entering the propagator  */
-    int nterms;
+    int nterms;          /* terms over all substeps             */
+    int nsub;            /* series the step was split into      */
+    int* sub_terms;      /* terms of each series                */
     double dt;
 } step_rec;
 
@@ -156,6 +158,7 @@ struct oracle {
     int m, m_init;
     double tol;
     int nmax, fixed_terms;
+    double xmax;         /* substepping: series length bound rho dt / s <= xmax */
 
     rowset rows;         /* current H_eff                         */
     cplx* c;             /* amplitudes on rows                    */
@@ -257,6 +260,7 @@ oracle_t* or_create(int n_sites, int lattice_kind, const int* dims, int coupling
     o->tol = tol;
     o->nmax = nmax;
     o->fixed_terms = fixed_terms;
+    o->xmax = 8.0;
     rs_init(&o->rows, o->len);
     rs_init(&o->init, o->len);
     o->lvlcap = 64;
@@ -264,9 +268,17 @@ oracle_t* or_create(int n_sites, int lattice_kind, const int* dims, int coupling
     return o;
 }
 
+int or_set_xmax(oracle_t* o, double xmax)
+{
+    if (!o) return OR_INVALID;
+    o->xmax = xmax;
+    return OR_OK;
+}
+
 static void free_recs(oracle_t* o)
 {
     for (int i = 0; i < o->nrec; ++i) {
+        free(o->rec[i].sub_terms);
         free(o->rec[i].tuples);
         free(o->rec[i].from);
         free(o->rec[i].cprime);
@@ -494,43 +506,93 @@ static double norm2(const cplx* v, int n)
     return s;
 }
 
-/* r = sum_n (-i dt H)^n / n! c via phi_n = (-i dt / n) H phi_{n-1} (App. C.1) */
-static int taylor(oracle_t* o, double dt, cplx* c, int* nterms_out, double* energy)
+/* Bound rho on ||P H P||_2: the largest absolute row sum of H over the rows of
+ * H_eff (a row sum of H bounds that of P H P, and for a Hermitian matrix the
+ * largest row sum bounds the spectral norm).  Each term is rounded up to a
+ * multiple of 2^-20 and the terms are added as integers, so the value does not
+ * depend on the order of the additions. */
+static unsigned long long up20(double x) { return (unsigned long long)ceil(fabs(x) * 1048576.0); }
+
+static unsigned long long row_bound(const oracle_t* o, const int* t)
+{
+    int N = o->N, s = t[0], ns = t[1 + s];
+    unsigned long long b = up20(o->eps[s]);
+    for (int j = 0; j < N; ++j) b += up20(o->omega[j]) * (unsigned long long)t[1 + j];
+    for (int u = 0; u < N; ++u)
+        if (u != s) b += up20(o->Jm[u * N + s]);
+    if (o->g[s] != 0.0) {
+        if (ns < o->cap[s]) b += up20(o->g[s] * sqrt((double)(ns + 1)));
+        if (ns > 0) b += up20(o->g[s] * sqrt((double)ns));
+    }
+    return b;
+}
+
+#define OR_MAX_SUB 1024
+
+/* Number of series a step of length dt is split into: s = ceil(rho dt / xmax)
+ * (1 when xmax <= 0).  0 when more than OR_MAX_SUB would be needed. */
+static int substeps(const oracle_t* o, double dt, double* rho_out)
+{
+    unsigned long long rb = 0;
+    for (int i = 0; i < o->rows.nrows; ++i) {
+        unsigned long long b = row_bound(o, rs_row(&o->rows, i));
+        if (b > rb) rb = b;
+    }
+    double rho = (double)rb / 1048576.0;
+    *rho_out = rho;
+    if (o->xmax <= 0.0) return 1;
+    double ns = ceil(rho * dt / o->xmax);
+    if (ns > (double)OR_MAX_SUB) return 0;
+    return ns < 1.0 ? 1 : (int)ns;
+}
+
+/* c <- exp(-i dt H_P) c as nsub successive Taylor series of length h = dt/nsub,
+ * each r = sum_n (-i h H)^n / n! v via phi_n = (-i h / n) H phi_{n-1}
+ * (App. C.1), stopping at the first n >= 2 with ||phi_n||^2 <= tol^2 ||r||^2.
+ * sub_terms[j] receives the terms of series j; energy = <c|H_P|c> of the input. */
+static int taylor(oracle_t* o, double dt, int nsub, cplx* c, int* sub_terms, int* nterms_out, double* energy)
 {
     int q = o->hp_rows;
     cplx* phi = (cplx*)malloc(sizeof(cplx) * ((size_t)q + 1));
     cplx* y = (cplx*)malloc(sizeof(cplx) * ((size_t)q + 1));
     cplx* r = (cplx*)malloc(sizeof(cplx) * ((size_t)q + 1));
     if (!phi || !y || !r) return OR_NOMEM;
-    memcpy(phi, c, sizeof(cplx) * (size_t)q);
-    memcpy(r, c, sizeof(cplx) * (size_t)q);
-    int converged = 0, n = 0;
+    double h = dt / (double)nsub;
+    int converged = 1, total = 0;
     int nlimit = o->fixed_terms > 0 ? o->fixed_terms : o->nmax;
     *energy = 0.0;
-    for (n = 1; n <= nlimit; ++n) {
-        apply_h(o, phi, y);
-        if (n == 1) {
-            double e = 0.0;
+    for (int j = 0; j < nsub && converged; ++j) {
+        memcpy(phi, c, sizeof(cplx) * (size_t)q);
+        memcpy(r, c, sizeof(cplx) * (size_t)q);
+        int done = 0, n = 0;
+        for (n = 1; n <= nlimit; ++n) {
+            apply_h(o, phi, y);
+            if (j == 0 && n == 1) {
+                double e = 0.0;
 #ifdef OR_MUTANT_ENERGY_CONJ
-            for (int i = 0; i < q; ++i) e += creal(c[i] * y[i]);        /* planted: conj dropped */
+                for (int i = 0; i < q; ++i) e += creal(c[i] * y[i]);        /* planted: conj dropped */
 #else
-            for (int i = 0; i < q; ++i) e += creal(conj(c[i]) * y[i]);
+                for (int i = 0; i < q; ++i) e += creal(conj(c[i]) * y[i]);
 #endif
-            *energy = e;
+                *energy = e;
+            }
+            cplx f = -I * h / (double)n;
+            for (int i = 0; i < q; ++i) {
+                phi[i] = f * y[i];
+                r[i] += phi[i];
+            }
+            if (o->fixed_terms > 0) continue;
+            double a = norm2(phi, q), b = norm2(r, q);
+            if (n >= 2 && a <= o->tol * o->tol * b) { done = 1; break; }
         }
-        cplx f = -I * dt / (double)n;
-        for (int i = 0; i < q; ++i) {
-            phi[i] = f * y[i];
-            r[i] += phi[i];
-        }
-        if (o->fixed_terms > 0) continue;
-        double a = norm2(phi, q), b = norm2(r, q);
-        if (n >= 2 && a <= o->tol * o->tol * b) { converged = 1; break; }
+        if (o->fixed_terms > 0) { done = 1; n = o->fixed_terms; }
+        if (!done) { converged = 0; n = nlimit; }
+        if (sub_terms) sub_terms[j] = n;
+        total += n;
+        memcpy(c, r, sizeof(cplx) * (size_t)q);
     }
-    if (o->fixed_terms > 0) { converged = 1; n = o->fixed_terms; }
-    memcpy(c, r, sizeof(cplx) * (size_t)q);
     free(phi); free(y); free(r);
-    *nterms_out = n;
+    *nterms_out = total;
     return converged ? OR_OK : OR_NOCONVERGE;
 }
 
@@ -656,12 +718,21 @@ int or_step(oracle_t* o, double dt, double theta, const unsigned char* keep_over
     }
     double n0 = norm2(o->c, q);
     int nterms = 0;
-    double energy = 0.0;
-    int rc = taylor(o, dt, o->c, &nterms, &energy);
+    double energy = 0.0, rho = 0.0;
+    int nsub = substeps(o, dt, &rho);
+    int* sub_terms = (int*)calloc((size_t)(nsub > 0 ? nsub : 1), sizeof(int));
+    if (!sub_terms) return OR_NOMEM;
+    int rc = nsub > 0 ? taylor(o, dt, nsub, o->c, sub_terms, &nterms, &energy) : OR_NOCONVERGE;
     if (o->recording) {
         o->rec[o->nrec - 1].nterms = nterms;
+        o->rec[o->nrec - 1].nsub = nsub;
+        o->rec[o->nrec - 1].sub_terms = sub_terms;
         o->rec[o->nrec - 1].dt = dt;
+    } else {
+        free(sub_terms);
     }
+    o->st[OR_ST_SUBSTEPS] = nsub;
+    o->st[OR_ST_HBOUND] = rho;
     o->time += dt;
     o->fresh = 0;
     o->tstep += 1;
@@ -860,20 +931,39 @@ int or_backward(oracle_t* o, int nsteps_rec, const double* dL_dc_final, const do
     int rc = OR_OK;
     for (int k = nsteps_rec - 1; k >= 0 && rc == OR_OK; --k) {
         const step_rec* R = &o->rec[k];
-        int q = R->nrows, nt = R->nterms;
+        int q = R->nrows;
         rc = load_rec_rows(o, R);
         if (rc) break;
-        /* forward terms of this step, recomputed */
+        /* forward terms of this step, recomputed: series j of the step keeps
+         * phi^(j)_0 .. phi^(j)_{n_j} at phis + (base_j + n) qs, phi^(j)_0 being
+         * the input of series j (c' for j = 0, else the output of series j-1) */
+        int ns = R->nsub;
+        double h = R->dt / (double)ns;
         size_t qs = (size_t)q + 1;
-        cplx* phis = (cplx*)malloc(sizeof(cplx) * (size_t)(nt + 1) * qs);
+        int* base = (int*)malloc(sizeof(int) * ((size_t)ns + 1));
+        if (!base) { rc = OR_NOMEM; break; }
+        base[0] = 0;
+        for (int j = 0; j < ns; ++j) base[j + 1] = base[j] + R->sub_terms[j] + 1;
+        cplx* phis = (cplx*)malloc(sizeof(cplx) * (size_t)base[ns] * qs);
         cplx* y = (cplx*)malloc(sizeof(cplx) * qs);
         cplx* mu = (cplx*)malloc(sizeof(cplx) * qs);
         if (!phis || !y || !mu) { rc = OR_NOMEM; break; }
         memcpy(phis, R->cprime, sizeof(cplx) * (size_t)q);
-        for (int n = 1; n <= nt; ++n) {
-            apply_h(o, phis + (size_t)(n - 1) * qs, y);
-            cplx f = -I * R->dt / (double)n;
-            for (int i = 0; i < q; ++i) phis[(size_t)n * qs + i] = f * y[i];
+        for (int j = 0; j < ns; ++j) {
+            cplx* ph = phis + (size_t)base[j] * qs;
+            if (j > 0) {           /* input of series j = sum of the terms of series j-1 */
+                const cplx* prv = phis + (size_t)base[j - 1] * qs;
+                for (int i = 0; i < q; ++i) {
+                    cplx v = 0.0;
+                    for (int n = 0; n <= R->sub_terms[j - 1]; ++n) v += prv[(size_t)n * qs + i];
+                    ph[i] = v;
+                }
+            }
+            for (int n = 1; n <= R->sub_terms[j]; ++n) {
+                apply_h(o, ph + (size_t)(n - 1) * qs, y);
+                cplx f = -I * h / (double)n;
+                for (int i = 0; i < q; ++i) ph[(size_t)n * qs + i] = f * y[i];
+            }
         }
         if (dL_dC) {   /* C(t_k) = sum_j conj(psi0_j) c(key_j)  =>  gbar_j += psi0_j w_k */
             cplx w = dL_dC[2 * k] + I * dL_dC[2 * k + 1];
@@ -883,26 +973,34 @@ int or_backward(oracle_t* o, int nsteps_rec, const double* dL_dc_final, const do
             }
         }
         if (dL_dP) {   /* P_s(t_k) = sum_{i: site s} |c_i|^2  =>  gbar_i += 2 c_i dL/dP_s */
+            const cplx* last_ph = phis + (size_t)base[ns - 1] * qs;
+            int nl = R->sub_terms[ns - 1];
             for (int i = 0; i < q; ++i) {
                 cplx c = 0.0;
-                for (int n = 0; n <= nt; ++n) c += phis[(size_t)n * qs + i];
+                for (int n = 0; n <= nl; ++n) c += last_ph[(size_t)n * qs + i];
                 gbar[i] += 2.0 * c * dL_dP[(size_t)k * N + rs_row(&o->rows, i)[0]];
             }
         }
-        /* reverse recurrence */
-        memcpy(mu, gbar, sizeof(cplx) * (size_t)q);
-        for (int n = nt; n >= 1; --n) {
-            cplx f = -I * R->dt / (double)n;
-            const cplx* phi_prev = phis + (size_t)(n - 1) * qs;
-            for (int p = 0; p < P; ++p) {
-                apply_dh(o, p, phi_prev, y);
-                cplx s = 0.0;
-                for (int i = 0; i < q; ++i) s += conj(mu[i]) * (f * y[i]);
-                grad[p] += creal(s);
+        /* reverse recurrence, series by series from the last: gbar is the
+         * cotangent of the series' output, mu ends as that of its input */
+        for (int j = ns - 1; j >= 0; --j) {
+            const cplx* ph = phis + (size_t)base[j] * qs;
+            memcpy(mu, gbar, sizeof(cplx) * (size_t)q);
+            for (int n = R->sub_terms[j]; n >= 1; --n) {
+                cplx f = -I * h / (double)n;
+                const cplx* phi_prev = ph + (size_t)(n - 1) * qs;
+                for (int p = 0; p < P; ++p) {
+                    apply_dh(o, p, phi_prev, y);
+                    cplx sacc = 0.0;
+                    for (int i = 0; i < q; ++i) sacc += conj(mu[i]) * (f * y[i]);
+                    grad[p] += creal(sacc);
+                }
+                apply_h(o, mu, y);                     /* B_n^dag mu = (i h/n) H mu */
+                for (int i = 0; i < q; ++i) mu[i] = gbar[i] + conj(f) * y[i];
             }
-            apply_h(o, mu, y);                     /* B_n^dag mu = (i dt/n) H mu */
-            for (int i = 0; i < q; ++i) mu[i] = gbar[i] + conj(f) * y[i];
+            if (j > 0) memcpy(gbar, mu, sizeof(cplx) * (size_t)q);
         }
+        free(base);
         /* mu is now the cotangent of c'; scatter through the rescue map */
         cplx* prev = (cplx*)calloc((size_t)R->nprev + 1, sizeof(cplx));
         for (int i = 0; i < q; ++i)

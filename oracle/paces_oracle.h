@@ -35,6 +35,12 @@ oracle_t* or_create(int n_sites, int lattice_kind, const int* dims, int coupling
                     int m, int m_init, double tol, int nmax, int fixed_terms);
 void or_destroy(oracle_t* o);
 
+/* Substepping (App. C.1, the scaling alternative to one series per step): a
+ * step of length dt runs as s = ceil(rho dt / xmax) series of length dt / s,
+ * rho the largest absolute row sum of H over the rows of H_eff (see
+ * paces_oracle.c).  xmax <= 0: always one series.  Default 8. */
+int or_set_xmax(oracle_t* o, double xmax);
+
 /* hopping matrix J_ab the oracle built (N*N, row-major) */
 void or_get_hopping(const oracle_t* o, double* out);
 
@@ -81,7 +87,9 @@ long or_build_hamiltonian(oracle_t* o, int* cnt, int* cols, double* vals, double
 #define OR_ST_TERMS 8       /* Taylor terms used                          */
 #define OR_ST_NORM_BEFORE 9 /* ||c||^2 before truncation                  */
 #define OR_ST_TIME 10
-#define OR_NST 12
+#define OR_ST_SUBSTEPS 11   /* Taylor series the step was split into       */
+#define OR_ST_HBOUND 12     /* bound rho on ||P H P|| used to split it      */
+#define OR_NST 13
 void or_stats(const oracle_t* o, double* st);
 /* populations P_s[N] and mean phonon numbers nbar_j[N] of the current state */
 void or_populations(const oracle_t* o, double* P, double* nbar);

@@ -20,8 +20,8 @@ NEAREST, DIPOLAR = 0, 1
 C128, DW, C64_SPMV = 0, 1, 2
 MAX_SITES, MAX_WORDS = 128, 4
 OBS_FIELDS = ("time", "norm", "norm_phi0", "energy", "C_re", "C_im", "rows", "kept", "nnz", "terms",
-              "norm_before")
-OBS_FIXED = 12
+              "norm_before", "substeps", "hbound")
+OBS_FIXED = 14
 STAGES = ("truncate", "expand", "hamiltonian", "propagate", "observe")
 
 EXPORTED = (
@@ -41,7 +41,7 @@ class Params(C.Structure):
                 ("g", C.POINTER(C.c_double)), ("phonon_cap", C.POINTER(C.c_int32)), ("m", C.c_int32),
                 ("m_init", C.c_int32), ("precision", C.c_int32), ("fixed_terms", C.c_int32),
                 ("taylor_tol", C.c_double), ("taylor_nmax", C.c_int32), ("max_rows", C.c_uint64),
-                ("batch", C.c_int32), ("reserved0", C.c_int32)]
+                ("batch", C.c_int32), ("reserved0", C.c_int32), ("taylor_xmax", C.c_double)]
 
 
 class Layout(C.Structure):
@@ -153,9 +153,10 @@ def _ip(a):
 
 def make_params(n_sites, lattice_kind=RING, dims=(0, 0, 0), coupling_kind=NEAREST, J=1.0, eps=None,
                 omega=None, g=None, cap=None, m=2, m_init=10, precision=C128, fixed_terms=0, tol=0.0,
-                nmax=0, max_rows=0, J_explicit=None, batch=1):
+                nmax=0, max_rows=0, J_explicit=None, batch=1, xmax=0.0):
     """Build a Params struct; returns (struct, keepalive arrays).  For an
-    ensemble (batch R > 1) eps is [R, N] (or broadcastable to it)."""
+    ensemble (batch R > 1) eps is [R, N] (or broadcastable to it).  xmax: the
+    substep bound (0: the library's 8; < 0: one Taylor series per step)."""
     N = int(n_sites)
     R = max(1, int(batch))
     vec = lambda v: np.ascontiguousarray(np.broadcast_to(np.asarray(0.0 if v is None else v,
@@ -181,6 +182,7 @@ def make_params(n_sites, lattice_kind=RING, dims=(0, 0, 0), coupling_kind=NEARES
     p.m, p.m_init, p.precision, p.fixed_terms = int(m), int(m_init), int(precision), int(fixed_terms)
     p.taylor_tol, p.taylor_nmax, p.max_rows = float(tol), int(nmax), int(max_rows)
     p.batch = R
+    p.taylor_xmax = float(xmax)
     return p, keep
 
 

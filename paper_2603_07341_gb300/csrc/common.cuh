@@ -24,6 +24,7 @@ constexpr uint32_t kCand = 0x80000000u;
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr uint64_t kEmpty = ~0ull;
 constexpr uint32_t kMaxProbe = 1u << 16;
+constexpr int kMaxSub = 1024;         // Taylor series per time step (substeps)
 
 // device error codes (Counters::err)
 enum DevErr : int {
@@ -216,6 +217,12 @@ struct DevModel {
     uint8_t adj[kMaxSites * (kMaxMoves - 2)];
     uint8_t adj_cid[kMaxSites * (kMaxMoves - 2)];
     double coef[kMaxCoefs];
+    // bound on ||P H P||: every term |x| rounded up to a multiple of 2^-20 and
+    // held as an integer (up20), so that row sums are exact and order-free
+    unsigned long long hb_coef[kMaxCoefs];   // up20(|coef|)
+    unsigned long long hb_eps[kMaxSites];    // up20(|eps_s|) (single model)
+    unsigned long long hb_omega[kMaxSites];  // up20(|omega_j|)
+    unsigned long long hb_hop[kMaxSites];    // sum over the hops t of s of up20(|J_ts|)
     double coef_dJ[kMaxCoefs];
     double coef_dg[kMaxCoefs];
     int ncoef;
@@ -233,9 +240,12 @@ struct Counters {
     int err, err_step, err_info, pad0;
     unsigned bar_count, bar_gen;
     int nterms, pad1;
+    int nsub, pad2;                  // Taylor series of the last step (substeps)
+    unsigned long long hbound;       // largest row bound of P H P in 2^-20 units (a5)
     double norm_r, norm_phi0, energy, norm_last;
     double time;                     // t of the last record
     long long rec_index;             // next observables record
+    int sub_terms[kMaxSub];          // terms of each series of the last step
 };
 
 // Record the first device error (code, step, detail); later ones are dropped.

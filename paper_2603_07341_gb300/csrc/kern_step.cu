@@ -322,7 +322,8 @@ __global__ void __launch_bounds__(kBlock) k_level_scatter(const DevModel* __rest
 // recorded, so the column is one read of that slot's tag; rows of the last
 // level probe the table.
 struct DiagAcc {
-    double d;      // FP64 diagonal, summed in site order as the oracle does
+    double d;      // FP64 diagonal: eps_s + omega N_ph (one rounding) when every
+                   // omega_j is equal, else summed in site order
     dwf dd;        // double-word diagonal
 };
 
@@ -336,8 +337,10 @@ __device__ __forceinline__ DiagAcc row_diag(const DevModel* __restrict__ M, cons
         e64 = M->eps_b64[rz * M->N + s];
         edw = M->eps_bdw[rz * M->N + s];
     }
-    if (M->fmt == 0 && M->uniform_omega) {    // eps_s + omega N_ph, no digits needed
-        DiagAcc r{0.0, dw_add(edw, dw_mul_f(M->omega_dw[0], (float)nph))};
+    if (M->uniform_omega) {                   // eps_s + omega N_ph, no digits needed
+        DiagAcc r{0.0, {0.f, 0.f}};
+        if (M->fmt == 1) r.d = fma(M->omega[0], (double)nph, e64);
+        else r.dd = dw_add(edw, dw_mul_f(M->omega_dw[0], (float)nph));
         return r;
     }
     uint64_t q0 = udiv(k.w[0], M->div_exc);
@@ -358,6 +361,54 @@ __device__ __forceinline__ DiagAcc row_diag(const DevModel* __restrict__ M, cons
     }
     if (!f64 && M->uniform_omega) r.dd = dw_add(r.dd, dw_mul_f(M->omega_dw[0], (float)nph));
     return r;
+}
+
+// Row bound used to choose the number of Taylor series of a step (a6):
+// up20(|eps_s|) + sum_j up20(|omega_j|) n_j + up20 of every off-diagonal
+// element of H in the row (hops and ladder moves, in H_eff or not), where
+// up20(x) = ceil(|x| 2^20).  The largest row sum of |H| over H_eff bounds
+// ||P H P||_2; integer sums make the bound exact and free of summation order.
+template <int W>
+__device__ __forceinline__ unsigned long long row_hbound(const DevModel* __restrict__ M, const Key<W>& k, int s,
+                                                         int ns, int nph)
+{
+    unsigned long long b;
+    if (M->batch > 1) {
+        int rz = key_real<W>(k, M);
+        b = (unsigned long long)ceil(fabs(M->eps_b64[rz * M->N + s]) * 1048576.0);
+    } else {
+        b = M->hb_eps[s];
+    }
+    b += M->hb_hop[s];
+    if (M->uniform_omega) {
+        b += M->hb_omega[0] * (unsigned long long)nph;
+    } else {
+        uint64_t q0 = udiv(k.w[0], M->div_exc);
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            uint64_t x = (w == 0) ? q0 : k.w[w];
+            for (int j = M->word_first[w]; j < M->word_first[w + 1]; ++j) {
+                uint64_t xq = udiv(x, M->div_radix[j]);
+                b += M->hb_omega[j] * (x - xq * M->div_radix[j].d);
+                x = xq;
+            }
+        }
+    }
+    if (M->gnz[s]) {
+        if (ns < M->cap[s]) b += M->hb_coef[M->lad_cid[M->lad_off[s] + ns]];
+        if (ns > 0) b += M->hb_coef[M->lad_cid[M->lad_off[s] + ns - 1]];
+    }
+    return b;
+}
+
+__device__ __forceinline__ void hbound_publish(Counters* ctr, unsigned long long hb)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long v = __shfl_xor_sync(0xffffffffu, hb, o);
+        hb = v > hb ? v : hb;
+    }
+    if ((threadIdx.x & 31) == 0 && hb) atomicMax(&ctr->hbound, hb);
 }
 
 __device__ __forceinline__ void store_diag(const DevModel* __restrict__ M, double* diag, uint64_t i, const DiagAcc& a)
@@ -384,7 +435,7 @@ __global__ void __launch_bounds__(kBlock) k_csr_grp(const DevModel* __restrict__
     const int lane = threadIdx.x & 31, mv = lane % GS, gbase = lane - mv;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-    unsigned long long nnz = 0;
+    unsigned long long nnz = 0, hb = 0;
     for (uint32_t rb = warp * RPW; rb < q; rb += nwarps * RPW) {
         uint32_t row = rb + lane / GS;
         bool valid = row < q;
@@ -430,9 +481,12 @@ __global__ void __launch_bounds__(kBlock) k_csr_grp(const DevModel* __restrict__
             int e = __popc(gm);
             cnt[row] = (uint8_t)e;
             store_diag(M, diag, row, row_diag<W>(M, k, s, meta_nph(m)));
+            unsigned long long b = row_hbound<W>(M, k, s, ns, meta_nph(m));
+            hb = b > hb ? b : hb;
             nnz += e;
         }
     }
+    hbound_publish(ctr, hb);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) nnz += __shfl_xor_sync(0xffffffffu, nnz, o);
     if ((threadIdx.x & 31) == 0 && nnz) atomicAdd(&ctr->nnz, nnz);
@@ -450,7 +504,7 @@ __global__ void __launch_bounds__(kBlock) k_csr(const DevModel* __restrict__ M, 
     if (ctr->err) return;
     const uint32_t q = ctr->q, lim = ctr->level_off[ctr->nlevels - 1];
     const int D = M->D, P = M->P;
-    unsigned long long nnz = 0;
+    unsigned long long nnz = 0, hb = 0;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < q; i += gridDim.x * blockDim.x) {
         Key<W> k = load_key<W>(keys, i);
         uint32_t m = meta[i];
@@ -475,8 +529,11 @@ __global__ void __launch_bounds__(kBlock) k_csr(const DevModel* __restrict__ M, 
         }
         cnt[i] = (uint8_t)e;
         store_diag(M, diag, i, row_diag<W>(M, k, s, meta_nph(m)));
+        unsigned long long b = row_hbound<W>(M, k, s, ns, meta_nph(m));
+        hb = b > hb ? b : hb;
         nnz += e;
     }
+    hbound_publish(ctr, hb);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) nnz += __shfl_xor_sync(0xffffffffu, nnz, o);
     if ((threadIdx.x & 31) == 0 && nnz) atomicAdd(&ctr->nnz, nnz);
@@ -749,6 +806,8 @@ __global__ void __launch_bounds__(kBlock) k_obs_finish_batch(const DevModel* __r
         rec[PACES_OBS_NNZ] = initial ? 0.0 : (double)(ctr->nnz + ctr->q);
         rec[PACES_OBS_TERMS] = initial ? 0.0 : (double)ctr->nterms;
         rec[PACES_OBS_NORM_BEFORE] = initial ? norm : ctr->norm_last;
+        rec[PACES_OBS_SUBSTEPS] = initial ? 0.0 : (double)ctr->nsub;
+        rec[PACES_OBS_HBOUND] = initial ? 0.0 : (double)ctr->hbound * (1.0 / 1048576.0);
         ctr->norm_last = norm;
         ctr->nnz = 0;
     }
@@ -813,6 +872,8 @@ __global__ void __launch_bounds__(kBlock) k_obs_finish(const DevModel* __restric
         rec[PACES_OBS_NNZ] = initial ? 0.0 : (double)(ctr->nnz + ctr->q);
         rec[PACES_OBS_TERMS] = initial ? 0.0 : (double)ctr->nterms;
         rec[PACES_OBS_NORM_BEFORE] = initial ? norm : ctr->norm_last;
+        rec[PACES_OBS_SUBSTEPS] = initial ? 0.0 : (double)ctr->nsub;
+        rec[PACES_OBS_HBOUND] = initial ? 0.0 : (double)ctr->hbound * (1.0 / 1048576.0);
         ctr->norm_last = norm;
         ctr->nnz = 0;            // the next step's P H P build counts from zero
     }
@@ -911,6 +972,8 @@ static int csr_w(const Bufs& b, int gen, cudaStream_t st)
 #define PACES_CSR_ARGS \
     b.model, b.ctr, b.keys[gen], b.meta[gen], b.table[gen], b.table_slots, b.cand_slot, b.col, b.cid, b.cnt, \
         b.diag
+    // the row bound is a maximum over this build's rows only
+    cudaMemsetAsync(reinterpret_cast<char*>(b.ctr) + offsetof(Counters, hbound), 0, sizeof(unsigned long long), st);
     if (b.D <= 4) k_csr_grp<W, 4><<<b.grid, kBlock, 0, st>>>(PACES_CSR_ARGS);
     else if (b.D <= 8) k_csr_grp<W, 8><<<b.grid, kBlock, 0, st>>>(PACES_CSR_ARGS);
     else if (b.D <= 16) k_csr_grp<W, 16><<<b.grid, kBlock, 0, st>>>(PACES_CSR_ARGS);

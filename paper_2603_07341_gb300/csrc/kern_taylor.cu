@@ -136,16 +136,35 @@ __device__ __forceinline__ float mag_scaled_f32(double v)
     return __int_as_float((e << 23) | ((h & 0xFFFFF) << 3));
 }
 
+// Number of Taylor series a step runs as (App. C.1's scaling alternative):
+// s = ceil(rho dt / xmax), rho = the row bound of P H P that the build of the
+// step's Hamiltonian left in the counters (in units of 2^-20); 1 when xmax <= 0;
+// 0 when more than kMaxSub series would be needed.
+__device__ __forceinline__ int series_count(const Counters* ctr, const TaylorParams& p)
+{
+    if (p.xmax <= 0.0) return 1;
+    double rho = (double)__ldcg(&ctr->hbound) * (1.0 / 1048576.0);
+    double ns = ceil(rho * p.dt / p.xmax);
+    if (ns > (double)kMaxSub) return 0;
+    return ns < 1.0 ? 1 : (int)ns;
+}
+
 // FP64 amplitudes.  The FP64 pipe of this part retires about two operations
 // per SM per clock, so the kernel spends FP64 operations only on the
-// amplitudes themselves: the factor dt/n is folded into the shared coefficient
-// table and into one product with the diagonal, so a row of c off-diagonal
-// entries costs 2c + 5 FP64 operations (products, the diagonal, r += phi_n).
-// The stop test compares ||phi_n||^2, summed in FP32 from the leading 20 bits
-// of every component, with tol^2 ||c'||^2 (||c'|| in FP64 from term 1): the
-// partial sum r_n differs from c' in norm by about ||phi_{n+1}||, which is
-// far below the test's resolution when the test is near to passing.  A term
-// more or less changes r by at most tol ||c'||.
+// amplitudes themselves: the factor h/n (h = dt / series) is folded into the
+// shared coefficient table and into one product with the diagonal, so a row of
+// c off-diagonal entries costs 2c + 5 FP64 operations (products, the diagonal,
+// r += phi_n).  The stop test compares ||phi_n||^2, summed in FP32 from the
+// leading 20 bits of every component, with tol^2 ||v||^2, v the input of the
+// series (||v|| in FP64 from its first term): the partial sum r_n differs from
+// v in norm by about ||phi_{n+1}||, far below the test's resolution when the
+// test is near to passing.  A term more or less changes r by at most tol ||v||.
+//
+// A step of several series (substeps) copies the output of one series, held
+// in r, into a term buffer as the input of the next, so that r is updated in
+// place while that input is gathered.  Adjoint re-runs store, in order, the
+// terms phi_1.. of the first series, then for each later series its input and
+// its terms (16 bytes per row each).
 template <int LPR>
 __global__ void __launch_bounds__(kBlock) k_taylor_f64(TaylorArgs a)
 {
@@ -167,71 +186,108 @@ __global__ void __launch_bounds__(kBlock) k_taylor_f64(TaylorArgs a)
 
     const int fixed = a.p.fixed_terms;
     const int nlimit = fixed > 0 ? fixed : a.p.nmax;
-    const double2* x = a.c_in;
-    double2* y = a.ta;
+    const int nsub = series_count(ctr, a.p);
+    if (nsub < 1) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_err(ctr, kErrNoConverge, a.p.step, -1);
+        return;
+    }
+    const double h = a.p.dt / (double)nsub;
+    double2* store = reinterpret_cast<double2*>(a.terms);
     double E = 0.0, n0 = 0.0;
-    int nd = 0;
-    bool conv = false;
-    for (int n = 1; n <= nlimit; ++n) {
-        const double s = a.p.dt / (double)n;
-        __syncthreads();
-        for (int t = threadIdx.x; t < ncoef; t += blockDim.x) coef[t] = s * M->coef[t];
-        __syncthreads();
-        float phi2 = 0.f;
-        double acc_e = 0.0, acc_n = 0.0;
-        for (uint32_t rb = warp * RPW; rb < q; rb += nwarps * RPW) {
-            uint32_t row = rb + sub;
-            bool valid = row < q;
-            uint32_t c = valid ? a.cnt[row] : 0u;
-            uint64_t base = (uint64_t)row * P;
-            double2 yv = row_apply<LPR, double2>(a.col, a.cid, c, base, coef, x, lane);   // s (H x) off the diagonal
-            if (valid && lane == 0) {
-                double2 xi = x[row];
-                double d = s * a.diag[row];
-                yv.x = fma(d, xi.x, yv.x);
-                yv.y = fma(d, xi.y, yv.y);
-                double2 phi = make_double2(yv.y, -yv.x);            // (-i) s H x
-                y[row] = phi;
-                if (a.terms && n <= a.term_max) reinterpret_cast<double2*>(a.terms)[(size_t)(n - 1) * q + row] = phi;
-                double2 rr = (n == 1) ? xi : a.r[row];
-                rr.x += phi.x;
-                rr.y += phi.y;
-                a.r[row] = rr;
-                float p0 = mag_scaled_f32(phi.x), p1 = mag_scaled_f32(phi.y);
-                phi2 = __fmaf_rn(p0, p0, __fmaf_rn(p1, p1, phi2));
-                if (n == 1) {
-                    acc_e = fma(xi.x, yv.x, fma(xi.y, yv.y, acc_e));     // Re(conj(c') dt H c')
-                    acc_n = fma(xi.x, xi.x, fma(xi.y, xi.y, acc_n));
+    int total = 0, slot = 0, bar = 0;
+    bool conv = true;
+    for (int j = 0; j < nsub && conv; ++j) {
+        const double2* x = a.c_in;
+        double2* y = a.ta;
+        if (j > 0) {
+            for (uint32_t row = blockIdx.x * blockDim.x + threadIdx.x; row < q; row += G * blockDim.x) {
+                double2 v = a.r[row];
+                a.ta[row] = v;
+                if (store && slot < a.term_max) store[(size_t)slot * q + row] = v;
+            }
+            ++slot;
+            double z[4] = {0.0, 0.0, 0.0, 0.0};
+            double* part = a.partials + (size_t)(bar & 1) * G * 4;
+            double* tot = a.totals + (bar & 1) * 4;
+            ++bar;
+            block_sum<kBlock, 4>(z, part + 4 * blockIdx.x);
+            if (!barrier_reduce(ctr, part, tot, G)) return;
+            x = a.ta;
+            y = a.tb;
+        }
+        double nin = 0.0;
+        int nd = 0;
+        bool cj = fixed > 0;
+        for (int n = 1; n <= nlimit; ++n) {
+            const double s = h / (double)n;
+            __syncthreads();
+            for (int t = threadIdx.x; t < ncoef; t += blockDim.x) coef[t] = s * M->coef[t];
+            __syncthreads();
+            float phi2 = 0.f;
+            double acc_e = 0.0, acc_n = 0.0;
+            for (uint32_t rb = warp * RPW; rb < q; rb += nwarps * RPW) {
+                uint32_t row = rb + sub;
+                bool valid = row < q;
+                uint32_t c = valid ? a.cnt[row] : 0u;
+                uint64_t base = (uint64_t)row * P;
+                double2 yv = row_apply<LPR, double2>(a.col, a.cid, c, base, coef, x, lane);   // s (H x) off the diagonal
+                if (valid && lane == 0) {
+                    double2 xi = x[row];
+                    double d = s * a.diag[row];
+                    yv.x = fma(d, xi.x, yv.x);
+                    yv.y = fma(d, xi.y, yv.y);
+                    double2 phi = make_double2(yv.y, -yv.x);            // (-i) s H x
+                    y[row] = phi;
+                    if (store && slot < a.term_max) store[(size_t)slot * q + row] = phi;
+                    double2 rr = (n == 1) ? xi : a.r[row];
+                    rr.x += phi.x;
+                    rr.y += phi.y;
+                    a.r[row] = rr;
+                    float p0 = mag_scaled_f32(phi.x), p1 = mag_scaled_f32(phi.y);
+                    phi2 = __fmaf_rn(p0, p0, __fmaf_rn(p1, p1, phi2));
+                    if (n == 1) {
+                        acc_e = fma(xi.x, yv.x, fma(xi.y, yv.y, acc_e));     // Re(conj(v) h H v)
+                        acc_n = fma(xi.x, xi.x, fma(xi.y, xi.y, acc_n));
+                    }
                 }
             }
+            ++slot;
+            double acc[4] = {(double)phi2, acc_e, acc_n, 0.0};
+            double* part = a.partials + (size_t)(bar & 1) * G * 4;
+            double* tot = a.totals + (bar & 1) * 4;
+            ++bar;
+            block_sum<kBlock, 4>(acc, part + 4 * blockIdx.x);
+            if (!barrier_reduce(ctr, part, tot, G)) return;
+            if (threadIdx.x < 4) tsh[threadIdx.x] = __ldcg(tot + threadIdx.x);
+            __syncthreads();
+            nd = n;
+            if (n == 1) {
+                nin = tsh[2];
+                if (j == 0) {
+                    E = tsh[1] / h;
+                    n0 = tsh[2];
+                }
+            }
+            if (fixed <= 0 && n >= 2 && tsh[0] <= a.p.tol2 * nin * (double)kScale2) {
+                cj = true;
+                break;
+            }
+            x = y;
+            y = (y == a.ta) ? a.tb : a.ta;
         }
-        double acc[4] = {(double)phi2, acc_e, acc_n, 0.0};
-        double* part = a.partials + (size_t)(n & 1) * G * 4;
-        double* tot = a.totals + (n & 1) * 4;
-        block_sum<kBlock, 4>(acc, part + 4 * blockIdx.x);
-        if (!barrier_reduce(ctr, part, tot, G)) return;
-        if (threadIdx.x < 4) tsh[threadIdx.x] = __ldcg(tot + threadIdx.x);
-        __syncthreads();
-        nd = n;
-        if (n == 1) {
-            E = tsh[1] / a.p.dt;
-            n0 = tsh[2];
-        }
-        if (fixed <= 0 && n >= 2 && tsh[0] <= a.p.tol2 * n0 * (double)kScale2) {
-            conv = true;
-            break;
-        }
-        x = y;
-        y = (y == a.ta) ? a.tb : a.ta;
+        total += nd;
+        if (blockIdx.x == 0 && threadIdx.x == 0) ctr->sub_terms[j] = nd;
+        conv = cj;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        ctr->nterms = nd;
+        ctr->nterms = total;
+        ctr->nsub = nsub;
         ctr->norm_r = 0.0;
         ctr->norm_phi0 = n0;
         ctr->energy = E;
-        if (!conv && fixed <= 0 && atomicCAS(&ctr->err, 0, (int)kErrNoConverge) == 0) {
+        if (!conv && atomicCAS(&ctr->err, 0, (int)kErrNoConverge) == 0) {
             ctr->err_step = a.p.step;
-            ctr->err_info = nd;
+            ctr->err_info = total;
         }
     }
 }
@@ -386,84 +442,117 @@ __global__ void __launch_bounds__(kBlock) k_taylor_dw(TaylorArgs a)
     const uint32_t nwarps = (G * blockDim.x) >> 5;
     const int lane = (threadIdx.x & 31) % LPR;
     const uint32_t sub = (threadIdx.x & 31) / LPR;
-    const float4* X = reinterpret_cast<const float4*>(a.c_in);
-    float4* Y = reinterpret_cast<float4*>(a.ta);
+    float4* TA = reinterpret_cast<float4*>(a.ta);
+    float4* TB = reinterpret_cast<float4*>(a.tb);
     float4* R = reinterpret_cast<float4*>(a.r);
+    float4* store = reinterpret_cast<float4*>(a.terms);
     const float2* DG = reinterpret_cast<const float2*>(a.diag);
     const float kScale = 4294967296.0f;       // 2^32: keeps the coarse norms in FP32 range
 
     const int fixed = a.p.fixed_terms;
     const int nlimit = fixed > 0 ? fixed : a.p.nmax;
     const float tol2 = (float)a.p.tol2;
+    const int nsub = series_count(ctr, a.p);
+    if (nsub < 1) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_err(ctr, kErrNoConverge, a.p.step, -1);
+        return;
+    }
+    const double h = a.p.dt / (double)nsub;
     dwf E{0.f, 0.f}, N0{0.f, 0.f};
-    int nd = 0;
-    bool conv = false;
-    for (int n = 1; n <= nlimit; ++n) {
-        const double s = a.p.dt / (double)n;
-        const dwf sdw = dw_from_double(s);
-        __syncthreads();
-        for (int t = threadIdx.x; t < ncoef; t += blockDim.x) coef[t] = dw_from_double(s * M->coef[t]);
-        __syncthreads();
-        Red8 acc{0.f, 0.f, {0.f, 0.f}, {0.f, 0.f}};
-        for (uint32_t rb = warp * RPW; rb < q; rb += nwarps * RPW) {
-            uint32_t row = rb + sub;
-            bool valid = row < q;
-            uint32_t c = valid ? a.cnt[row] : 0u;
-            uint64_t base = (uint64_t)row * P;
-            Dot2 re{0.f, 0.f}, im{0.f, 0.f};
-            row_apply_dw<LPR>(a.col, a.cid, c, base, coef, X, lane, re, im);
-            if (valid && lane == 0) {
-                float4 xi = X[row];
-                float2 d = DG[row];
-                dwf ds = dw_mul(dwf{d.x, d.y}, sdw);
-                dot2_mac(re, ds, xi.x, xi.y);
-                dot2_mac(im, ds, xi.z, xi.w);
-                dwf yre = dot2_result(re), yim = dot2_result(im);      // y = s H x
-                float4 phi = make_float4(yim.hi, yim.lo, -yre.hi, -yre.lo);   // phi = -i y
-                Y[row] = phi;
-                if (a.terms && n <= a.term_max) reinterpret_cast<float4*>(a.terms)[(size_t)(n - 1) * q + row] = phi;
-                float4 rr = (n == 1) ? xi : R[row];
-                dwf r_re = dw_add(dwf{rr.x, rr.y}, dwf{phi.x, phi.y});
-                dwf r_im = dw_add(dwf{rr.z, rr.w}, dwf{phi.z, phi.w});
-                R[row] = make_float4(r_re.hi, r_re.lo, r_im.hi, r_im.lo);
-                float p0 = phi.x * kScale, p1 = phi.z * kScale, q0 = r_re.hi * kScale, q1 = r_im.hi * kScale;
-                acc.phi2 = __fmaf_rn(p0, p0, __fmaf_rn(p1, p1, acc.phi2));
-                acc.r2 = __fmaf_rn(q0, q0, __fmaf_rn(q1, q1, acc.r2));
-                if (n == 1) {
-                    acc.e = dw_add(acc.e, dw_add(dw_mul(dwf{xi.x, xi.y}, yre), dw_mul(dwf{xi.z, xi.w}, yim)));
-                    acc.n0 = dw_add(acc.n0, dw_norm2(xi));
+    int total = 0, slot = 0, bar = 0;
+    bool conv = true;
+    for (int j = 0; j < nsub && conv; ++j) {
+        const float4* X = reinterpret_cast<const float4*>(a.c_in);
+        float4* Y = TA;
+        if (j > 0) {            // input of this series = output of the previous one, copied out of r
+            for (uint32_t row = blockIdx.x * blockDim.x + threadIdx.x; row < q; row += G * blockDim.x) {
+                float4 v = R[row];
+                TA[row] = v;
+                if (store && slot < a.term_max) store[(size_t)slot * q + row] = v;
+            }
+            ++slot;
+            float* part = reinterpret_cast<float*>(a.partials) + (size_t)(bar & 1) * G * 8;
+            float* tot = reinterpret_cast<float*>(a.totals) + (bar & 1) * 8;
+            ++bar;
+            Red8 z = red8_block(Red8{0.f, 0.f, {0.f, 0.f}, {0.f, 0.f}});
+            if (threadIdx.x == 0) red8_store(part + 8 * blockIdx.x, z);
+            if (!barrier_reduce8(ctr, part, tot, G)) return;
+            X = TA;
+            Y = TB;
+        }
+        int nd = 0;
+        bool cj = fixed > 0;
+        for (int n = 1; n <= nlimit; ++n) {
+            const double s = h / (double)n;
+            const dwf sdw = dw_from_double(s);
+            __syncthreads();
+            for (int t = threadIdx.x; t < ncoef; t += blockDim.x) coef[t] = dw_from_double(s * M->coef[t]);
+            __syncthreads();
+            Red8 acc{0.f, 0.f, {0.f, 0.f}, {0.f, 0.f}};
+            for (uint32_t rb = warp * RPW; rb < q; rb += nwarps * RPW) {
+                uint32_t row = rb + sub;
+                bool valid = row < q;
+                uint32_t c = valid ? a.cnt[row] : 0u;
+                uint64_t base = (uint64_t)row * P;
+                Dot2 re{0.f, 0.f}, im{0.f, 0.f};
+                row_apply_dw<LPR>(a.col, a.cid, c, base, coef, X, lane, re, im);
+                if (valid && lane == 0) {
+                    float4 xi = X[row];
+                    float2 d = DG[row];
+                    dwf ds = dw_mul(dwf{d.x, d.y}, sdw);
+                    dot2_mac(re, ds, xi.x, xi.y);
+                    dot2_mac(im, ds, xi.z, xi.w);
+                    dwf yre = dot2_result(re), yim = dot2_result(im);      // y = s H x
+                    float4 phi = make_float4(yim.hi, yim.lo, -yre.hi, -yre.lo);   // phi = -i y
+                    Y[row] = phi;
+                    if (store && slot < a.term_max) store[(size_t)slot * q + row] = phi;
+                    float4 rr = (n == 1) ? xi : R[row];
+                    dwf r_re = dw_add(dwf{rr.x, rr.y}, dwf{phi.x, phi.y});
+                    dwf r_im = dw_add(dwf{rr.z, rr.w}, dwf{phi.z, phi.w});
+                    R[row] = make_float4(r_re.hi, r_re.lo, r_im.hi, r_im.lo);
+                    float p0 = phi.x * kScale, p1 = phi.z * kScale, q0 = r_re.hi * kScale, q1 = r_im.hi * kScale;
+                    acc.phi2 = __fmaf_rn(p0, p0, __fmaf_rn(p1, p1, acc.phi2));
+                    acc.r2 = __fmaf_rn(q0, q0, __fmaf_rn(q1, q1, acc.r2));
+                    if (n == 1 && j == 0) {
+                        acc.e = dw_add(acc.e, dw_add(dw_mul(dwf{xi.x, xi.y}, yre), dw_mul(dwf{xi.z, xi.w}, yim)));
+                        acc.n0 = dw_add(acc.n0, dw_norm2(xi));
+                    }
                 }
             }
+            ++slot;
+            float* part = reinterpret_cast<float*>(a.partials) + (size_t)(bar & 1) * G * 8;
+            float* tot = reinterpret_cast<float*>(a.totals) + (bar & 1) * 8;
+            ++bar;
+            acc = red8_block(acc);
+            if (threadIdx.x == 0) red8_store(part + 8 * blockIdx.x, acc);
+            if (!barrier_reduce8(ctr, part, tot, G)) return;
+            if (threadIdx.x < 6) tsh[threadIdx.x] = __ldcg(tot + threadIdx.x);
+            __syncthreads();
+            nd = n;
+            if (n == 1 && j == 0) {
+                E = dwf{tsh[2], tsh[3]};
+                N0 = dwf{tsh[4], tsh[5]};
+            }
+            if (fixed <= 0 && n >= 2 && tsh[0] <= tol2 * tsh[1]) {
+                cj = true;
+                break;
+            }
+            X = Y;
+            Y = (Y == TA) ? TB : TA;
         }
-        float* part = reinterpret_cast<float*>(a.partials) + (size_t)(n & 1) * G * 8;
-        float* tot = reinterpret_cast<float*>(a.totals) + (n & 1) * 8;
-        acc = red8_block(acc);
-        if (threadIdx.x == 0) red8_store(part + 8 * blockIdx.x, acc);
-        if (!barrier_reduce8(ctr, part, tot, G)) return;
-        if (threadIdx.x < 6) tsh[threadIdx.x] = __ldcg(tot + threadIdx.x);
-        __syncthreads();
-        nd = n;
-        if (n == 1) {
-            E = dwf{tsh[2], tsh[3]};
-            N0 = dwf{tsh[4], tsh[5]};
-        }
-        bool stop = fixed <= 0 && n >= 2 && tsh[0] <= tol2 * tsh[1];
-        if (stop) {
-            conv = true;
-            break;
-        }
-        X = Y;
-        Y = (Y == reinterpret_cast<float4*>(a.ta)) ? reinterpret_cast<float4*>(a.tb)
-                                                   : reinterpret_cast<float4*>(a.ta);
+        total += nd;
+        if (blockIdx.x == 0 && threadIdx.x == 0) ctr->sub_terms[j] = nd;
+        conv = cj;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        ctr->nterms = nd;
+        ctr->nterms = total;
+        ctr->nsub = nsub;
         ctr->norm_phi0 = (double)N0.hi + (double)N0.lo;
-        ctr->energy = ((double)E.hi + (double)E.lo) / a.p.dt;
+        ctr->energy = ((double)E.hi + (double)E.lo) / h;
         ctr->norm_r = 0.0;
-        if (!conv && fixed <= 0 && atomicCAS(&ctr->err, 0, (int)kErrNoConverge) == 0) {
+        if (!conv && atomicCAS(&ctr->err, 0, (int)kErrNoConverge) == 0) {
             ctr->err_step = a.p.step;
-            ctr->err_info = nd;
+            ctr->err_info = total;
         }
     }
 }
@@ -539,9 +628,8 @@ __global__ void __launch_bounds__(kBlock) k_taylor_c64(TaylorArgs a)
     const uint32_t nwarps = (G * blockDim.x) >> 5;
     const int lane = (threadIdx.x & 31) % LPR;
     const uint32_t sub = (threadIdx.x & 31) / LPR;
-    const float4* X = reinterpret_cast<const float4*>(a.c_in);
     float4* Y = reinterpret_cast<float4*>(a.ta);
-    float4* Y2 = reinterpret_cast<float4*>(a.tb);
+    float4* Y2 = reinterpret_cast<float4*>(a.tb);   // input copy of series after the first
     float4* R = reinterpret_cast<float4*>(a.r);
     float2* F[2] = {a.fa, a.fb};
     const float2* DG = reinterpret_cast<const float2*>(a.diag);
@@ -550,92 +638,117 @@ __global__ void __launch_bounds__(kBlock) k_taylor_c64(TaylorArgs a)
     const int fixed = a.p.fixed_terms;
     const int nlimit = fixed > 0 ? fixed : a.p.nmax;
     const float tol2 = (float)a.p.tol2;
+    const int nsub = series_count(ctr, a.p);
+    if (nsub < 1) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_err(ctr, kErrNoConverge, a.p.step, -1);
+        return;
+    }
+    const double h = a.p.dt / (double)nsub;
     dwf E{0.f, 0.f}, N0{0.f, 0.f};
-    int nd = 0;
-    bool conv = false;
-    for (int n = 1; n <= nlimit; ++n) {
-        const double s = a.p.dt / (double)n;
-        const dwf sdw = dw_from_double(s);
-        const float s32 = (float)s;
-        const bool dw_term = n <= kDwTerms;
-        __syncthreads();
-        for (int t = threadIdx.x; t < ncoef; t += blockDim.x) {
-            coef[t] = dw_from_double(s * M->coef[t]);
-            coef32[t] = (float)(s * M->coef[t]);
+    int total = 0, bar = 0;
+    bool conv = true;
+    for (int j = 0; j < nsub && conv; ++j) {
+        const float4* X = reinterpret_cast<const float4*>(a.c_in);
+        if (j > 0) {
+            for (uint32_t row = blockIdx.x * blockDim.x + threadIdx.x; row < q; row += G * blockDim.x) Y2[row] = R[row];
+            float* part = reinterpret_cast<float*>(a.partials) + (size_t)(bar & 1) * G * 8;
+            float* tot = reinterpret_cast<float*>(a.totals) + (bar & 1) * 8;
+            ++bar;
+            Red8 z = red8_block(Red8{0.f, 0.f, {0.f, 0.f}, {0.f, 0.f}});
+            if (threadIdx.x == 0) red8_store(part + 8 * blockIdx.x, z);
+            if (!barrier_reduce8(ctr, part, tot, G)) return;
+            X = Y2;
         }
-        __syncthreads();
-        const float4* Xd = (n == 1) ? X : (n == 2 ? Y : nullptr);        // double-word input
-        float4* Yd = (n == 1) ? Y : Y2;                                  // double-word output
-        const float2* Xf = F[(n + 1) & 1];                               // complex64 input (n >= 3)
-        float2* Yf = F[n & 1];                                           // complex64 output
-        Red8 acc{0.f, 0.f, {0.f, 0.f}, {0.f, 0.f}};
-        for (uint32_t rb = warp * RPW; rb < q; rb += nwarps * RPW) {
-            uint32_t row = rb + sub;
-            bool valid = row < q;
-            uint32_t c = valid ? a.cnt[row] : 0u;
-            uint64_t base = (uint64_t)row * P;
-            float4 phi;
-            if (dw_term) {
-                Dot2 re{0.f, 0.f}, im{0.f, 0.f};
-                row_apply_dw<LPR>(a.col, a.cid, c, base, coef, Xd, lane, re, im);
-                if (!(valid && lane == 0)) continue;
-                float4 xi = Xd[row];
-                float2 d = DG[row];
-                dwf ds = dw_mul(dwf{d.x, d.y}, sdw);
-                dot2_mac(re, ds, xi.x, xi.y);
-                dot2_mac(im, ds, xi.z, xi.w);
-                dwf yre = dot2_result(re), yim = dot2_result(im);
-                phi = make_float4(yim.hi, yim.lo, -yre.hi, -yre.lo);
-                if (n < kDwTerms) Yd[row] = phi;
-                else Yf[row] = make_float2(phi.x + phi.y, phi.z + phi.w);   // next input, rounded
-                if (n == 1) {
-                    acc.e = dw_add(acc.e, dw_add(dw_mul(dwf{xi.x, xi.y}, yre), dw_mul(dwf{xi.z, xi.w}, yim)));
-                    acc.n0 = dw_add(acc.n0, dw_norm2(xi));
-                }
-            } else {
-                float2 y = row_apply_f32<LPR>(a.col, a.cid, c, base, coef32, Xf, lane);
-                if (!(valid && lane == 0)) continue;
-                float2 xi = Xf[row];
-                float2 d = DG[row];
-                float ds = __fmul_rn(d.x + d.y, s32);
-                y.x = __fmaf_rn(ds, xi.x, y.x);
-                y.y = __fmaf_rn(ds, xi.y, y.y);
-                Yf[row] = make_float2(y.y, -y.x);
-                phi = make_float4(y.y, 0.f, -y.x, 0.f);
+        int nd = 0;
+        bool cj = fixed > 0;
+        for (int n = 1; n <= nlimit; ++n) {
+            const double s = h / (double)n;
+            const dwf sdw = dw_from_double(s);
+            const float s32 = (float)s;
+            const bool dw_term = n <= kDwTerms;
+            __syncthreads();
+            for (int t = threadIdx.x; t < ncoef; t += blockDim.x) {
+                coef[t] = dw_from_double(s * M->coef[t]);
+                coef32[t] = (float)(s * M->coef[t]);
             }
-            float4 rr = (n == 1) ? X[row] : R[row];
-            dwf r_re = dw_term ? dw_add(dwf{rr.x, rr.y}, dwf{phi.x, phi.y}) : dw_add_f(dwf{rr.x, rr.y}, phi.x);
-            dwf r_im = dw_term ? dw_add(dwf{rr.z, rr.w}, dwf{phi.z, phi.w}) : dw_add_f(dwf{rr.z, rr.w}, phi.z);
-            R[row] = make_float4(r_re.hi, r_re.lo, r_im.hi, r_im.lo);
-            float p0 = phi.x * kScale, p1 = phi.z * kScale, q0 = r_re.hi * kScale, q1 = r_im.hi * kScale;
-            acc.phi2 = __fmaf_rn(p0, p0, __fmaf_rn(p1, p1, acc.phi2));
-            acc.r2 = __fmaf_rn(q0, q0, __fmaf_rn(q1, q1, acc.r2));
+            __syncthreads();
+            const float4* Xd = (n == 1) ? X : (n == 2 ? Y : nullptr);        // double-word input
+            const float2* Xf = F[(n + 1) & 1];                               // complex64 input (n >= 3)
+            float2* Yf = F[n & 1];                                           // complex64 output
+            Red8 acc{0.f, 0.f, {0.f, 0.f}, {0.f, 0.f}};
+            for (uint32_t rb = warp * RPW; rb < q; rb += nwarps * RPW) {
+                uint32_t row = rb + sub;
+                bool valid = row < q;
+                uint32_t c = valid ? a.cnt[row] : 0u;
+                uint64_t base = (uint64_t)row * P;
+                float4 phi;
+                if (dw_term) {
+                    Dot2 re{0.f, 0.f}, im{0.f, 0.f};
+                    row_apply_dw<LPR>(a.col, a.cid, c, base, coef, Xd, lane, re, im);
+                    if (!(valid && lane == 0)) continue;
+                    float4 xi = Xd[row];
+                    float2 d = DG[row];
+                    dwf ds = dw_mul(dwf{d.x, d.y}, sdw);
+                    dot2_mac(re, ds, xi.x, xi.y);
+                    dot2_mac(im, ds, xi.z, xi.w);
+                    dwf yre = dot2_result(re), yim = dot2_result(im);
+                    phi = make_float4(yim.hi, yim.lo, -yre.hi, -yre.lo);
+                    if (n < kDwTerms) Y[row] = phi;
+                    else Yf[row] = make_float2(phi.x + phi.y, phi.z + phi.w);   // next input, rounded
+                    if (n == 1 && j == 0) {
+                        acc.e = dw_add(acc.e, dw_add(dw_mul(dwf{xi.x, xi.y}, yre), dw_mul(dwf{xi.z, xi.w}, yim)));
+                        acc.n0 = dw_add(acc.n0, dw_norm2(xi));
+                    }
+                } else {
+                    float2 yv = row_apply_f32<LPR>(a.col, a.cid, c, base, coef32, Xf, lane);
+                    if (!(valid && lane == 0)) continue;
+                    float2 xi = Xf[row];
+                    float2 d = DG[row];
+                    float ds = __fmul_rn(d.x + d.y, s32);
+                    yv.x = __fmaf_rn(ds, xi.x, yv.x);
+                    yv.y = __fmaf_rn(ds, xi.y, yv.y);
+                    Yf[row] = make_float2(yv.y, -yv.x);
+                    phi = make_float4(yv.y, 0.f, -yv.x, 0.f);
+                }
+                float4 rr = (n == 1) ? X[row] : R[row];
+                dwf r_re = dw_term ? dw_add(dwf{rr.x, rr.y}, dwf{phi.x, phi.y}) : dw_add_f(dwf{rr.x, rr.y}, phi.x);
+                dwf r_im = dw_term ? dw_add(dwf{rr.z, rr.w}, dwf{phi.z, phi.w}) : dw_add_f(dwf{rr.z, rr.w}, phi.z);
+                R[row] = make_float4(r_re.hi, r_re.lo, r_im.hi, r_im.lo);
+                float p0 = phi.x * kScale, p1 = phi.z * kScale, q0 = r_re.hi * kScale, q1 = r_im.hi * kScale;
+                acc.phi2 = __fmaf_rn(p0, p0, __fmaf_rn(p1, p1, acc.phi2));
+                acc.r2 = __fmaf_rn(q0, q0, __fmaf_rn(q1, q1, acc.r2));
+            }
+            float* part = reinterpret_cast<float*>(a.partials) + (size_t)(bar & 1) * G * 8;
+            float* tot = reinterpret_cast<float*>(a.totals) + (bar & 1) * 8;
+            ++bar;
+            acc = red8_block(acc);
+            if (threadIdx.x == 0) red8_store(part + 8 * blockIdx.x, acc);
+            if (!barrier_reduce8(ctr, part, tot, G)) return;
+            if (threadIdx.x < 6) tsh[threadIdx.x] = __ldcg(tot + threadIdx.x);
+            __syncthreads();
+            nd = n;
+            if (n == 1 && j == 0) {
+                E = dwf{tsh[2], tsh[3]};
+                N0 = dwf{tsh[4], tsh[5]};
+            }
+            if (fixed <= 0 && n >= 2 && tsh[0] <= tol2 * tsh[1]) {
+                cj = true;
+                break;
+            }
         }
-        float* part = reinterpret_cast<float*>(a.partials) + (size_t)(n & 1) * G * 8;
-        float* tot = reinterpret_cast<float*>(a.totals) + (n & 1) * 8;
-        acc = red8_block(acc);
-        if (threadIdx.x == 0) red8_store(part + 8 * blockIdx.x, acc);
-        if (!barrier_reduce8(ctr, part, tot, G)) return;
-        if (threadIdx.x < 6) tsh[threadIdx.x] = __ldcg(tot + threadIdx.x);
-        __syncthreads();
-        nd = n;
-        if (n == 1) {
-            E = dwf{tsh[2], tsh[3]};
-            N0 = dwf{tsh[4], tsh[5]};
-        }
-        if (fixed <= 0 && n >= 2 && tsh[0] <= tol2 * tsh[1]) {
-            conv = true;
-            break;
-        }
+        total += nd;
+        if (blockIdx.x == 0 && threadIdx.x == 0) ctr->sub_terms[j] = nd;
+        conv = cj;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        ctr->nterms = nd;
+        ctr->nterms = total;
+        ctr->nsub = nsub;
         ctr->norm_phi0 = (double)N0.hi + (double)N0.lo;
-        ctr->energy = ((double)E.hi + (double)E.lo) / a.p.dt;
+        ctr->energy = ((double)E.hi + (double)E.lo) / h;
         ctr->norm_r = 0.0;
-        if (!conv && fixed <= 0 && atomicCAS(&ctr->err, 0, (int)kErrNoConverge) == 0) {
+        if (!conv && atomicCAS(&ctr->err, 0, (int)kErrNoConverge) == 0) {
             ctr->err_step = a.p.step;
-            ctr->err_info = nd;
+            ctr->err_info = total;
         }
     }
 }

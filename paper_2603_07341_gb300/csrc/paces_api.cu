@@ -219,6 +219,7 @@ paces_status check_params(const paces_params* p, std::string& why)
     }
     if (p->taylor_tol < 0 || p->taylor_nmax < 0 || p->fixed_terms < 0) { why = "series limits"; return PACES_ERR_INVALID; }
     if (p->batch < 0 || p->batch > PACES_MAX_BATCH) { why = "batch out of range"; return PACES_ERR_INVALID; }
+    if (!std::isfinite(p->taylor_xmax)) { why = "taylor_xmax"; return PACES_ERR_INVALID; }
     return PACES_OK;
 }
 
@@ -478,6 +479,7 @@ TaylorParams taylor_params(paces_t h, double dt, int step)
     p.tol2 = tol * tol;
     p.nmax = h->prm.taylor_nmax > 0 ? h->prm.taylor_nmax : 200;
     p.fixed_terms = h->prm.fixed_terms;
+    p.xmax = h->prm.taylor_xmax == 0.0 ? 8.0 : (h->prm.taylor_xmax < 0.0 ? 0.0 : h->prm.taylor_xmax);
     p.step = step;
     p.lpr = h->lpr;
     p.c64 = h->prm.precision == PACES_C64_SPMV;
@@ -766,6 +768,16 @@ paces_status paces::fill_model(const paces_params* params, const paces_layout& L
     }
     M->adj_off[N] = nadj;
     M->lad_off[N] = nlad;
+    // integer row-bound tables (up20 = |x| rounded up to a multiple of 2^-20)
+    auto up20 = [](double x) { return (unsigned long long)std::ceil(std::fabs(x) * 1048576.0); };
+    for (int c = 0; c < (int)ids.size() && c < kMaxCoefs; ++c) M->hb_coef[c] = up20(M->coef[c]);
+    for (int si = 0; si < N; ++si) {
+        M->hb_eps[si] = up20(M->eps[si]);
+        M->hb_omega[si] = up20(M->omega[si]);
+        unsigned long long hs = 0;
+        for (int e = M->adj_off[si]; e < M->adj_off[si + 1]; ++e) hs += M->hb_coef[M->adj_cid[e]];
+        M->hb_hop[si] = hs;
+    }
     M->nlad = nlad;
     M->ncoef = (int)ids.size();
     if (M->ncoef > kMaxCoefs) return PACES_ERR_UNSUPPORTED;
@@ -1527,13 +1539,16 @@ paces_status paces_backward(paces_t h, int64_t nsteps, const double* dL_dc_final
     CUDA_TRY(h, cudaMemcpyAsync(rec.data(), h->b.obs + (size_t)h->rec_base * rl, sizeof(double) * rec.size(),
                                 cudaMemcpyDeviceToHost, h->st));
     CUDA_TRY(h, cudaStreamSynchronize(h->st));
+    // a step of ns Taylor series with nt terms in all keeps nt + ns - 1 vectors
+    // of its re-run: the terms of every series and the inputs of all but the first
     std::vector<uint32_t> qk((size_t)nsteps);
-    std::vector<int> ntk((size_t)nsteps);
+    std::vector<int> ntk((size_t)nsteps), nsk((size_t)nsteps);
     size_t term_bytes = 256, seg_bytes = 256;
     for (int64_t k = 0; k < nsteps; ++k) {
         qk[k] = (uint32_t)rec[(size_t)k * rl + PACES_OBS_ROWS];
         ntk[k] = (int)rec[(size_t)k * rl + PACES_OBS_TERMS];
-        term_bytes = std::max(term_bytes, (size_t)std::max(ntk[k] - 1, 0) * qk[k] * 16);
+        nsk[k] = std::max(1, (int)rec[(size_t)k * rl + PACES_OBS_SUBSTEPS]);
+        term_bytes = std::max(term_bytes, (size_t)std::max(ntk[k] + nsk[k] - 1, 0) * qk[k] * 16);
     }
     if (qk[nsteps - 1] != q_live) return fail(h, PACES_ERR_STATE, "the live state is not the last recorded one");
     for (int64_t k0 = 0; k0 < nsteps; k0 += S) {
@@ -1622,7 +1637,7 @@ paces_status paces_backward(paces_t h, int64_t nsteps, const double* dL_dc_final
         if (capture) {
             h->b.from = from;
             h->b.terms = terms;
-            h->b.term_max = std::max(ntk[k] - 1, 0);
+            h->b.term_max = std::max(ntk[k] + nsk[k] - 1, 0);
         }
         gen = enqueue_kernels(h, h->st, h->gen, h->fresh, h->rec_dt[k], h->rec_th2[k], h->rec_nom[k], h->rec_seed[k],
                               (int)k, false, 0);
@@ -1636,7 +1651,7 @@ paces_status paces_backward(paces_t h, int64_t nsteps, const double* dL_dc_final
         if (h->hctr->err)
             return fail(h, PACES_ERR_CUDA, "device error " + std::to_string(h->hctr->err) + " replaying step " +
                                                std::to_string(k));
-        if (h->hctr->q != qk[k] || (int)h->hctr->nterms != ntk[k])
+        if (h->hctr->q != qk[k] || (int)h->hctr->nterms != ntk[k] || h->hctr->nsub != nsk[k])
             return fail(h, PACES_ERR_STATE, "replay of recorded step " + std::to_string(k) + " diverged");
         h->fresh = false;
         return PACES_OK;
@@ -1671,18 +1686,35 @@ paces_status paces_backward(paces_t h, int64_t nsteps, const double* dL_dc_final
             s = replay(k, true);
             if (s) return finish(s);
             const uint32_t q = qk[k];
-            const int nt = ntk[k];
+            const int nt = ntk[k], ns = nsk[k];
+            const double hs = h->rec_dt[k] / ns;
             double2* gb = G[cur];
             count(h, Stage::Other, launch_adj_obs(h->b, gen, h->b.V[0], dP ? dP + (size_t)k * N : nullptr,
                                                   dC ? dC + k : nullptr, gb, h->st));
+            // stored vectors of the re-run: series 0 keeps phi_n at slot n - 1;
+            // series j >= 1 keeps its input at slot b_j and phi_n at b_j + n
+            std::vector<int> bj((size_t)ns, 0);
+            for (int j = 1; j < ns; ++j) bj[j] = bj[j - 1] + h->hctr->sub_terms[j - 1] + (j > 1 ? 1 : 0);
+            auto slot_ptr = [&](int sl) { return (const void*)(terms + (size_t)sl * q * 16); };
             const double2* mu = gb;
             int x = 0;
-            for (int n = nt; n >= 1; --n) {
-                const void* phi = n == 1 ? (const void*)h->b.V[1] : (const void*)(terms + (size_t)(n - 2) * q * 16);
-                count(h, Stage::Other, launch_adj_term(h->b, lpr, mu, phi, gb, MU[x], acc, cap, h->rec_dt[k] / n,
-                                                       n == nt, h->st));
-                mu = MU[x];
-                x ^= 1;
+            bool first = true;
+            for (int j = ns - 1; j >= 0; --j) {
+                const int nj = h->hctr->sub_terms[j];
+                for (int n = nj; n >= 1; --n) {
+                    const void* phi;
+                    if (j == 0) phi = n == 1 ? (const void*)h->b.V[1] : slot_ptr(n - 2);
+                    else phi = slot_ptr(bj[j] + n - 1);
+                    count(h, Stage::Other, launch_adj_term(h->b, lpr, mu, phi, gb, MU[x], acc, cap, hs / n, first,
+                                                           h->st));
+                    first = false;
+                    mu = MU[x];
+                    x ^= 1;
+                }
+                if (j > 0) {     // the input cotangent of series j is the output cotangent of series j-1
+                    ADJ_TRY(cudaMemcpyAsync(gb, mu, (size_t)q * 16, cudaMemcpyDeviceToDevice, h->st));
+                    mu = gb;
+                }
             }
             if (nt >= 1) {
                 count(h, Stage::Other, launch_adj_bins(h->b, gen, acc, cap, bins, h->st));

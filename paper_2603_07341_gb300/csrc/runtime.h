@@ -84,6 +84,7 @@ struct Bufs {
 
 struct TaylorParams {
     double dt;
+    double xmax;                    // substeps: ceil(rho dt / xmax); <= 0: one series
     double tol2;
     int nmax;
     int fixed_terms;

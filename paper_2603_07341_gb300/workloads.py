@@ -63,11 +63,14 @@ def model_kwargs(cfg, **over):
     c.update(over)
     N = c["n_sites"]
     arr = lambda v: np.broadcast_to(np.asarray(v, dtype=np.float64), (N,)).copy()
-    return dict(n_sites=N, lattice_kind=c["lattice_kind"], dims=tuple(c["dims"]),
-                coupling_kind=c["coupling_kind"], J=float(c["J"]), eps=arr(c["eps"]),
-                omega=arr(c["omega"]), g=arr(c["g"]),
-                cap=np.broadcast_to(np.asarray(c["cap"], dtype=np.int32), (N,)).copy(),
-                m=int(c["m"]), m_init=int(c["m_init"]))
+    out = dict(n_sites=N, lattice_kind=c["lattice_kind"], dims=tuple(c["dims"]),
+               coupling_kind=c["coupling_kind"], J=float(c["J"]), eps=arr(c["eps"]),
+               omega=arr(c["omega"]), g=arr(c["g"]),
+               cap=np.broadcast_to(np.asarray(c["cap"], dtype=np.int32), (N,)).copy(),
+               m=int(c["m"]), m_init=int(c["m_init"]))
+    if "xmax" in c:          # substep bound of the propagator (library default otherwise)
+        out["xmax"] = float(c["xmax"])
+    return out
 
 
 def describe(cfg):

@@ -324,9 +324,9 @@ def test_spectrum_of_single_line_matches_geometric_sum():
 
 
 # ---------------------------------------------------------------- gradients
-def _loss_run(params, keeps=None, record=False, nsteps=12, theta=2e-3):
+def _loss_run(params, keeps=None, record=False, nsteps=12, theta=2e-3, xmax=8.0):
     J, g, w, eps = params
-    o = Oracle(3, W.RING, J=J, eps=eps, omega=w, g=g, cap=2, m=1, m_init=1)
+    o = Oracle(3, W.RING, J=J, eps=eps, omega=w, g=g, cap=2, m=1, m_init=1, xmax=xmax)
     o.set_state([0, 1], [[0, 0, 0], [0, 0, 0]], [0.8, 0.6j])
     if record:
         o.record(True)
@@ -345,13 +345,16 @@ def _loss_run(params, keeps=None, record=False, nsteps=12, theta=2e-3):
     return L, o, masks, Cs, target, Ps
 
 
-def test_adjoint_matches_finite_differences():
+@pytest.mark.parametrize("xmax", [8.0, 0.3], ids=["one-series", "substeps"])
+def test_adjoint_matches_finite_differences(xmax):
     """Adjoint of the truncated Taylor map with the subspace sequence held fixed
     agrees with central differences of the same replayed map (extension; the paper
-    has no gradient: parity pinned by finite differences)."""
+    has no gradient: parity pinned by finite differences); also when every step
+    is split into several series."""
     eps = W.seeded_normal(3, 7) * 0.2
     base = (0.4, 0.7, 1.1, eps)
-    L0, o, masks, Cs, target, _ = _loss_run(base, record=True)
+    L0, o, masks, Cs, target, _ = _loss_run(base, record=True, xmax=xmax)
+    assert (o.stats()["substeps"] > 1) == (xmax < 1.0)
     t, a = o.rows()
     dL_dc = np.where(t[:, 0] == 0, 2.0 * a, 0.0)
     grad = o.backward(len(Cs), dL_dc_final=dL_dc, dL_dC=2.0 * (Cs - target))
@@ -368,8 +371,8 @@ def test_adjoint_matches_finite_differences():
 
     for p in range(3 + 3):
         h = 1e-5
-        lp = _loss_run(perturbed(p, h), keeps=masks)[0]
-        lm = _loss_run(perturbed(p, -h), keeps=masks)[0]
+        lp = _loss_run(perturbed(p, h), keeps=masks, xmax=xmax)[0]
+        lm = _loss_run(perturbed(p, -h), keeps=masks, xmax=xmax)[0]
         fd = (lp - lm) / (2 * h)
         assert abs(grad[p] - fd) <= 1e-6 * max(1.0, abs(fd)), (p, grad[p], fd)
 
@@ -626,3 +629,53 @@ def test_energy_value_is_the_expectation_in_the_rescued_state():
 
 def test_energy_pin_fails_on_a_dropped_conjugate():
     assert _energy_run(mutant="ENERGY_CONJ") > 1e-3
+
+
+# ---------------------------------------------------------------- substepping (App. C.1, App. I)
+def _ring4_state_after(dt, nsteps, xmax):
+    eps, H, D, strides = _ring4_dense()
+    o = Oracle(4, W.RING, J=1.0, eps=eps, omega=1.0, g=1.0, cap=4, m=2, m_init=-1, xmax=xmax)
+    o.set_state([0], [[0] * 4], [1.0])
+    psi0 = state_vector(o, D, strides, H.shape[0])
+    for _ in range(nsteps):
+        o.step(dt, 0.0)
+    return o, state_vector(o, D, strides, H.shape[0]), propagator(H)(nsteps * dt, psi0)
+
+
+def test_large_dt_substeps_match_dense_expm():
+    """App. I: past a threshold in dt the single-series step fails and the norm
+    explodes (here dt = 3 on the full ring4 space, ||H|| = 19.4: the norm
+    grows past 1e100).  Split into s = ceil(rho dt / 8) series (App. C.1's
+    scaling), the same steps equal exp(-iHt) psi0 to 1e-12."""
+    o, v, ref = _ring4_state_after(3.0, 10, 8.0)
+    st = o.stats()
+    assert st["substeps"] == math.ceil(st["hbound"] * 3.0 / 8.0) and st["substeps"] >= 8
+    assert np.linalg.norm(v - ref) <= 1e-12
+    o1, v1, _ = _ring4_state_after(3.0, 10, 0.0)
+    assert o1.stats()["substeps"] == 1 and o1.stats()["norm"] > 1e100
+
+
+@pytest.mark.parametrize("dt", [0.05, 0.5, 1.5])
+def test_substeps_are_exact_at_moderate_dt(dt):
+    o, v, ref = _ring4_state_after(dt, 6, 8.0)
+    assert np.linalg.norm(v - ref) <= 1e-12
+
+
+def test_hbound_bounds_the_restricted_norm():
+    """rho (largest row sum of |eps_s| + sum_j |omega_j| n_j + the absolute
+    off-diagonal elements of H over H_eff, each term rounded up to 2^-20) is an
+    upper bound of ||P H P||_2; checked against that sum taken from the dense H
+    (off-diagonal part) and the tuples (diagonal part)."""
+    eps, H, D, strides = _ring4_dense()
+    o = Oracle(4, W.RING, J=1.0, eps=eps, omega=1.0, g=1.0, cap=4, m=2, m_init=2)
+    o.set_state([0], [[0] * 4], [1.0])
+    for _ in range(8):
+        o.step(0.05, 1e-3)
+        t, _ = o.rows()
+        idx = dense_index(t, D, strides)
+        HP = H[np.ix_(idx, idx)]
+        rho = o.stats()["hbound"]
+        off = np.abs(H[idx]).sum(1) - np.abs(H[idx, idx])
+        rowsum = np.max(off + np.abs(eps[t[:, 0]]) + t[:, 1:].sum(1))
+        assert np.max(np.abs(np.linalg.eigvalsh(HP))) <= rho
+        assert rowsum <= rho <= rowsum + 12 * 2.0 ** -20

@@ -107,8 +107,9 @@ def test_initial_expansion_keys_bitexact(libpaces, name, over):
 @pytest.mark.parametrize("name,over", SET_STATE_CASES, ids=[c[0] for c in SET_STATE_CASES])
 def test_hamiltonian_parity(libpaces, name, over, precision):
     """P_m H P_m: per-row counts, columns and values in move order, diagonal
-    (bit-exact in FP64; within the double-word rounding, 2^-47 relative,
-    when the diagonal is held as a double-word)."""
+    (in FP64 within 2^-50 relative: eps_s + sum_j omega_j n_j summed in another
+    order; within the double-word rounding, 2^-47 relative, when the diagonal is
+    held as a double-word)."""
     cfg = W.WORKLOADS[name]
     gpu, ora = make_pair(cfg, gpu_extra=dict(precision=precision), **over)
     st = W.start_state(cfg)
@@ -120,7 +121,7 @@ def test_hamiltonian_parity(libpaces, name, over, precision):
     assert np.array_equal(colg, colo)
     assert np.array_equal(vg, vo)
     if precision == B.C128:
-        assert np.array_equal(dg, do)
+        assert np.all(np.abs(dg - do) <= 2.0 ** -50 * np.abs(do))
     else:
         assert np.all(np.abs(dg - do) <= 2.0 ** -47 * np.abs(do))
 
