@@ -277,13 +277,15 @@ def cpu_baseline(name, budget_s=15.0):
                       % (min(r[2] for r in allc), name, max(r[1] for r in allc), allc[0][3], len(allc), one[2])}
 
 
-def ensemble_model(cfg, realisations=None):
-    """Model keyword arguments; a disorder ensemble gets batch R and its eps table."""
+def ensemble_model(cfg, realisations=None, block=None):
+    """Model keyword arguments; a disorder ensemble gets batch R and its eps
+    table, or, with block = (lo, hi), the realisations lo..hi-1 of it."""
     model = W.model_kwargs(cfg)
     if "realisations" in cfg:
         R = int(realisations or cfg["realisations"])
-        model["batch"] = R
-        model["eps"] = np.stack([W.realisation_eps(cfg, r) for r in range(R)])
+        lo, hi = block if block is not None else (0, R)
+        model["batch"] = hi - lo
+        model["eps"] = np.stack([W.realisation_eps(cfg, r) for r in range(lo, hi)])
     return model
 
 
@@ -422,6 +424,8 @@ def main():
     ap.add_argument("--compare", action="store_true",
                     help="also time the plain FP64 single-instance form and report observable errors")
     ap.add_argument("--compare-sample", type=int, default=4)
+    ap.add_argument("--replicas", action="store_true",
+                    help="ensembles under several ranks: every rank runs all realisations instead of a block")
     args = ap.parse_args()
     cfg = W.WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -444,7 +448,15 @@ def main():
     end = args.end_step or cfg["nsteps"]
     start = max(0, end - K - Wm)
     prec = {"dw": B.DW, "c128": B.C128, "c64": B.C64_SPMV}
-    model = ensemble_model(cfg, args.realisations)
+    # an ensemble under several ranks is sharded: rank k evolves its block of
+    # realisations; the disorder-averaged C(t) is one all-reduce at the end
+    R_all = int(args.realisations or cfg.get("realisations", 1))
+    shard = R_all > 1 and ws > 1 and not args.replicas
+    block = None
+    if shard:
+        from paper_2603_07341_gb300.sharding import shard_range
+        block = shard_range(R_all, ws, rank)
+    model = ensemble_model(cfg, args.realisations, block)
     model["precision"] = prec[args.precision]
     R = int(model.get("batch", 1))
 
@@ -466,6 +478,18 @@ def main():
     sol, ms, t_host, all_units, rec = run["solver"], run["ms"], run["t_host"], run["all_units"], run["rec"]
     stage_ms, launches, stage_bytes = run["stage_ms"], run["launches"], run["stage_bytes"]
     units, tbytes, tflops = taylor_counts(rec, sol)
+    ens = None
+    if shard:
+        from paper_2603_07341_gb300.sharding import run_sharded_ensemble
+        nrec = sol.num_records()
+        R_loc = int(model["batch"])
+        allrec = sol.observables(0, nrec)
+        C_loc = B.records_dict(allrec, cfg["n_sites"], R_loc)["C_r"] if R_loc > 1 else \
+            (allrec[:, 4] + 1j * allrec[:, 5]).reshape(-1, 1)
+        C_mean, _, _ = run_sharded_ensemble(R_all, nrec - 1, lambda lo, hi: C_loc, device="cuda")
+        ens = {"realisations": R_all, "block": list(block), "C_mean_final": [float(C_mean[-1].real),
+                                                                             float(C_mean[-1].imag)],
+               "collective": "one all-reduce (sum) of sum_r C_r(t) over %d records" % nrec}
     t_max, total_units, t_host, all_units = reduce_over_ranks(dist, ms, units, t_host, all_units, "cuda")
     value = total_units / (t_max / 1e3)
 
@@ -511,7 +535,8 @@ def main():
         q = rec[:, 6]
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": Wm,
-            "ms_per_step": t_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "ms_per_step": t_max / K, "higher_is_better": True, "scaling": "strong" if shard else "weak",
+            "vs_baseline": None,
             "dtype": {"dw": "f32x2 (double-word FP32, 48-bit significand)", "c128": "f64",
                       "c64": "f32 terms, f32x2 accumulator"}[sol_precision(model)],
             "data": "synthetic",
@@ -519,7 +544,8 @@ def main():
                            args.workload, W.describe(cfg), start + Wm + 1, start + Wm + K, cfg["nsteps"]),
                        "rows_mean": float(np.mean(q)), "rows_max": float(np.max(q)),
                        "nnz_mean": float(np.mean(rec[:, 8])), "terms_mean": float(np.mean(rec[:, 9])),
-                       "parallelism": "replicas" if ws > 1 else "single GPU",
+                       "parallelism": ("realisations sharded over %d ranks" % ws) if shard else
+                                      ("replicas" if ws > 1 else "single GPU"),
                        "l2": "no flush between steps; per-step working set %.0f MB vs 129 MB L2"
                              % (np.max(q) * (16 * 4 + 8 * 2 + 16 * 2 + 4 * 4 + 5 * 4 + 9) / 1e6)},
             "steps_per_s": K / (t_max / 1e3),
@@ -533,11 +559,13 @@ def main():
                                       for n, b, m in zip(B.STAGES, stage_bytes, stage_ms)},
             "clocks": clk.summary(),
         }
-        if R > 1:
-            line["config"]["realisations"] = R
+        if R > 1 or shard:
+            line["config"]["realisations"] = R_all if shard else R
             line["config"]["units"] = "rows of all realisations x Taylor terms"
         if variants is not None:
             line["variants"] = variants
+        if ens is not None:
+            line["ensemble"] = ens
         print(json.dumps(line))
     sol.close()
     if dist is not None:
