@@ -354,6 +354,19 @@ paces_status paces_record(paces_t h, int32_t ckpt_every);
 paces_status paces_backward(paces_t h, int64_t nsteps, const double* dL_dc_final, const double* dL_dC,
                             const double* dL_dP, double* grad);
 
+/* ---- Self-test of the bounded grid barrier (no counterpart in the paper) ----
+ * The propagator runs all Taylor terms of a step in one cooperative launch
+ * whose blocks meet at a grid barrier after every term; every wait there is
+ * bounded, and a wait that runs out records a device error instead of hanging.
+ * This call exercises that path on the current device: one 256-thread block
+ * per SM arrives at a barrier that expects (SMs + extra_arrivals) arrivals,
+ * with a limit of timeout_ms (0 < timeout_ms <= 10000).  extra_arrivals = 0:
+ * the barrier completes and *device_error = 0; extra_arrivals > 0: no block is
+ * the last to arrive, every wait runs out and *device_error = 5 (the barrier
+ * error code).  The context stays usable.  Allocates and frees its own small
+ * buffers with cudaMalloc.  Returns INVALID or CUDA. */
+paces_status paces_selftest_barrier(int32_t extra_arrivals, double timeout_ms, int32_t* device_error);
+
 /* ---- Expansion without allocation (no counterpart in the paper) -----------
  * Some callers cannot allocate device memory: hosts whose framework has
  * already reserved all of it in its own pool, real-time loops that must never

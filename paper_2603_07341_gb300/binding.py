@@ -30,7 +30,7 @@ EXPORTED = (
     "paces_get_levels", "paces_get_keep", "paces_get_hamiltonian", "paces_record_len",
     "paces_num_records", "paces_observables", "paces_profile", "paces_stage_stats",
     "paces_expand_noalloc", "paces_get_tuning", "paces_set_tuning", "paces_record", "paces_backward",
-    "paces_step_nom",
+    "paces_step_nom", "paces_selftest_barrier",
 )
 
 
@@ -139,6 +139,8 @@ def load():
     lib.paces_backward.argtypes = [P, C.c_int64, dp, dp, dp, dp]
     lib.paces_expand_noalloc.restype = S
     lib.paces_expand_noalloc.argtypes = [C.POINTER(Params), P, C.c_int64, P, C.c_int64, i64p, P]
+    lib.paces_selftest_barrier.restype = S
+    lib.paces_selftest_barrier.argtypes = [C.c_int32, C.c_double, C.POINTER(C.c_int32)]
     _lib = lib
     return lib
 
@@ -455,3 +457,14 @@ def records_dict(rec, N, batch=1):
     c = rec[:, o + 2 * R * N:o + 2 * R * N + 2 * R].reshape(-1, R, 2)
     d["C_r"] = c[:, :, 0] + 1j * c[:, :, 1]
     return d
+
+
+def selftest_barrier(extra_arrivals, timeout_ms=1.0):
+    """Run the bounded grid barrier on the current device (paces_selftest_barrier):
+    returns the device error code it recorded (0: completed, 5: a wait ran out)."""
+    lib = load()
+    err = C.c_int32(-1)
+    rc = lib.paces_selftest_barrier(int(extra_arrivals), float(timeout_ms), C.byref(err))
+    if rc:
+        raise PacesError(rc, "paces_selftest_barrier")
+    return int(err.value)

@@ -39,8 +39,10 @@ struct TaylorArgs {
 
 // Barrier that also reduces the per-block partials: the last block to arrive
 // sums them in block order and publishes the four totals before releasing the
-// others.  Every wait is bounded (kBarrierTimeoutNs).
-__device__ __forceinline__ bool barrier_reduce(Counters* ctr, const double* part, double* tot, unsigned G)
+// others.  Every wait is bounded (timeout_ns, kBarrierTimeoutNs by default):
+// a wait that runs out records kErrBarrier and the block returns false.
+__device__ __forceinline__ bool barrier_reduce(Counters* ctr, const double* part, double* tot, unsigned G,
+                                               uint64_t timeout_ns = kBarrierTimeoutNs)
 {
     __shared__ int last, ok;
     __threadfence();          // publish this thread's partial before the block arrives
@@ -74,7 +76,7 @@ __device__ __forceinline__ bool barrier_reduce(Counters* ctr, const double* part
         uint64_t t0 = global_ns();
         while (*(volatile unsigned*)&ctr->bar_gen == g) {
             __nanosleep(20);
-            if (global_ns() - t0 > kBarrierTimeoutNs) {
+            if (global_ns() - t0 > timeout_ns) {
                 atomicCAS(&ctr->err, 0, (int)kErrBarrier);
                 ok = 0;
                 break;
@@ -84,6 +86,18 @@ __device__ __forceinline__ bool barrier_reduce(Counters* ctr, const double* part
     }
     __syncthreads();
     return ok != 0;
+}
+
+// Self-test of the bounded wait: every block arrives at a barrier that expects
+// `expect` arrivals.  With expect == gridDim.x it completes; with more, no block
+// is the last to arrive, every wait runs out after timeout_ns and kErrBarrier is
+// recorded, and the kernel returns with the context intact.
+__global__ void __launch_bounds__(kBlock) k_barrier_selftest(Counters* ctr, double* part, double* tot,
+                                                             unsigned expect, unsigned long long timeout_ns)
+{
+    double z[4] = {1.0, 0.0, 0.0, 0.0};
+    block_sum<kBlock, 4>(z, part + 4 * blockIdx.x);
+    barrier_reduce(ctr, part, tot, expect, timeout_ns);
 }
 
 // y_row = (P H P x)_row for the rows of one warp round; LPR lanes per row.
@@ -817,6 +831,23 @@ int launch_taylor(const Bufs& b, const TaylorParams& p, cudaStream_t st)
     cfg.numAttrs = 1;
     cudaError_t e = cudaLaunchKernelExC(&cfg, fn, args);
     return e == cudaSuccess ? 1 : -1;
+}
+
+int launch_barrier_selftest(Counters* ctr, double* part, int grid, unsigned expect, unsigned long long timeout_ns,
+                            cudaStream_t st)
+{
+    double* tot = part + 4 * (size_t)grid;
+    void* args[] = {&ctr, &part, &tot, &expect, &timeout_ns};
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kBlock);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, (const void*)k_barrier_selftest, args) == cudaSuccess ? 1 : -1;
 }
 
 }  // namespace paces

@@ -1464,6 +1464,36 @@ paces_status paces_set_tuning(paces_t h, const paces_tuning* in)
 
 int32_t paces_record_len(paces_t h) { return h ? h->b.rec_len : 0; }
 
+paces_status paces_selftest_barrier(int32_t extra_arrivals, double timeout_ms, int32_t* device_error)
+{
+    if (!device_error || extra_arrivals < 0 || !(timeout_ms > 0.0) || timeout_ms > 10000.0) return PACES_ERR_INVALID;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+        return PACES_ERR_CUDA;
+    Counters* ctr = nullptr;
+    double* part = nullptr;
+    const size_t pbytes = sizeof(double) * (4 * (size_t)sms + 8);
+    if (cudaMalloc(&ctr, sizeof(Counters)) != cudaSuccess) return PACES_ERR_CUDA;
+    if (cudaMalloc(&part, pbytes) != cudaSuccess) {
+        cudaFree(ctr);
+        return PACES_ERR_CUDA;
+    }
+    paces_status s = PACES_OK;
+    Counters hc;
+    if (cudaMemset(ctr, 0, sizeof(Counters)) != cudaSuccess || cudaMemset(part, 0, pbytes) != cudaSuccess ||
+        launch_barrier_selftest(ctr, part, sms, (unsigned)(sms + extra_arrivals),
+                                (unsigned long long)(timeout_ms * 1e6), 0) < 0 ||
+        cudaStreamSynchronize(0) != cudaSuccess ||
+        cudaMemcpy(&hc, ctr, sizeof(Counters), cudaMemcpyDeviceToHost) != cudaSuccess)
+        s = PACES_ERR_CUDA;
+    else
+        *device_error = hc.err;
+    cudaFree(part);
+    cudaFree(ctr);
+    return s;
+}
+
 paces_status paces_num_records(paces_t h, int64_t* n)
 {
     if (!h || !n) return PACES_ERR_INVALID;

@@ -118,6 +118,9 @@ int launch_export_csr(const Bufs& b, uint32_t q, const uint64_t* off, int32_t* c
                       double* vals, cudaStream_t st);
 
 int taylor_blocks_per_sm(int lpr, int precision);
+// Cooperative self-test of the bounded grid barrier (kern_taylor.cu).
+int launch_barrier_selftest(Counters* ctr, double* part, int grid, unsigned expect, unsigned long long timeout_ns,
+                            cudaStream_t st);
 
 // Reverse pass of one step (kern_adjoint.cu).
 int launch_adj_obs(const Bufs& b, int gen, const void* vec, const double* dLdP, const double2* wC, double2* gbar,

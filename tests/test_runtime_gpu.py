@@ -69,3 +69,20 @@ def test_autotuner_picks_valid_settings(libpaces, tmp_path):
     tr, ar = ref.tuples()
     assert np.array_equal(ts, tr)
     assert np.max(np.abs(as_ - ar)) <= 1e-12 * np.linalg.norm(ar)
+
+
+def test_grid_barrier_time_limit_runs_out_safely(libpaces):
+    """The propagator's grid barrier bounds every wait: a barrier that expects
+    one arrival more than the grid has runs out after 1 ms and records the
+    barrier error (5) instead of hanging; the context stays usable (a full
+    barrier then completes, and a solver still steps)."""
+    import torch
+    assert B.selftest_barrier(0, 1.0) == 0
+    assert B.selftest_barrier(1, 1.0) == 5
+    assert B.selftest_barrier(0, 1.0) == 0
+    torch.cuda.synchronize()
+    cfg = W.WORKLOADS["ring4"]
+    s = B.Solver(**W.model_kwargs(cfg))
+    s.set_state(*W.start_state(cfg))
+    s.step(cfg["dt"], 2, cfg["theta"])
+    assert s.num_records() == 3
