@@ -64,23 +64,19 @@ __global__ void __launch_bounds__(kBlock) k_rs_hist(const Counters* __restrict__
     for (int d = threadIdx.x; d < kDigits; d += blockDim.x) hist[(size_t)d * gridDim.x + blockIdx.x] = h[d];
 }
 
-// Exclusive scan of hist[0 .. kDigits * G) in place (digit-major, block-minor):
-// the first output position of every (digit, block).
-__global__ void __launch_bounds__(1024) k_rs_scan(const Counters* __restrict__ ctr, uint32_t* __restrict__ hist, int G)
+// One block per digit d: exclusive scan of the G block counts hist[d G ..
+// d G + G) in place (G <= 1024, one count per thread) and the digit's total in
+// dtot[d].  The scatter adds the exclusive scan of the 256 totals itself.
+__global__ void __launch_bounds__(1024) k_rs_scan(const Counters* __restrict__ ctr, uint32_t* __restrict__ hist,
+                                                  uint32_t* __restrict__ dtot, int G)
 {
     if (ctr->err) return;
-    const uint32_t n = (uint32_t)kDigits * (uint32_t)G;
-    const uint32_t per = (n + blockDim.x - 1) / blockDim.x;
-    const uint32_t a = threadIdx.x * per, b = min(n, a + per);
-    uint32_t s = 0;
-    for (uint32_t i = a; i < b; ++i) s += hist[i];
+    uint32_t* h = hist + (size_t)blockIdx.x * G;
+    const uint32_t v = (int)threadIdx.x < G ? h[threadIdx.x] : 0u;
     uint32_t tot;
-    uint32_t run = block_excl_scan<1024>(s, &tot);
-    for (uint32_t i = a; i < b; ++i) {
-        uint32_t v = hist[i];
-        hist[i] = run;
-        run += v;
-    }
+    const uint32_t ex = block_excl_scan<1024>(v, &tot);
+    if ((int)threadIdx.x < G) h[threadIdx.x] = ex;
+    if (threadIdx.x == 0) dtot[blockIdx.x] = tot;
 }
 
 // Stable scatter of one digit.  Each block walks its chunk in tiles of
@@ -100,7 +96,8 @@ template <int W>
 __global__ void __launch_bounds__(kBlock) k_rs_scatter(const Counters* __restrict__ ctr,
                                                        const uint64_t* __restrict__ kin, const uint32_t* __restrict__ iin,
                                                        uint64_t* __restrict__ kout, uint32_t* __restrict__ iout,
-                                                       int word, int shift, const uint32_t* __restrict__ offs)
+                                                       int word, int shift, const uint32_t* __restrict__ offs,
+                                                       const uint32_t* __restrict__ dtot)
 {
     static_assert(kBlock == kDigits, "one thread per digit in the per-tile scans");
     constexpr int IPT = ScatterTile<W>::kIPT, T = ScatterTile<W>::kItems;
@@ -115,7 +112,11 @@ __global__ void __launch_bounds__(kBlock) k_rs_scatter(const Counters* __restric
     uint32_t n = ctr->kept, lo, hi;
     chunk_of(n, gridDim.x, blockIdx.x, lo, hi);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    base[threadIdx.x] = offs[(size_t)threadIdx.x * gridDim.x + blockIdx.x];
+    {   // first output position of (digit, block): the digits below it, then the earlier blocks
+        uint32_t all;
+        const uint32_t below = block_excl_scan<kBlock>(dtot[threadIdx.x], &all);
+        base[threadIdx.x] = below + offs[(size_t)threadIdx.x * gridDim.x + blockIdx.x];
+    }
     for (uint32_t t0 = lo; t0 < hi; t0 += T) {
         run[threadIdx.x] = 0u;
         int dg[IPT];
@@ -194,7 +195,8 @@ __global__ void __launch_bounds__(kBlock) k_trunc_place(Counters* ctr, const uin
                                                         const uint32_t* __restrict__ meta_in,
                                                         uint64_t* __restrict__ keys_out, double2* __restrict__ c_out,
                                                         uint32_t* __restrict__ meta_out, uint64_t* table_out,
-                                                        uint64_t slots, uint32_t* __restrict__ from, int step)
+                                                        uint64_t slots, UDiv dexc, uint32_t* __restrict__ from,
+                                                        int step)
 {
     if (ctr->err) return;
     const uint32_t n = ctr->kept;
@@ -205,7 +207,7 @@ __global__ void __launch_bounds__(kBlock) k_trunc_place(Counters* ctr, const uin
         c_out[dst] = c_in[src];
         meta_out[dst] = meta_in[src];
         if (from) from[dst] = src;
-        if (!table_insert_unique<W>(table_out, slots, k, dst)) set_err(ctr, kErrProbe, step, 1);
+        if (!table_insert_unique<W>(table_out, slots, dexc, k, dst)) set_err(ctr, kErrProbe, step, 1);
     }
 }
 
@@ -219,15 +221,17 @@ static int sorted_m(const Bufs& b, int gin, int gout, int step, cudaStream_t st)
     for (int w = 0; w < W; ++w) {
         for (int s = 0; s < b.key_bits[w]; s += 8) {
             k_rs_hist<W><<<b.G, kBlock, 0, st>>>(b.ctr, b.sortk[cur], w, s, b.rs_hist);
-            k_rs_scan<<<1, 1024, 0, st>>>(b.ctr, b.rs_hist, b.G);
+            k_rs_scan<<<kDigits, 1024, 0, st>>>(b.ctr, b.rs_hist, b.rs_hist + (size_t)kDigits * b.G, b.G);
             k_rs_scatter<W><<<b.G, kBlock, 0, st>>>(b.ctr, b.sortk[cur], b.sorti[cur], b.sortk[1 - cur],
-                                                     b.sorti[1 - cur], w, s, b.rs_hist);
+                                                     b.sorti[1 - cur], w, s, b.rs_hist,
+                                                     b.rs_hist + (size_t)kDigits * b.G);
             cur = 1 - cur;
             n += 3;
         }
     }
     k_trunc_place<W><<<b.grid, kBlock, 0, st>>>(b.ctr, b.sortk[cur], b.sorti[cur], b.V[0], b.meta[gin], b.keys[gout],
-                                                 b.V[1], b.meta[gout], b.table[gout], b.table_slots, b.from, step);
+                                                 b.V[1], b.meta[gout], b.table[gout], b.table_slots, b.div_exc, b.from,
+                                                 step);
     return n + 1;
 }
 

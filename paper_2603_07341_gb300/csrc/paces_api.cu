@@ -896,9 +896,10 @@ paces_status paces_create(const paces_params* params, const paces_allocator* all
     }
 
     b.model = alloc_track<DevModel>(h, h->fixed_allocs, 1);
+    b.div_exc = M->div_exc;
     b.ctr = alloc_track<Counters>(h, h->fixed_allocs, 1);
     b.topq = alloc_track<TopqState>(h, h->fixed_allocs, 1);
-    b.rs_hist = alloc_track<uint32_t>(h, h->fixed_allocs, 256 * (size_t)kMaxChunkBlocks);
+    b.rs_hist = alloc_track<uint32_t>(h, h->fixed_allocs, 256 * (size_t)kMaxChunkBlocks + 256);
     b.blk_cnt = alloc_track<uint32_t>(h, h->fixed_allocs, kMaxChunkBlocks);
     b.blk_off = alloc_track<uint32_t>(h, h->fixed_allocs, kMaxChunkBlocks);
     b.partials = alloc_track<double>(h, h->fixed_allocs, 8 * (size_t)h->sms * std::max(bps, bps_max) + 16);

@@ -46,6 +46,7 @@ struct Bufs {
     uint32_t* meta[2];             // row -> (site, phonons at site, total phonons)
     uint64_t* table[2];            // hash tables, two generations
     uint64_t table_slots;          // slots per table (below 2^32)
+    UDiv div_exc;                  // key word 0 / exciton radix (table placement)
     double2* V[4];                 // V0: state / accumulator r, V1: c' (phi_0), V2, V3: terms
     float2* F[2];                  // complex64 term buffers (C64_SPMV)
     uint32_t* col;                 // P H P columns, row pitch P
