@@ -65,6 +65,7 @@ def _load(mutant=None):
         lib.or_set_xmax.argtypes = [P, C.c_double]
         lib.or_get_hopping.argtypes = [P, dp]
         lib.or_set_state.argtypes = [P, C.c_int, ip, ip, dp]
+        lib.or_load_state.argtypes = [P, C.c_int, ip, ip, dp]
         lib.or_step.argtypes = [P, C.c_double, C.c_double, C.POINTER(C.c_ubyte), C.c_int]
         lib.or_step_nom.argtypes = [P, C.c_double, C.c_longlong, C.c_ulonglong]
         lib.or_nom_keep.argtypes = [P, C.c_longlong, C.c_ulonglong, C.POINTER(C.c_ubyte)]
@@ -152,6 +153,16 @@ class Oracle:
         rc = self._lib.or_set_state(self._h, len(site), _ip(site), _ip(occ), _dp(ri))
         if rc:
             raise OracleError(rc, "or_set_state")
+
+    def load_state(self, site, occ, amps):
+        """A mid-trajectory state taken as the current H_eff and vector."""
+        site = np.ascontiguousarray(site, dtype=np.int32)
+        occ = np.ascontiguousarray(occ, dtype=np.int32).reshape(len(site), self.N)
+        a = np.asarray(amps, dtype=np.complex128)
+        ri = np.ascontiguousarray(np.stack([a.real, a.imag], 1).reshape(-1))
+        rc = self._lib.or_load_state(self._h, len(site), _ip(site), _ip(occ), _dp(ri))
+        if rc:
+            raise OracleError(rc, "or_load_state")
 
     def step(self, dt, theta, keep=None):
         kp, kl = None, 0

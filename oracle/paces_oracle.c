@@ -447,6 +447,45 @@ int or_set_state(oracle_t* o, int n, const int* site, const int* occ, const doub
     return OR_OK;
 }
 
+int or_load_state(oracle_t* o, int n, const int* site, const int* occ, const double* amps)
+{
+    if (!o || n <= 0 || !site || !occ || !amps) return OR_INVALID;
+    int N = o->N, len = o->len;
+    rs_free(&o->rows);
+    rs_init(&o->rows, len);
+    int* tup = (int*)malloc(sizeof(int) * (size_t)len);
+    if (!tup || ensure_c(o, n)) { free(tup); return OR_NOMEM; }
+    for (int i = 0; i < n; ++i) {
+        if (site[i] < 0 || site[i] >= N) { free(tup); return OR_INVALID; }
+        tup[0] = site[i];
+        for (int j = 0; j < N; ++j) {
+            int v = occ[(size_t)i * N + j];
+            if (v < 0 || v > o->cap[j]) { free(tup); return OR_INVALID; }
+            tup[1 + j] = v;
+        }
+        if (rs_find(&o->rows, tup) >= 0) { free(tup); return OR_INVALID; }
+        if (rs_add(&o->rows, tup) < 0) { free(tup); return OR_NOMEM; }
+        o->c[i] = amps[2 * i] + I * amps[2 * i + 1];
+    }
+    free(tup);
+    o->fresh = 0;
+    o->nlvl = 0;
+    lvl_push(o, 0);
+    lvl_push(o, n);
+    free(o->keep);
+    o->keep = NULL;
+    o->nkeep = 0;
+    free(o->last_from);
+    o->last_from = NULL;
+    free_recs(o);
+    observe(o);
+    o->st[OR_ST_ROWS] = n;
+    o->st[OR_ST_KEPT] = n;
+    o->st[OR_ST_NORM_PHI0] = o->st[OR_ST_NORM];
+    o->st[OR_ST_NORM_BEFORE] = o->st[OR_ST_NORM];
+    return OR_OK;
+}
+
 long or_build_hamiltonian(oracle_t* o, int* cnt, int* cols, double* vals, double* diag)
 {
     int q = o->rows.nrows, len = o->len, D = max_moves(o);

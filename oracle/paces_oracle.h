@@ -48,6 +48,12 @@ void or_get_hopping(const oracle_t* o, double* out);
  * H_eff(0) is the ball of radius m_init (m_init < 0: closure) around them. */
 int or_set_state(oracle_t* o, int n, const int* site, const int* occ, const double* amps);
 
+/* A mid-trajectory state: n distinct rows (same form) with their amplitudes
+ * become the current H_eff and vector exactly as a completed step leaves them,
+ * so the next step truncates and regrows from them.  psi(0), the reference of
+ * C(t), and the time are kept. */
+int or_load_state(oracle_t* o, int n, const int* site, const int* occ, const double* amps);
+
 /* One time step.  keep_override (length = rows before the step, or NULL)
  * replaces the threshold decision row by row. */
 int or_step(oracle_t* o, double dt, double theta, const unsigned char* keep_override,

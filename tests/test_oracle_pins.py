@@ -679,3 +679,26 @@ def test_hbound_bounds_the_restricted_norm():
         rowsum = np.max(off + np.abs(eps[t[:, 0]]) + t[:, 1:].sum(1))
         assert np.max(np.abs(np.linalg.eigvalsh(HP))) <= rho
         assert rowsum <= rho <= rowsum + 12 * 2.0 ** -20
+
+
+def test_load_state_continues_the_trajectory_exactly():
+    """A state taken from step k and loaded into a fresh oracle (with the same
+    psi(0)) continues bit for bit as the uninterrupted run: the test
+    infrastructure the GPU parity at scale relies on."""
+    cfg = W.WORKLOADS["ring16"]
+    a = oracle_for(cfg, m_init=4)
+    a.set_state(*W.start_state(cfg))
+    for _ in range(6):
+        a.step(0.02, 1e-5)
+    t, amp = a.rows()
+    b = oracle_for(cfg, m_init=4)
+    b.set_state(*W.start_state(cfg))
+    b.load_state(t[:, 0], t[:, 1:], amp)
+    for _ in range(3):
+        a.step(0.02, 1e-5)
+        b.step(0.02, 1e-5)
+        ta, aa = a.rows()
+        tb, ab = b.rows()
+        assert np.array_equal(ta, tb) and np.array_equal(aa, ab)
+        sa, sb = a.stats(), b.stats()
+        assert all(sa[k] == sb[k] for k in sa if k != "time")     # b's clock started at its set_state
