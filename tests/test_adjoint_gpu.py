@@ -219,3 +219,34 @@ def test_cube4_directional_derivative_at_scale(libpaces):
         pytest.skip("the perturbation moved a row across theta")
     fd = (Lp - Lm) / (2 * h)
     assert abs(g @ v - fd) <= 1e-6 * max(1.0, abs(fd)), (g @ v, fd)
+
+
+def test_cube4_population_spectrum_loss_gradient(libpaces):
+    """The gradient workload's loss -- site-0 population at T plus the mean
+    squared deviation of the absorption spectrum from a seeded target (the
+    spectrum of a run at parameters perturbed by 5% seeded noise) -- through
+    the autograd function: grad . v against central differences of the same
+    loss along a seeded direction (4x4x4 cube, theta = 1e-4, 40 steps,
+    checkpoints every 20)."""
+    import torch
+    from paper_2603_07341_gb300.autograd import population_spectrum_loss, seeded_target
+    cfg = W.WORKLOADS["cube4"]
+    nsteps, dt, theta = 40, cfg["dt"], cfg["theta"]
+    N = cfg["n_sites"]
+    model = W.model_kwargs(cfg)
+    start = W.start_state(cfg)
+    p0 = np.concatenate([[cfg["J"], cfg["g"], cfg["omega"]], np.zeros(N)])
+    omega = np.linspace(-6.0, 6.0, 1024)
+    A_t = seeded_target(model, start, dt, nsteps, theta, omega, p0 + np.r_[0, 0, 0, 0.01 * np.ones(N)])
+    p = torch.tensor(p0, dtype=torch.float64, requires_grad=True)
+    L = population_spectrum_loss(p, model, start, dt, nsteps, theta, omega, A_t, ckpt_every=cfg["ckpt_every"])
+    L.backward()
+    g = p.grad.numpy()
+    v = W.seeded_normal(3 + N, 91)
+    v /= np.linalg.norm(v)
+    h = 1e-6
+    with torch.no_grad():
+        Lp = float(population_spectrum_loss(torch.tensor(p0 + h * v), model, start, dt, nsteps, theta, omega, A_t))
+        Lm = float(population_spectrum_loss(torch.tensor(p0 - h * v), model, start, dt, nsteps, theta, omega, A_t))
+    fd = (Lp - Lm) / (2 * h)
+    assert np.isfinite(g).all() and abs(g @ v - fd) <= 1e-5 * max(1.0, abs(fd)), (g @ v, fd)

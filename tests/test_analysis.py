@@ -1,5 +1,6 @@
 """Host post-processing against the oracle's spectrum and closed forms."""
 import numpy as np
+import pytest
 
 from oracle.oracle import absorption_spectrum as oracle_spectrum
 from paper_2603_07341_gb300 import analysis as A
@@ -32,3 +33,18 @@ def test_rmsd_closed_forms():
     r = A.rmsd(P)
     assert np.allclose(r, [0.0, 2.0, np.sqrt(2.0)])
     assert np.allclose(A.rmsd(P[1], x=[0, 1, 2, 3, 8]), 4.0)
+
+
+def test_differentiable_spectrum_equals_host_spectrum():
+    """The torch spectrum of the autograd path and the host post-processing
+    agree (same trapezoid weights, damping and sign convention)."""
+    torch = pytest.importorskip("torch")
+    from paper_2603_07341_gb300.autograd import spectrum
+    from paper_2603_07341_gb300.analysis import absorption_spectrum
+    K, dt = 64, 0.05
+    k = np.arange(1, K + 1)
+    C = np.exp(-0.7j * k * dt) * (1.0 - 0.004 * k) + 0.1 * np.exp(1.3j * k * dt)
+    om = np.linspace(-6.0, 6.0, 257)
+    A = spectrum(torch.from_numpy(np.stack([C.real, C.imag], 1)), 1.1, dt, om).numpy()
+    ref = absorption_spectrum(np.concatenate([[1.1], C]), dt, om)
+    assert np.max(np.abs(A - ref)) <= 1e-13
