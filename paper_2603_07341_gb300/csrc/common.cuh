@@ -350,6 +350,15 @@ __device__ __forceinline__ uint64_t fmix64(uint64_t h)
     return h;
 }
 
+template <int W>
+__device__ __forceinline__ uint64_t key_hash(const Key<W>& k)
+{
+    uint64_t h = fmix64(k.w[0] + 0x9E3779B97F4A7C15ull);
+#pragma unroll
+    for (int i = 1; i < W; ++i) h = fmix64(h ^ k.w[i]);
+    return h;
+}
+
 // Move mv of a state with exciton site s and n_s phonons there:
 //   mv < deg(s): hop to the mv-th neighbour (ascending site index)
 //   mv == deg(s): a_s^dag (valid if g_s != 0 and n_s < K_s)
@@ -408,60 +417,23 @@ struct Slot {
     static constexpr int kWords = (W == 1) ? 2 : (W <= 3 ? 4 : 6);
 };
 
-// Placement of a key: home slot and fingerprint.  The hash covers the key with
-// the exciton digit divided out -- the phonon occupations (and, in ensembles,
-// the realisation) -- and is placed by multiplicative range reduction of its
-// low 32 bits (any table size below 2^32); the exciton site s is then added to
-// the home slot.  The states that differ only by an exciton hop therefore
-// occupy consecutive slots (one or two cache lines for N <= 16 sites), so the
-// hop moves of a parent, and the siblings of a row in the sorted kept set,
-// probe lines that a neighbouring thread of the same warp has just loaded.
-// The fingerprint mixes s into the high hash bits (an odd multiplier keeps the
-// siblings' fingerprints distinct); the all-ones value is never used.
-struct Place {
-    uint64_t home;
-    uint64_t fp;
-};
-
-template <int W>
-__device__ __forceinline__ uint64_t phonon_hash(const Key<W>& k, const UDiv& dexc, uint64_t& s)
+// Home slot from the low 32 hash bits by multiplicative range reduction (any
+// table size below 2^32); the fingerprint comes from the high 32 bits.
+__device__ __forceinline__ uint64_t slot_home(uint64_t h, uint64_t slots)
 {
-    const uint64_t q0 = udiv(k.w[0], dexc);
-    s = k.w[0] - q0 * dexc.d;
-    uint64_t h = fmix64(q0 + 0x9E3779B97F4A7C15ull);
-#pragma unroll
-    for (int i = 1; i < W; ++i) h = fmix64(h ^ k.w[i]);
-    return h;
-}
-
-__device__ __forceinline__ uint64_t fp_of(uint64_t h, uint64_t s)
-{
-    const uint32_t f = (uint32_t)(h >> 32) + (uint32_t)s * 0x9E3779B1u;
-    return f == 0xFFFFFFFFu ? 0xFFFFFFFEull : (uint64_t)f;
-}
-
-template <int W>
-__device__ __forceinline__ Place key_place(const Key<W>& k, uint64_t slots, const UDiv& dexc)
-{
-    uint64_t s;
-    const uint64_t h = phonon_hash<W>(k, dexc, s);
-    uint64_t pos = (((h & 0xFFFFFFFFull) * slots) >> 32) + (s < slots ? s : s % slots);
-    if (pos >= slots) pos -= slots;
-    return {pos, fp_of(h, s)};
-}
-
-// The fingerprint alone (it does not depend on the table size).
-template <int W>
-__device__ __forceinline__ uint64_t key_fp(const Key<W>& k, const UDiv& dexc)
-{
-    uint64_t s;
-    const uint64_t h = phonon_hash<W>(k, dexc, s);
-    return fp_of(h, s);
+    return ((h & 0xFFFFFFFFull) * slots) >> 32;
 }
 
 __device__ __forceinline__ uint64_t slot_next(uint64_t pos, uint64_t slots)
 {
     return pos + 1 == slots ? 0 : pos + 1;
+}
+
+template <int W>
+__device__ __forceinline__ uint32_t fingerprint(uint64_t h)
+{
+    uint32_t f = (uint32_t)(h >> 32);
+    return f == 0xFFFFFFFFu ? 0xFFFFFFFEu : f;
 }
 
 // 16-byte compare-and-swap (PTX atom.cas.b128, sm_90 and later) of an aligned
@@ -485,15 +457,16 @@ __device__ __forceinline__ void cas128(uint64_t* p, uint64_t cmp_lo, uint64_t cm
 // Read-only lookup: row of key or -1.
 template <int W>
 __device__ __forceinline__ int64_t table_lookup(const uint64_t* __restrict__ table, uint64_t slots,
-                                                const UDiv& dexc, const Key<W>& key)
+                                                const Key<W>& key)
 {
-    const Place pl = key_place<W>(key, slots, dexc);
-    uint64_t pos = pl.home;
+    uint64_t h = key_hash<W>(key);
+    uint64_t fp = fingerprint<W>(h);
+    uint64_t pos = slot_home(h, slots);
     for (uint32_t probe = 0; probe < kMaxProbe; ++probe) {
         const uint64_t* sl = table + pos * Slot<W>::kWords;
         uint64_t tag = __ldg(sl);
         if (tag == kEmpty) return -1;
-        if ((tag >> 32) == pl.fp) {
+        if ((tag >> 32) == fp) {
             bool eq = true;
 #pragma unroll
             for (int i = 0; i < W; ++i) eq &= (__ldg(sl + 1 + i) == key.w[i]);
@@ -506,12 +479,12 @@ __device__ __forceinline__ int64_t table_lookup(const uint64_t* __restrict__ tab
 
 // Insert a unique row key (no duplicates possible): claim the first empty slot.
 template <int W>
-__device__ __forceinline__ bool table_insert_unique(uint64_t* table, uint64_t slots, const UDiv& dexc,
-                                                    const Key<W>& key, uint32_t row)
+__device__ __forceinline__ bool table_insert_unique(uint64_t* table, uint64_t slots, const Key<W>& key,
+                                                    uint32_t row)
 {
-    const Place pl = key_place<W>(key, slots, dexc);
-    const uint64_t tag = (pl.fp << 32) | row;
-    uint64_t pos = pl.home;
+    uint64_t h = key_hash<W>(key);
+    uint64_t tag = ((uint64_t)fingerprint<W>(h) << 32) | row;
+    uint64_t pos = slot_home(h, slots);
     for (uint32_t probe = 0; probe < kMaxProbe; ++probe) {
         uint64_t* sl = table + pos * Slot<W>::kWords;
         if (__ldcg(sl) == kEmpty) {

@@ -108,7 +108,6 @@ __global__ void __launch_bounds__(kAdjBlock) k_adj_obs_rows(const Counters* __re
 // distinct, so no two threads touch one row.
 template <int W>
 __global__ void __launch_bounds__(kAdjBlock) k_adj_obs_psi0(const uint64_t* __restrict__ table, uint64_t slots,
-                                                            UDiv dexc,
                                                             const uint64_t* __restrict__ psi0_keys,
                                                             const double2* __restrict__ psi0_amp, int64_t n0,
                                                             const double2* __restrict__ w_ptr,
@@ -117,7 +116,7 @@ __global__ void __launch_bounds__(kAdjBlock) k_adj_obs_psi0(const uint64_t* __re
     const double2 w = *w_ptr;
     if (w.x == 0.0 && w.y == 0.0) return;
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n0; j += (int64_t)gridDim.x * blockDim.x) {
-        int64_t row = table_lookup<W>(table, slots, dexc, load_key<W>(psi0_keys, (uint64_t)j));
+        int64_t row = table_lookup<W>(table, slots, load_key<W>(psi0_keys, (uint64_t)j));
         if (row < 0) continue;
         double2 a = psi0_amp[j], g = gbar[row];
         g.x += a.x * w.x - a.y * w.y;
@@ -303,10 +302,10 @@ int launch_adj_obs(const Bufs& b, int gen, const void* vec, const double* dLdP, 
     if (wC && b.n0 > 0) {
         int grid = (int)std::min<int64_t>((b.n0 + kAdjBlock - 1) / kAdjBlock, (int64_t)b.grid);
         switch (b.W) {
-        case 1: k_adj_obs_psi0<1><<<grid, kAdjBlock, 0, st>>>(b.table[gen], b.table_slots, b.div_exc, b.psi0_keys, b.psi0_amp, b.n0, wC, gbar); break;
-        case 2: k_adj_obs_psi0<2><<<grid, kAdjBlock, 0, st>>>(b.table[gen], b.table_slots, b.div_exc, b.psi0_keys, b.psi0_amp, b.n0, wC, gbar); break;
-        case 3: k_adj_obs_psi0<3><<<grid, kAdjBlock, 0, st>>>(b.table[gen], b.table_slots, b.div_exc, b.psi0_keys, b.psi0_amp, b.n0, wC, gbar); break;
-        case 4: k_adj_obs_psi0<4><<<grid, kAdjBlock, 0, st>>>(b.table[gen], b.table_slots, b.div_exc, b.psi0_keys, b.psi0_amp, b.n0, wC, gbar); break;
+        case 1: k_adj_obs_psi0<1><<<grid, kAdjBlock, 0, st>>>(b.table[gen], b.table_slots, b.psi0_keys, b.psi0_amp, b.n0, wC, gbar); break;
+        case 2: k_adj_obs_psi0<2><<<grid, kAdjBlock, 0, st>>>(b.table[gen], b.table_slots, b.psi0_keys, b.psi0_amp, b.n0, wC, gbar); break;
+        case 3: k_adj_obs_psi0<3><<<grid, kAdjBlock, 0, st>>>(b.table[gen], b.table_slots, b.psi0_keys, b.psi0_amp, b.n0, wC, gbar); break;
+        case 4: k_adj_obs_psi0<4><<<grid, kAdjBlock, 0, st>>>(b.table[gen], b.table_slots, b.psi0_keys, b.psi0_amp, b.n0, wC, gbar); break;
         default: return -1;
         }
         ++n;

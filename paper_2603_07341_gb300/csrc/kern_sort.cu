@@ -195,8 +195,7 @@ __global__ void __launch_bounds__(kBlock) k_trunc_place(Counters* ctr, const uin
                                                         const uint32_t* __restrict__ meta_in,
                                                         uint64_t* __restrict__ keys_out, double2* __restrict__ c_out,
                                                         uint32_t* __restrict__ meta_out, uint64_t* table_out,
-                                                        uint64_t slots, UDiv dexc, uint32_t* __restrict__ from,
-                                                        int step)
+                                                        uint64_t slots, uint32_t* __restrict__ from, int step)
 {
     if (ctr->err) return;
     const uint32_t n = ctr->kept;
@@ -207,7 +206,7 @@ __global__ void __launch_bounds__(kBlock) k_trunc_place(Counters* ctr, const uin
         c_out[dst] = c_in[src];
         meta_out[dst] = meta_in[src];
         if (from) from[dst] = src;
-        if (!table_insert_unique<W>(table_out, slots, dexc, k, dst)) set_err(ctr, kErrProbe, step, 1);
+        if (!table_insert_unique<W>(table_out, slots, k, dst)) set_err(ctr, kErrProbe, step, 1);
     }
 }
 
@@ -230,8 +229,7 @@ static int sorted_m(const Bufs& b, int gin, int gout, int step, cudaStream_t st)
         }
     }
     k_trunc_place<W><<<b.grid, kBlock, 0, st>>>(b.ctr, b.sortk[cur], b.sorti[cur], b.V[0], b.meta[gin], b.keys[gout],
-                                                 b.V[1], b.meta[gout], b.table[gout], b.table_slots, b.div_exc, b.from,
-                                                 step);
+                                                 b.V[1], b.meta[gout], b.table[gout], b.table_slots, b.from, step);
     return n + 1;
 }
 

@@ -23,11 +23,11 @@ namespace paces {
 // ---------------------------------------------------------------- insert rows
 template <int W>
 __global__ void k_insert_rows(const uint64_t* __restrict__ keys, uint32_t n, uint64_t* table, uint64_t slots,
-                              UDiv dexc, Counters* ctr)
+                              Counters* ctr)
 {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         Key<W> k = load_key<W>(keys, i);
-        if (!table_insert_unique<W>(table, slots, dexc, k, i)) set_err(ctr, kErrProbe, -1, 0);
+        if (!table_insert_unique<W>(table, slots, k, i)) set_err(ctr, kErrProbe, -1, 0);
     }
 }
 
@@ -117,10 +117,10 @@ __device__ __forceinline__ uint32_t insert_candidate(const DevModel* __restrict_
                                                      const uint32_t* __restrict__ meta, uint32_t lo, Counters* ctr,
                                                      int step, bool& resolved)
 {
-    const Place pl = key_place<W>(key, slots, M->div_exc);
-    const uint64_t fp = pl.fp;
+    uint64_t h = key_hash<W>(key);
+    uint64_t fp = fingerprint<W>(h);
     uint64_t mine = (fp << 32) | (uint64_t)(kCand | c);
-    uint64_t pos = pl.home;
+    uint64_t pos = slot_home(h, slots);
     resolved = false;
     for (uint32_t probe = 0; probe < kMaxProbe; ++probe) {
         uint64_t* sl = table + pos * Slot<W>::kWords;
@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(kBlock) k_level_scatter(const DevModel* __rest
             meta[row] = child_meta<W>(M, k, pm, mv);
             uint64_t* sl = table + (uint64_t)cand_slot[(uint64_t)p * D + mv] * Slot<W>::kWords;
             // the tag is rebuilt from the key's hash: a store, no read of the slot
-            const uint64_t tag = (key_fp<W>(child, M->div_exc) << 32) | (uint64_t)row;
+            const uint64_t tag = ((uint64_t)fingerprint<W>(key_hash<W>(child)) << 32) | (uint64_t)row;
             if constexpr (W == 1) {
                 *reinterpret_cast<ulonglong2*>(sl) = make_ulonglong2(tag, child.w[0]);
             } else {
@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(kBlock) k_level_scatter(const DevModel* __rest
             double2 a = make_double2(0.0, 0.0);
             int64_t orow = -1;
             if (old_table) {
-                orow = table_lookup<W>(old_table, old_slots, M->div_exc, child);
+                orow = table_lookup<W>(old_table, old_slots, child);
                 if (orow >= 0) a = c_old[orow];
             }
             c_new[row] = a;
@@ -461,7 +461,7 @@ __global__ void __launch_bounds__(kBlock) k_csr_grp(const DevModel* __restrict__
                         found = true;
                     }
                 } else {
-                    int64_t r = table_lookup<W>(table, slots, M->div_exc, child);
+                    int64_t r = table_lookup<W>(table, slots, child);
                     if (r >= 0) {
                         colv = (uint32_t)r;
                         found = true;
@@ -520,7 +520,7 @@ __global__ void __launch_bounds__(kBlock) k_csr(const DevModel* __restrict__ M, 
                 uint32_t sl = cand_slot[(uint64_t)i * D + mv];
                 if (sl != kNone) r = (sl & kCand) ? (sl & ~kCand) : (uint32_t)table[(uint64_t)sl * Slot<W>::kWords];
             } else {
-                r = table_lookup<W>(table, slots, M->div_exc, child);
+                r = table_lookup<W>(table, slots, child);
             }
             if (r < 0) continue;
             col[rbase + e] = (uint32_t)r;
@@ -769,7 +769,7 @@ __global__ void __launch_bounds__(kBlock) k_obs_finish_batch(const DevModel* __r
         double cr = 0.0, ci = 0.0;
         for (int64_t k = (int64_t)rz * per; k < (int64_t)(rz + 1) * per; ++k) {
             Key<W> key = load_key<W>(psi0_keys, (uint64_t)k);
-            int64_t r = table_lookup<W>(table, slots, M->div_exc, key);
+            int64_t r = table_lookup<W>(table, slots, key);
             if (r < 0) continue;
             double2 a = psi0_amp[k], c;
             if (M->fmt == 1) {
@@ -840,7 +840,7 @@ __global__ void __launch_bounds__(kBlock) k_obs_finish(const DevModel* __restric
     double acc[2] = {0.0, 0.0};
     for (int64_t k = threadIdx.x; k < n0; k += blockDim.x) {
         Key<W> key = load_key<W>(psi0_keys, (uint64_t)k);
-        int64_t r = table_lookup<W>(table, slots, M->div_exc, key);
+        int64_t r = table_lookup<W>(table, slots, key);
         if (r < 0) continue;
         double2 a = psi0_amp[k], c;
         if (M->fmt == 1) {
@@ -1023,7 +1023,7 @@ int launch_insert_rows(const Bufs& b, int gen, uint32_t n, cudaStream_t st)
 {
     int grid = b.grid;
     PACES_DISPATCH_W(b.W, (k_insert_rows<KW><<<grid, kBlock, 0, st>>>(b.keys[gen], n, b.table[gen], b.table_slots,
-                                                                       b.div_exc, b.ctr), 1))
+                                                                       b.ctr), 1))
 }
 
 int launch_truncate(const Bufs& b, int gin, int gout, double th2, int step, cudaStream_t st)

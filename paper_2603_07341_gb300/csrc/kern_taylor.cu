@@ -24,6 +24,8 @@ struct TaylorArgs {
     const uint8_t* cid;
     const uint8_t* cnt;
     const double* diag;
+    double* diag_h;          // FP64 variant: h times the diagonal, formed in the first term
+    const uint8_t* rperm;    // FP64 variant: rows of each 256-row window by entry count
     const double2* c_in;     // phi_0 = c'
     double2* r;              // accumulator (the new state)
     double2* ta;             // term buffers
@@ -138,14 +140,14 @@ __device__ __forceinline__ double2 row_apply(const uint32_t* __restrict__ col, c
     return make_double2(yr, yi);
 }
 
-// |v| 2^32 as an FP32 number, from the upper 32 bits of the FP64 v (20 bits of
-// significand, relative error below 2^-20) with integer operations only, so
-// that the stop test costs the FP64 pipe nothing.  |v| below 2^-158 gives 0 (or
-// a subnormal), |v| at or above 2^96 saturates.
-__device__ __forceinline__ float mag_scaled_f32(double v)
+// |v| 2^(32 - L) as an FP32 number, from the upper 32 bits of the FP64 v (20
+// bits of significand, relative error below 2^-20), with integer operations
+// only, so that the stop test costs the FP64 pipe nothing.  Results below
+// 2^-126 give 0 or a subnormal; results at or above 2^128 saturate near 2^128.
+__device__ __forceinline__ float mag_scaled_f32(double v, int L)
 {
     int h = __double2hiint(v) & 0x7FFFFFFF;
-    int e = (h >> 20) - (1023 - 127 - 32);
+    int e = (h >> 20) - (1023 - 127 - 32) - L;
     e = min(max(e, 0), 254);
     return __int_as_float((e << 23) | ((h & 0xFFFFF) << 3));
 }
@@ -163,22 +165,69 @@ __device__ __forceinline__ int series_count(const Counters* ctr, const TaylorPar
     return ns < 1.0 ? 1 : (int)ns;
 }
 
+// Rows of every 256-row window ordered by their entry count, largest first
+// (stable: equal counts keep row order): rperm[w + k] = offset in window w of
+// its k-th row.  The FP64 propagator gives each warp 32 consecutive ranks, so
+// the rows of a warp have (nearly) equal counts and no warp issues FP64
+// products for entries that only some of its rows have.  Deterministic, so
+// that replays repeat the reduction order bit for bit.
+__global__ void __launch_bounds__(kBlock) k_row_order(const Counters* __restrict__ ctr, const uint8_t* __restrict__ cnt,
+                                                      int pmax, uint8_t* __restrict__ rperm)
+{
+    __shared__ uint32_t off[kMaxMoves + 1][kBlock / 32];
+    if (ctr->err) return;
+    const uint32_t q = ctr->q;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint32_t wb = blockIdx.x * kBlock; wb < q; wb += gridDim.x * kBlock) {
+        const uint32_t row = wb + threadIdx.x;
+        const int c = row < q ? (int)cnt[row] : -1;
+        for (int k = 0; k <= pmax; ++k) {
+            const unsigned bal = __ballot_sync(0xffffffffu, c == k);
+            if (lane == 0) off[k][warp] = (uint32_t)__popc(bal);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {            // exclusive offsets: counts descending, then warps in order
+            uint32_t acc = 0;
+            for (int k = pmax; k >= 0; --k)
+                for (int w = 0; w < kBlock / 32; ++w) {
+                    const uint32_t v = off[k][w];
+                    off[k][w] = acc;
+                    acc += v;
+                }
+        }
+        __syncthreads();
+        const unsigned peers = __match_any_sync(0xffffffffu, c);       // rows past q match only each other
+        if (c >= 0) rperm[wb + off[c][warp] + __popc(peers & ((1u << lane) - 1u))] = (uint8_t)threadIdx.x;
+        __syncthreads();
+    }
+}
+
 // FP64 amplitudes.  The FP64 pipe of this part retires about two operations
-// per SM per clock, so the kernel spends FP64 operations only on the
-// amplitudes themselves: the factor h/n (h = dt / series) is folded into the
-// shared coefficient table and into one product with the diagonal, so a row of
-// c off-diagonal entries costs 2c + 5 FP64 operations (products, the diagonal,
-// r += phi_n).  The stop test compares ||phi_n||^2, summed in FP32 from the
-// leading 20 bits of every component, with tol^2 ||v||^2, v the input of the
-// series (||v|| in FP64 from its first term): the partial sum r_n differs from
-// v in norm by about ||phi_{n+1}||, far below the test's resolution when the
-// test is near to passing.  A term more or less changes r by at most tol ||v||.
+// per SM per clock, so the kernel spends FP64 operations on the amplitudes
+// only.  With B = h P H P (h = dt / series), the series is evaluated through
+// the unscaled powers psi_n = B psi_{n-1}, psi_0 = v (the series' input), and
+// r = sum_n (-i)^n / n! psi_n: B's off-diagonal entries live in a shared table
+// and its diagonal h d is formed once per step, so a row of c off-diagonal
+// entries costs 2c + 4 FP64 operations per term (the products, the diagonal,
+// and r += (-i)^n psi_n / n! as two FMAs).  ||psi_n|| <= (rho h)^n ||v|| stays
+// far inside the FP64 range for the series lengths substepping allows.
 //
-// A step of several series (substeps) copies the output of one series, held
-// in r, into a term buffer as the input of the next, so that r is updated in
-// place while that input is gathered.  Adjoint re-runs store, in order, the
-// terms phi_1.. of the first series, then for each later series its input and
-// its terms (16 bytes per row each).
+// Rows are taken in 256-row windows, one per block, in the order k_row_order
+// leaves (one lane per row), so that a warp's 32 rows have nearly equal entry
+// counts; models with more entries per row use LPR lanes per row in row order.
+//
+// The stop test compares ||phi_n||^2 = ||psi_n||^2 / n!^2, summed in FP32 from
+// the leading 20 bits of every component of psi_n (scaled by 2^-L, 2^L <= n!,
+// in the integer exponent field), with tol^2 ||v||^2 (||v|| in FP64 from the
+// first term): the partial sum r_n differs from v in norm by about
+// ||phi_{n+1}||, far below the test's resolution when the test is near to
+// passing.  A term more or less changes r by at most tol ||v||.
+//
+// A step of several series copies the output of one series, held in r, into
+// a term buffer as the input of the next, so that r is updated in place while
+// that input is gathered.  Adjoint re-runs store, in order, the terms
+// phi_1.. of the first series, then for each later series its input and its
+// terms (16 bytes per row each).
 template <int LPR>
 __global__ void __launch_bounds__(kBlock) k_taylor_f64(TaylorArgs a)
 {
@@ -196,7 +245,6 @@ __global__ void __launch_bounds__(kBlock) k_taylor_f64(TaylorArgs a)
     const uint32_t nwarps = (G * blockDim.x) >> 5;
     const int lane = (threadIdx.x & 31) % LPR;
     const uint32_t sub = (threadIdx.x & 31) / LPR;
-    const float kScale2 = 18446744073709551616.0f;          // 2^64 = (2^32)^2
 
     const int fixed = a.p.fixed_terms;
     const int nlimit = fixed > 0 ? fixed : a.p.nmax;
@@ -206,6 +254,8 @@ __global__ void __launch_bounds__(kBlock) k_taylor_f64(TaylorArgs a)
         return;
     }
     const double h = a.p.dt / (double)nsub;
+    for (int t = threadIdx.x; t < ncoef; t += blockDim.x) coef[t] = h * M->coef[t];
+    __syncthreads();
     double2* store = reinterpret_cast<double2*>(a.terms);
     double E = 0.0, n0 = 0.0;
     int total = 0, slot = 0, bar = 0;
@@ -229,40 +279,97 @@ __global__ void __launch_bounds__(kBlock) k_taylor_f64(TaylorArgs a)
             x = a.ta;
             y = a.tb;
         }
-        double nin = 0.0;
+        double nin = 0.0, cn = 1.0;                 // cn = 1 / n!
         int nd = 0;
         bool cj = fixed > 0;
         for (int n = 1; n <= nlimit; ++n) {
-            const double s = h / (double)n;
-            __syncthreads();
-            for (int t = threadIdx.x; t < ncoef; t += blockDim.x) coef[t] = s * M->coef[t];
-            __syncthreads();
+            cn = cn / (double)n;
+            const int L = -ilogb(cn);                // 2^(L-1) < n! <= 2^L
+            const double corr = ldexp(cn, L);        // 2^L / n!, in [1, 2)
+            // (-i)^n = s_re + i s_im with one of them +-1, the other 0
+            const int ph = n & 3;
+            const double sr = ph == 0 ? cn : (ph == 2 ? -cn : 0.0);
+            const double si = ph == 1 ? -cn : (ph == 3 ? cn : 0.0);
+            const bool first = (j == 0 && n == 1);
             float phi2 = 0.f;
             double acc_e = 0.0, acc_n = 0.0;
-            for (uint32_t rb = warp * RPW; rb < q; rb += nwarps * RPW) {
-                uint32_t row = rb + sub;
-                bool valid = row < q;
-                uint32_t c = valid ? a.cnt[row] : 0u;
-                uint64_t base = (uint64_t)row * P;
-                double2 yv = row_apply<LPR, double2>(a.col, a.cid, c, base, coef, x, lane);   // s (H x) off the diagonal
-                if (valid && lane == 0) {
-                    double2 xi = x[row];
-                    double d = s * a.diag[row];
-                    yv.x = fma(d, xi.x, yv.x);
-                    yv.y = fma(d, xi.y, yv.y);
-                    double2 phi = make_double2(yv.y, -yv.x);            // (-i) s H x
-                    y[row] = phi;
-                    if (store && slot < a.term_max) store[(size_t)slot * q + row] = phi;
-                    double2 rr = (n == 1) ? xi : a.r[row];
-                    rr.x += phi.x;
-                    rr.y += phi.y;
-                    a.r[row] = rr;
-                    float p0 = mag_scaled_f32(phi.x), p1 = mag_scaled_f32(phi.y);
-                    phi2 = __fmaf_rn(p0, p0, __fmaf_rn(p1, p1, phi2));
-                    if (n == 1) {
-                        acc_e = fma(xi.x, yv.x, fma(xi.y, yv.y, acc_e));     // Re(conj(v) h H v)
-                        acc_n = fma(xi.x, xi.x, fma(xi.y, xi.y, acc_n));
+            auto finish_row = [&](uint32_t row, double2 yv) {
+                double2 xi = x[row];
+                double d;
+                if (first) {
+                    d = h * a.diag[row];
+                    a.diag_h[row] = d;
+                } else {
+                    d = a.diag_h[row];
+                }
+                yv.x = fma(d, xi.x, yv.x);
+                yv.y = fma(d, xi.y, yv.y);                // psi_n = B x
+                y[row] = yv;
+                double2 rr = (n == 1) ? xi : a.r[row];
+                // r += (sr + i si) psi_n
+                rr.x = fma(sr, yv.x, fma(-si, yv.y, rr.x));
+                rr.y = fma(sr, yv.y, fma(si, yv.x, rr.y));
+                a.r[row] = rr;
+                if (store && slot < a.term_max)
+                    store[(size_t)slot * q + row] = make_double2(sr * yv.x - si * yv.y, sr * yv.y + si * yv.x);
+                float p0 = mag_scaled_f32(yv.x, L), p1 = mag_scaled_f32(yv.y, L);
+                phi2 = __fmaf_rn(p0, p0, __fmaf_rn(p1, p1, phi2));
+                if (n == 1) {
+                    acc_e = fma(xi.x, yv.x, fma(xi.y, yv.y, acc_e));     // Re(conj(v) h H v)
+                    acc_n = fma(xi.x, xi.x, fma(xi.y, xi.y, acc_n));
+                }
+            };
+            if constexpr (LPR == 1) {
+                // one 256-row window per block and round, rows by entry count
+                for (uint32_t wb = blockIdx.x * kBlock; wb < q; wb += G * kBlock) {
+                    const uint32_t sl = wb + threadIdx.x;
+                    const uint32_t row = sl < q ? wb + a.rperm[sl] : q;
+                    const bool valid = row < q;
+                    const uint32_t c = valid ? a.cnt[row] : 0u;
+                    double yr = 0.0, yi = 0.0;
+                    if (__any_sync(0xffffffffu, c > 0)) {
+                        const uint64_t base = (uint64_t)row * P;
+                        uint4 cc = make_uint4(0, 0, 0, 0);
+                        uint32_t ii = 0;
+                        if (valid) {
+                            cc = *reinterpret_cast<const uint4*>(a.col + base);
+                            ii = *reinterpret_cast<const uint32_t*>(a.cid + base);
+                        }
+                        const uint32_t cs[4] = {cc.x, cc.y, cc.z, cc.w};
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            if (__any_sync(0xffffffffu, c > (uint32_t)k) && c > (uint32_t)k) {
+                                const double av = coef[(ii >> (8 * k)) & 0xFFu];
+                                const double2 xv = x[cs[k]];
+                                yr = fma(av, xv.x, yr);
+                                yi = fma(av, xv.y, yi);
+                            }
+                        }
+                        for (uint32_t e = 4; e < c; e += 4) {      // pitches above 4 (P <= 8)
+                            const uint4 c2 = *reinterpret_cast<const uint4*>(a.col + base + e);
+                            const uint32_t i2 = *reinterpret_cast<const uint32_t*>(a.cid + base + e);
+                            const uint32_t cs2[4] = {c2.x, c2.y, c2.z, c2.w};
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) {
+                                if (e + k < c) {
+                                    const double av = coef[(i2 >> (8 * k)) & 0xFFu];
+                                    const double2 xv = x[cs2[k]];
+                                    yr = fma(av, xv.x, yr);
+                                    yi = fma(av, xv.y, yi);
+                                }
+                            }
+                        }
                     }
+                    if (valid) finish_row(row, make_double2(yr, yi));
+                }
+            } else {
+                for (uint32_t rb = warp * RPW; rb < q; rb += nwarps * RPW) {
+                    uint32_t row = rb + sub;
+                    bool valid = row < q;
+                    uint32_t c = valid ? a.cnt[row] : 0u;
+                    uint64_t base = (uint64_t)row * P;
+                    double2 yv = row_apply<LPR, double2>(a.col, a.cid, c, base, coef, x, lane);
+                    if (valid && lane == 0) finish_row(row, yv);
                 }
             }
             ++slot;
@@ -282,7 +389,8 @@ __global__ void __launch_bounds__(kBlock) k_taylor_f64(TaylorArgs a)
                     n0 = tsh[2];
                 }
             }
-            if (fixed <= 0 && n >= 2 && tsh[0] <= a.p.tol2 * nin * (double)kScale2) {
+            // sum f^2 = ||phi_n||^2 2^64 / corr^2
+            if (fixed <= 0 && n >= 2 && tsh[0] * corr * corr <= a.p.tol2 * nin * 18446744073709551616.0) {
                 cj = true;
                 break;
             }
@@ -795,6 +903,8 @@ int launch_taylor(const Bufs& b, const TaylorParams& p, cudaStream_t st)
     a.cid = b.cid;
     a.cnt = b.cnt;
     a.diag = b.diag;
+    a.diag_h = b.diag_h;
+    a.rperm = b.rperm;
     a.c_in = b.V[1];
     a.r = b.V[0];
     a.ta = b.V[2];
@@ -829,8 +939,13 @@ int launch_taylor(const Bufs& b, const TaylorParams& p, cudaStream_t st)
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    int n = 0;
+    if (p.fmt == 1 && p.lpr == 1) {          // rows of every window by entry count
+        k_row_order<<<b.grid, kBlock, 0, st>>>(b.ctr, b.cnt, b.P, b.rperm);
+        ++n;
+    }
     cudaError_t e = cudaLaunchKernelExC(&cfg, fn, args);
-    return e == cudaSuccess ? 1 : -1;
+    return e == cudaSuccess ? n + 1 : -1;
 }
 
 int launch_barrier_selftest(Counters* ctr, double* part, int grid, unsigned expect, unsigned long long timeout_ns,

@@ -129,7 +129,6 @@ extern "C" paces_status paces_expand_noalloc(const paces_params* params, const u
     b.meta[0] = (uint32_t*)carve((size_t)rows * 4);
     b.keys[0] = keys_out;
     b.table_slots = slots;
-    b.div_exc = M->div_exc;
     b.cap_rows = (uint32_t)rows;
     b.cand_cap = (uint64_t)n_in * D;
     b.W = W;

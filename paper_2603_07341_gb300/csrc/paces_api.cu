@@ -321,6 +321,13 @@ paces_status alloc_rows(paces_t h, uint32_t cap, std::vector<DevAlloc>& out, Buf
     chk(b.cid = alloc_track<uint8_t>(h, h->row_allocs, (size_t)cap * h->P));
     chk(b.cnt = alloc_track<uint8_t>(h, h->row_allocs, cap));
     chk(b.diag = alloc_track<double>(h, h->row_allocs, cap));
+    if (h->prm.precision == PACES_C128) {
+        chk(b.diag_h = alloc_track<double>(h, h->row_allocs, cap));
+        chk(b.rperm = alloc_track<uint8_t>(h, h->row_allocs, (size_t)cap + kBlock));
+    } else {
+        b.diag_h = nullptr;
+        b.rperm = nullptr;
+    }
     chk(b.cand_slot = alloc_track<uint32_t>(h, h->row_allocs, (size_t)cap * h->D));
     // sort of the kept set: indices in the winner-mask buffer (free during
     // truncation); keys in the two term buffers when a key fits in 16 bytes
@@ -896,7 +903,6 @@ paces_status paces_create(const paces_params* params, const paces_allocator* all
     }
 
     b.model = alloc_track<DevModel>(h, h->fixed_allocs, 1);
-    b.div_exc = M->div_exc;
     b.ctr = alloc_track<Counters>(h, h->fixed_allocs, 1);
     b.topq = alloc_track<TopqState>(h, h->fixed_allocs, 1);
     b.rs_hist = alloc_track<uint32_t>(h, h->fixed_allocs, 256 * (size_t)kMaxChunkBlocks + 256);

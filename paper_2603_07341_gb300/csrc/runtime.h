@@ -46,13 +46,14 @@ struct Bufs {
     uint32_t* meta[2];             // row -> (site, phonons at site, total phonons)
     uint64_t* table[2];            // hash tables, two generations
     uint64_t table_slots;          // slots per table (below 2^32)
-    UDiv div_exc;                  // key word 0 / exciton radix (table placement)
     double2* V[4];                 // V0: state / accumulator r, V1: c' (phi_0), V2, V3: terms
     float2* F[2];                  // complex64 term buffers (C64_SPMV)
     uint32_t* col;                 // P H P columns, row pitch P
     uint8_t* cid;                  // coefficient ids, row pitch P
     uint8_t* cnt;                  // entries per row
     double* diag;                  // diagonal per row
+    double* diag_h;                // FP64 propagator: h times the diagonal (h = dt / series)
+    uint8_t* rperm;                // FP64 propagator: rows of each 256-row window by entry count
     uint32_t* cand_slot;           // candidate -> table slot, kCand | row (an existing row), or kNone
     uint32_t* from;                // adjoint re-runs: row -> row of the previous state (or kNone)
     uint64_t* sortk[2];            // sort of the kept set: keys (ping-pong)
