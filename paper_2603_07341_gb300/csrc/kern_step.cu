@@ -101,9 +101,35 @@ __global__ void __launch_bounds__(1024) k_scan(const uint32_t* __restrict__ blk_
 }
 
 // ---------------------------------------------------------------- a2/a3 one level
-// One thread per candidate c = (parent p - lo) * D + move: the parents of a
-// level are the frontier rows [lo, hi); every candidate is inserted
-// independently, so a warp keeps 32 probe sequences in flight.
+// Candidate c = (parent p - lo) * D + move: the parents of a level are the
+// frontier rows [lo, hi); every candidate is inserted independently.  Each
+// thread takes kCPT candidates at once and issues their parent loads, moves
+// and home-slot loads before resolving any of them, so that a warp keeps
+// 32 kCPT probe sequences in flight instead of waiting on one dependent
+// chain (parent, move, hash, DRAM probe, atomic) at a time.
+//
+// The home slot of a key and its contents, loaded ahead of the probe loop.
+struct Probe {
+    uint64_t pos, fp, tag, kw;
+};
+
+template <int W>
+__device__ __forceinline__ void probe_start(const uint64_t* table, uint64_t slots, const Key<W>& key, Probe& pr)
+{
+    const uint64_t h = key_hash<W>(key);
+    pr.fp = fingerprint<W>(h);
+    pr.pos = slot_home(h, slots);
+    const uint64_t* sl = table + pr.pos * Slot<W>::kWords;
+    if constexpr (W == 1) {
+        ulonglong2 s2 = __ldcg(reinterpret_cast<const ulonglong2*>(sl));
+        pr.tag = s2.x;
+        pr.kw = s2.y;
+    } else {
+        pr.tag = __ldcg(sl);
+        pr.kw = kEmpty;
+    }
+}
+
 //
 // Insert a candidate.  Returns the slot that holds its key afterwards: a slot
 // it claimed, a candidate entry with the same key it joined (the lowest
@@ -115,12 +141,11 @@ template <int W>
 __device__ __forceinline__ uint32_t insert_candidate(const DevModel* __restrict__ M, uint64_t* table, uint64_t slots,
                                                      const Key<W>& key, uint32_t c, const uint64_t* __restrict__ keys,
                                                      const uint32_t* __restrict__ meta, uint32_t lo, Counters* ctr,
-                                                     int step, bool& resolved)
+                                                     int step, const Probe& pr, bool& resolved)
 {
-    uint64_t h = key_hash<W>(key);
-    uint64_t fp = fingerprint<W>(h);
+    const uint64_t fp = pr.fp;
     uint64_t mine = (fp << 32) | (uint64_t)(kCand | c);
-    uint64_t pos = slot_home(h, slots);
+    uint64_t pos = pr.pos;
     resolved = false;
     for (uint32_t probe = 0; probe < kMaxProbe; ++probe) {
         uint64_t* sl = table + pos * Slot<W>::kWords;
@@ -128,7 +153,8 @@ __device__ __forceinline__ uint32_t insert_candidate(const DevModel* __restrict_
         if constexpr (W == 1) {
             // a one-word slot is claimed with its key in one 16-byte atomic, so
             // a later candidate of the same key compares the key in the slot
-            ulonglong2 s2 = __ldcg(reinterpret_cast<const ulonglong2*>(sl));
+            ulonglong2 s2 = probe == 0 ? make_ulonglong2(pr.tag, pr.kw)
+                                       : __ldcg(reinterpret_cast<const ulonglong2*>(sl));
             tag = s2.x;
             kw = s2.y;
             if (tag == kEmpty) {
@@ -139,7 +165,7 @@ __device__ __forceinline__ uint32_t insert_candidate(const DevModel* __restrict_
                 kw = ohi;
             }
         } else {
-            tag = __ldcg(sl);
+            tag = probe == 0 ? pr.tag : __ldcg(sl);
             if (tag == kEmpty) {
                 unsigned long long old = atomicCAS((unsigned long long*)sl, kEmpty, mine);
                 if (old == kEmpty) return (uint32_t)pos;
@@ -182,6 +208,40 @@ __device__ __forceinline__ uint32_t insert_candidate(const DevModel* __restrict_
     return kNone;
 }
 
+// Read-only lookup continuing from a loaded home slot: row of key or -1.
+template <int W>
+__device__ __forceinline__ int64_t lookup_from(const uint64_t* __restrict__ table, uint64_t slots, const Key<W>& key,
+                                               const Probe& pr)
+{
+    uint64_t pos = pr.pos;
+    for (uint32_t probe = 0; probe < kMaxProbe; ++probe) {
+        const uint64_t* sl = table + pos * Slot<W>::kWords;
+        uint64_t tag, kw;
+        if constexpr (W == 1) {
+            ulonglong2 s2 = probe == 0 ? make_ulonglong2(pr.tag, pr.kw) : __ldcg(reinterpret_cast<const ulonglong2*>(sl));
+            tag = s2.x;
+            kw = s2.y;
+        } else {
+            tag = probe == 0 ? pr.tag : __ldcg(sl);
+            kw = kEmpty;
+        }
+        if (tag == kEmpty) return -1;
+        if ((tag >> 32) == pr.fp) {
+            bool eq;
+            if constexpr (W == 1) {
+                eq = kw == key.w[0];
+            } else {
+                eq = true;
+#pragma unroll
+                for (int i = 0; i < W; ++i) eq &= (__ldcg(sl + 1 + i) == key.w[i]);
+            }
+            if (eq) return (int64_t)(uint32_t)tag;
+        }
+        pos = slot_next(pos, slots);
+    }
+    return -1;
+}
+
 // Candidate c of the level whose frontier starts at row lo: parent row and move.
 __device__ __forceinline__ void cand_parent(const DevModel* __restrict__ M, uint32_t c, uint32_t lo, uint32_t& p,
                                             int& mv)
@@ -206,19 +266,40 @@ __global__ void __launch_bounds__(kBlock) k_level_insert(const DevModel* __restr
         if (blockIdx.x == 0 && threadIdx.x == 0) set_err(ctr, kErrCand, step, f);
         return;
     }
-    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < (uint32_t)ncand; c += gridDim.x * blockDim.x) {
-        uint32_t p;
-        int mv;
-        cand_parent(M, c, lo, p, mv);
-        Key<W> k = load_key<W>(keys, p);
-        uint32_t pm = meta[p];
-        Key<W> child;
-        int cid;
-        uint32_t r = kNone;
-        bool res = false;
-        if (apply_move<W>(M, k, meta_s(pm), meta_ns(pm), mv, child, cid))
-            r = insert_candidate<W>(M, table, slots, child, c, keys, meta, lo, ctr, step, res);
-        cand_slot[(uint64_t)p * D + mv] = res ? (kCand | r) : r;
+    constexpr int kCPT = W == 1 ? 4 : 2;
+    const uint32_t nc = (uint32_t)ncand, stride = gridDim.x * blockDim.x;
+    for (uint32_t c0 = blockIdx.x * blockDim.x + threadIdx.x; c0 < nc; c0 += stride * kCPT) {
+        Key<W> child[kCPT];
+        Probe pb[kCPT];
+        uint32_t pp[kCPT];
+        int mvv[kCPT];
+        bool ok[kCPT];
+#pragma unroll
+        for (int k = 0; k < kCPT; ++k) {        // parents and moves
+            const uint32_t c = c0 + (uint32_t)k * stride;
+            ok[k] = false;
+            pp[k] = 0;
+            mvv[k] = 0;
+            if (c < nc) {
+                cand_parent(M, c, lo, pp[k], mvv[k]);
+                const Key<W> pk = load_key<W>(keys, pp[k]);
+                const uint32_t pm = meta[pp[k]];
+                int cid;
+                ok[k] = apply_move<W>(M, pk, meta_s(pm), meta_ns(pm), mvv[k], child[k], cid);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kCPT; ++k)          // every home slot in flight at once
+            if (ok[k]) probe_start<W>(table, slots, child[k], pb[k]);
+#pragma unroll
+        for (int k = 0; k < kCPT; ++k) {
+            const uint32_t c = c0 + (uint32_t)k * stride;
+            if (c >= nc) continue;
+            uint32_t r = kNone;
+            bool res = false;
+            if (ok[k]) r = insert_candidate<W>(M, table, slots, child[k], c, keys, meta, lo, ctr, step, pb[k], res);
+            cand_slot[(uint64_t)pp[k] * D + mvv[k]] = res ? (kCand | r) : r;
+        }
     }
 }
 
@@ -255,16 +336,13 @@ __global__ void __launch_bounds__(kBlock) k_level_flags(const DevModel* __restri
     if (threadIdx.x == 0) blk_cnt[blockIdx.x] = tot;
 }
 
-// New rows in candidate order: key, table slot (key words + row), rescued amplitude.
+// New rows in candidate order: key, descriptor, table slot (key words + row).
 template <int W>
 __global__ void __launch_bounds__(kBlock) k_level_scatter(const DevModel* __restrict__ M, Counters* ctr, int f,
                                                           uint64_t* keys, uint32_t* meta, uint64_t* table,
                                                           const uint32_t* __restrict__ cand_slot,
                                                           const uint32_t* __restrict__ wmask,
-                                                          const uint32_t* __restrict__ blk_off,
-                                                          const uint64_t* __restrict__ old_table, uint64_t old_slots,
-                                                          const double2* __restrict__ c_old, double2* __restrict__ c_new,
-                                                          uint32_t* __restrict__ from)
+                                                          const uint32_t* __restrict__ blk_off)
 {
     if (ctr->err) return;
     uint32_t lo0 = ctr->level_off[f], base_row = ctr->level_off[f + 1];
@@ -301,16 +379,55 @@ __global__ void __launch_bounds__(kBlock) k_level_scatter(const DevModel* __rest
                 for (int w = 0; w < W; ++w) sl[1 + w] = child.w[w];
                 sl[0] = tag;
             }
-            double2 a = make_double2(0.0, 0.0);
-            int64_t orow = -1;
-            if (old_table) {
-                orow = table_lookup<W>(old_table, old_slots, child);
-                if (orow >= 0) a = c_old[orow];
-            }
-            c_new[row] = a;
-            if (from) from[row] = orow >= 0 ? (uint32_t)orow : kNone;
         }
         run += tot;
+    }
+}
+
+// Rescue (post-adaptation detruncation, Sec. 3.3) of the rows a level added:
+// each takes its amplitude from the previous step's table when its key was a
+// row there, else 0 (also 0 with no previous table).  Dense over the new rows;
+// each thread takes kRPT rows and issues their home-slot loads, then their
+// amplitude gathers, together.
+template <int W>
+__global__ void __launch_bounds__(kBlock) k_level_rescue(const Counters* __restrict__ ctr, int f,
+                                                         const uint64_t* __restrict__ keys,
+                                                         const uint64_t* __restrict__ old_table, uint64_t old_slots,
+                                                         const double2* __restrict__ c_old, double2* __restrict__ c_new,
+                                                         uint32_t* __restrict__ from)
+{
+    if (ctr->err) return;
+    constexpr int kRPT = W == 1 ? 4 : 2;
+    const uint32_t lo = ctr->level_off[f + 1], hi = ctr->level_off[f + 2];
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t r0 = lo + blockIdx.x * blockDim.x + threadIdx.x; r0 < hi; r0 += stride * kRPT) {
+        Key<W> key[kRPT];
+        Probe pb[kRPT];
+        int64_t orow[kRPT];
+#pragma unroll
+        for (int k = 0; k < kRPT; ++k) {
+            const uint32_t row = r0 + (uint32_t)k * stride;
+            orow[k] = -1;
+            if (row < hi) {
+                key[k] = load_key<W>(keys, row);
+                if (old_table) probe_start<W>(old_table, old_slots, key[k], pb[k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kRPT; ++k) {
+            const uint32_t row = r0 + (uint32_t)k * stride;
+            if (row < hi && old_table) orow[k] = lookup_from<W>(old_table, old_slots, key[k], pb[k]);
+        }
+        double2 a[kRPT];
+#pragma unroll
+        for (int k = 0; k < kRPT; ++k) a[k] = orow[k] >= 0 ? c_old[orow[k]] : make_double2(0.0, 0.0);
+#pragma unroll
+        for (int k = 0; k < kRPT; ++k) {
+            const uint32_t row = r0 + (uint32_t)k * stride;
+            if (row >= hi) continue;
+            c_new[row] = a[k];
+            if (from) from[row] = orow[k] >= 0 ? (uint32_t)orow[k] : kNone;
+        }
     }
 }
 
@@ -960,10 +1077,9 @@ static int level_w(const Bufs& b, int gen, int f, int rescue_gen, int step, cuda
     k_scan<<<1, 1024, 0, st>>>(b.blk_cnt, b.blk_off, b.G, b.ctr, kScanLevel, f, b.cap_rows, step);
     const uint64_t* ot = rescue_gen >= 0 ? b.table[rescue_gen] : nullptr;
     k_level_scatter<W><<<b.G, kBlock, 0, st>>>(b.model, b.ctr, f, b.keys[gen], b.meta[gen], b.table[gen],
-                                               b.cand_slot,
-                                               reinterpret_cast<const uint32_t*>(b.masks), b.blk_off, ot,
-                                               b.table_slots, b.V[0], b.V[1], b.from);
-    return 4;
+                                               b.cand_slot, reinterpret_cast<const uint32_t*>(b.masks), b.blk_off);
+    k_level_rescue<W><<<b.grid, kBlock, 0, st>>>(b.ctr, f, b.keys[gen], ot, b.table_slots, b.V[0], b.V[1], b.from);
+    return 5;
 }
 
 template <int W>
