@@ -26,7 +26,7 @@ ST_NAMES = ("norm", "norm_phi0", "energy", "C_re", "C_im", "rows", "kept", "nnz"
             "terms", "norm_before", "time", "substeps", "hbound")
 
 
-MUTANTS = ("NO_RESCUE", "OPEN3D_AXES", "ENERGY_CONJ")
+MUTANTS = ("NO_RESCUE", "OPEN3D_AXES", "ENERGY_CONJ", "LANCZOS_NO_BETA")
 
 
 def build_oracle(force: bool = False, mutant: str | None = None) -> str:
@@ -63,6 +63,8 @@ def _load(mutant=None):
                                   ip, C.c_int, C.c_int, C.c_double, C.c_int, C.c_int]
         lib.or_destroy.argtypes = [P]
         lib.or_set_xmax.argtypes = [P, C.c_double]
+        lib.or_set_propagator.argtypes = [P, C.c_int, C.c_int]
+        lib.or_last_krylov.argtypes = [P, dp, C.c_int]
         lib.or_get_hopping.argtypes = [P, dp]
         lib.or_set_state.argtypes = [P, C.c_int, ip, ip, dp]
         lib.or_load_state.argtypes = [P, C.c_int, ip, ip, dp]
@@ -108,13 +110,16 @@ class Oracle:
     J / r^3).  ``m`` and ``m_init`` are the neighbour orders of Eq. H_eff
     (``m_init < 0``: closure).  ``xmax`` bounds rho dt / s, the length of each
     of the s Taylor series a step is split into (rho: largest absolute row sum
-    of H over H_eff; ``xmax <= 0``: one series).  ``mutant`` (pin tests only) selects a build
-    with one planted mistake, see ``MUTANTS``.
+    of H over H_eff; ``xmax <= 0``: one series).  ``propagator`` 0 is the Taylor series
+    (App. C.1), 1 the Lanczos decomposition (App. C.3) with at most ``kmax`` Krylov
+    vectors per series.  ``mutant`` (pin tests only) selects a build with one planted
+    mistake, see ``MUTANTS``.
     """
 
     def __init__(self, n_sites, lattice_kind=0, dims=(0, 0, 0), coupling_kind=0, J=1.0,
                  eps=None, omega=None, g=None, cap=None, m=2, m_init=10, tol=1e-15,
-                 nmax=200, fixed_terms=0, J_explicit=None, xmax=8.0, mutant=None):
+                 nmax=200, fixed_terms=0, J_explicit=None, xmax=8.0, propagator=0, kmax=30,
+                 mutant=None):
         lib = _load(mutant)
         self.N = int(n_sites)
         N = self.N
@@ -133,12 +138,24 @@ class Oracle:
             raise OracleError(OR_INVALID, "or_create")
         self._lib = lib
         lib.or_set_xmax(self._h, float(xmax))
+        rc = lib.or_set_propagator(self._h, int(propagator), int(kmax))
+        if rc:
+            raise OracleError(rc, "or_set_propagator")
 
     def __del__(self):
         h = getattr(self, "_h", None)
         if h:
             self._lib.or_destroy(h)
             self._h = None
+
+    def krylov_basis(self):
+        """Lanczos vectors v_1..v_n of the last series of the last Lanczos step, [q, n]."""
+        n = self._lib.or_last_krylov(self._h, None, 0)
+        q = self.nrows()
+        buf = np.zeros(2 * q * max(n, 1))
+        self._lib.or_last_krylov(self._h, _dp(buf), n)
+        v = buf[0::2] + 1j * buf[1::2]
+        return v[: q * n].reshape(n, q).T.copy()
 
     def hopping(self):
         out = np.zeros((self.N, self.N))

@@ -29,10 +29,14 @@
  * Representation: a basis state is the int tuple (s, n_0, ..., n_{N-1}); rows
  * of H_eff are stored in order in a growable array with a linear-probing index.
  *
+ * Propagators: the Taylor series of App. C.1 (default) or the Lanczos
+ * decomposition of App. C.3 (or_set_propagator), with the same substep split.
+ *
  * Planted mistakes: the pin tests compile this file a second time with one of
- * the macros OR_MUTANT_NO_RESCUE, OR_MUTANT_OPEN3D_AXES or OR_MUTANT_ENERGY_CONJ
- * defined, each a plausible slip in one function, and check that the pin of
- * that function fails.  The default build defines none of them.
+ * the macros OR_MUTANT_NO_RESCUE, OR_MUTANT_OPEN3D_AXES, OR_MUTANT_ENERGY_CONJ
+ * or OR_MUTANT_LANCZOS_NO_BETA defined, each a plausible slip in one function,
+ * and check that the pin of that function fails.  The default build defines
+ * none of them.
  */
 #include "paces_oracle.h"
 
@@ -159,6 +163,10 @@ struct oracle {
     double tol;
     int nmax, fixed_terms;
     double xmax;         /* substepping: series length bound rho dt / s <= xmax */
+    int prop;            /* propagator: 0 Taylor series, 1 Lanczos (App. C.3)  */
+    int kmax;            /* Lanczos: largest Krylov dimension                  */
+    cplx* kry;           /* Lanczos basis v_1..v_n of the last series, q each  */
+    int kry_n, kry_q;
 
     rowset rows;         /* current H_eff                         */
     cplx* c;             /* amplitudes on rows                    */
@@ -261,6 +269,8 @@ oracle_t* or_create(int n_sites, int lattice_kind, const int* dims, int coupling
     o->nmax = nmax;
     o->fixed_terms = fixed_terms;
     o->xmax = 8.0;
+    o->prop = 0;
+    o->kmax = 30;
     rs_init(&o->rows, o->len);
     rs_init(&o->init, o->len);
     o->lvlcap = 64;
@@ -272,6 +282,15 @@ int or_set_xmax(oracle_t* o, double xmax)
 {
     if (!o) return OR_INVALID;
     o->xmax = xmax;
+    return OR_OK;
+}
+
+int or_set_propagator(oracle_t* o, int kind, int kmax)
+{
+    if (!o || kind < 0 || kind > 1 || (kind == 1 && (kmax < 1 || kmax > OR_MAX_KRYLOV))) return OR_INVALID;
+    if (kind == 1 && o->recording) return OR_INVALID;
+    o->prop = kind;
+    if (kind == 1) o->kmax = kmax;
     return OR_OK;
 }
 
@@ -297,6 +316,7 @@ void or_destroy(oracle_t* o)
     free(o->c); free(o->c0); free(o->lvl); free(o->keep);
     free(o->hp_off); free(o->hp_col); free(o->hp_val); free(o->hp_dJ); free(o->hp_dg);
     free(o->diag);
+    free(o->kry);
     free(o->last_from);
     free_recs(o);
     free(o);
@@ -635,6 +655,154 @@ static int taylor(oracle_t* o, double dt, int nsub, cplx* c, int* sub_terms, int
     return converged ? OR_OK : OR_NOCONVERGE;
 }
 
+/* ------------------------------------------------------------------ Lanczos */
+
+/* Eigen-decomposition of the real symmetric n x n matrix A (row-major, n <=
+ * OR_MAX_KRYLOV) by cyclic Jacobi rotations: on return the diagonal of A holds
+ * the eigenvalues and column k of Q (row-major) the eigenvector of A[k][k]. */
+static void jacobi_eigen(double* A, double* Q, int n)
+{
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) Q[i * n + j] = (i == j) ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+                tot += A[i * n + j] * A[i * n + j];
+                if (i != j) off += A[i * n + j] * A[i * n + j];
+            }
+        if (off <= 1e-34 * tot || off == 0.0) break;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                double apq = A[p * n + q];
+                if (apq == 0.0) continue;
+                /* rotation angle that zeroes A[p][q] */
+                double theta = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
+                double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+                for (int k = 0; k < n; ++k) {          /* A <- A G (columns p, q) */
+                    double akp = A[k * n + p], akq = A[k * n + q];
+                    A[k * n + p] = c * akp - sn * akq;
+                    A[k * n + q] = sn * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) {          /* A <- G^T A (rows p, q) */
+                    double apk = A[p * n + k], aqk = A[q * n + k];
+                    A[p * n + k] = c * apk - sn * aqk;
+                    A[q * n + k] = sn * apk + c * aqk;
+                }
+                for (int k = 0; k < n; ++k) {          /* Q <- Q G */
+                    double qkp = Q[k * n + p], qkq = Q[k * n + q];
+                    Q[k * n + p] = c * qkp - sn * qkq;
+                    Q[k * n + q] = sn * qkp + c * qkq;
+                }
+            }
+    }
+}
+
+/* y = exp(-i h T) e_1 for the n x n symmetric tridiagonal T with diagonal
+ * alpha[0..n-1] and off-diagonal beta[0..n-2], through T = Q diag(lambda) Q^T. */
+static void tridiag_exp_e1(const double* alpha, const double* beta, int n, double h, cplx* y)
+{
+    double A[OR_MAX_KRYLOV * OR_MAX_KRYLOV], Q[OR_MAX_KRYLOV * OR_MAX_KRYLOV];
+    for (int i = 0; i < n * n; ++i) A[i] = 0.0;
+    for (int i = 0; i < n; ++i) {
+        A[i * n + i] = alpha[i];
+        if (i + 1 < n) A[i * n + i + 1] = A[(i + 1) * n + i] = beta[i];
+    }
+    jacobi_eigen(A, Q, n);
+    for (int i = 0; i < n; ++i) {
+        cplx acc = 0.0;
+        for (int k = 0; k < n; ++k) acc += Q[i * n + k] * cexp(-I * h * A[k * n + k]) * Q[0 * n + k];
+        y[i] = acc;
+    }
+}
+
+/* c <- exp(-i dt H_P) c by the Lanczos decomposition of App. C.3,
+ * exp(-i h H) v ~ V_n exp(-i h T_n) V_n^dag v = beta_0 V_n exp(-i h T_n) e_1,
+ * as nsub successive decompositions of length h = dt / nsub.  The three-term
+ * recurrence: v_1 = v / beta_0 (beta_0 = ||v||); for j = 1, 2, ..:
+ * w = H v_j, alpha_j = <v_j|w>, w -= alpha_j v_j + beta_{j-1} v_{j-1},
+ * beta_j = ||w||, v_{j+1} = w / beta_j.  It stops at the first j whose error
+ * estimate h beta_j |(exp(-i h T_j) e_1)_j| (the norm of the residual of the
+ * Krylov solution, relative to ||v||, times h) is <= tol, and fails past
+ * kmax vectors.  sub_terms[j]: the dimension n of series j (= applications of
+ * H); energy = <c|H_P|c> of the input = beta_0^2 alpha_1.  The basis of the
+ * last series stays in o->kry. */
+static int lanczos(oracle_t* o, double dt, int nsub, cplx* c, int* sub_terms, int* nterms_out, double* energy)
+{
+    int q = o->hp_rows, K = o->kmax;
+    free(o->kry);
+    o->kry = (cplx*)malloc(sizeof(cplx) * ((size_t)q * (size_t)(K + 1) + 1));
+    cplx* w = (cplx*)malloc(sizeof(cplx) * ((size_t)q + 1));
+    if (!o->kry || !w) { free(w); return OR_NOMEM; }
+    double h = dt / (double)nsub;
+    double alpha[OR_MAX_KRYLOV], beta[OR_MAX_KRYLOV + 1];
+    cplx y[OR_MAX_KRYLOV];
+    int converged = 1, total = 0;
+    *energy = 0.0;
+    o->kry_n = 0;
+    o->kry_q = q;
+    for (int js = 0; js < nsub && converged; ++js) {
+        double b0 = sqrt(norm2(c, q));
+        if (b0 == 0.0) {              /* zero vector: exp(..) 0 = 0 */
+            if (sub_terms) sub_terms[js] = 0;
+            o->kry_n = 0;
+            continue;
+        }
+        cplx* V = o->kry;
+        for (int i = 0; i < q; ++i) V[i] = c[i] / b0;
+        int n = 0, done = 0;
+        for (int j = 1; j <= K; ++j) {
+            cplx* vj = V + (size_t)(j - 1) * q;
+            apply_h(o, vj, w);
+            double a = 0.0;
+            for (int i = 0; i < q; ++i) a += creal(conj(vj[i]) * w[i]);
+            alpha[j - 1] = a;
+            if (js == 0 && j == 1) *energy = b0 * b0 * a;
+            for (int i = 0; i < q; ++i) {
+                w[i] -= a * vj[i];
+#ifndef OR_MUTANT_LANCZOS_NO_BETA
+                if (j > 1) w[i] -= beta[j - 1] * V[(size_t)(j - 2) * q + i];
+#endif
+            }
+            double bj = sqrt(norm2(w, q));
+            beta[j] = bj;
+            /* T_j: diagonal alpha_1..alpha_j, off-diagonal beta_1..beta_{j-1} */
+            tridiag_exp_e1(alpha, beta + 1, j, h, y);
+            n = j;
+            if (h * bj * cabs(y[j - 1]) <= o->tol) { done = 1; break; }
+            if (j < K)
+                for (int i = 0; i < q; ++i) V[(size_t)j * q + i] = w[i] / bj;
+        }
+        if (!done) { converged = 0; n = K; }
+        if (sub_terms) sub_terms[js] = n;
+        total += n;
+        o->kry_n = n;
+        if (done)
+            for (int i = 0; i < q; ++i) {
+                cplx acc = 0.0;
+                for (int k = 0; k < n; ++k) acc += y[k] * V[(size_t)k * q + i];
+                c[i] = b0 * acc;
+            }
+    }
+    free(w);
+    *nterms_out = total;
+    return converged ? OR_OK : OR_NOCONVERGE;
+}
+
+int or_last_krylov(const oracle_t* o, double* V, int max_vectors)
+{
+    if (!o || !o->kry) return 0;
+    int n = o->kry_n < max_vectors ? o->kry_n : max_vectors;
+    if (V)
+        for (int k = 0; k < n; ++k)
+            for (int i = 0; i < o->kry_q; ++i) {
+                V[2 * ((size_t)k * o->kry_q + i)] = creal(o->kry[(size_t)k * o->kry_q + i]);
+                V[2 * ((size_t)k * o->kry_q + i) + 1] = cimag(o->kry[(size_t)k * o->kry_q + i]);
+            }
+    return o->kry_n;
+}
+
 static void observe(oracle_t* o)
 {
     int q = o->rows.nrows;
@@ -685,6 +853,7 @@ int or_step(oracle_t* o, double dt, double theta, const unsigned char* keep_over
             int keep_len)
 {
     if (!o || (o->rows.nrows == 0 && !o->fresh)) return OR_STATE;
+    if (o->prop == 1 && o->recording) return OR_INVALID;
     int len = o->len;
     int q_old = o->rows.nrows;
     double norm_before = norm2(o->c, q_old);
@@ -761,7 +930,9 @@ int or_step(oracle_t* o, double dt, double theta, const unsigned char* keep_over
     int nsub = substeps(o, dt, &rho);
     int* sub_terms = (int*)calloc((size_t)(nsub > 0 ? nsub : 1), sizeof(int));
     if (!sub_terms) return OR_NOMEM;
-    int rc = nsub > 0 ? taylor(o, dt, nsub, o->c, sub_terms, &nterms, &energy) : OR_NOCONVERGE;
+    int rc = nsub <= 0 ? OR_NOCONVERGE
+           : o->prop == 1 ? lanczos(o, dt, nsub, o->c, sub_terms, &nterms, &energy)
+                          : taylor(o, dt, nsub, o->c, sub_terms, &nterms, &energy);
     if (o->recording) {
         o->rec[o->nrec - 1].nterms = nterms;
         o->rec[o->nrec - 1].nsub = nsub;

@@ -41,6 +41,17 @@ void or_destroy(oracle_t* o);
  * paces_oracle.c).  xmax <= 0: always one series.  Default 8. */
 int or_set_xmax(oracle_t* o, double xmax);
 
+/* Propagator of a step: kind 0 the Taylor series of App. C.1 (default), kind 1
+ * the Lanczos decomposition of App. C.3 with at most kmax Krylov vectors per
+ * series (1 <= kmax <= OR_MAX_KRYLOV); the same substep split applies to both.
+ * Lanczos steps cannot be recorded for the adjoint (OR_INVALID). */
+#define OR_MAX_KRYLOV 64
+int or_set_propagator(oracle_t* o, int kind, int kmax);
+/* Orthonormal Lanczos vectors v_1..v_n of the last series of the last Lanczos
+ * step: fills V[2*q*k + 2*i + {0,1}] (re, im of row i of v_{k+1}) for k <
+ * max_vectors and returns n. */
+int or_last_krylov(const oracle_t* o, double* V, int max_vectors);
+
 /* hopping matrix J_ab the oracle built (N*N, row-major) */
 void or_get_hopping(const oracle_t* o, double* out);
 

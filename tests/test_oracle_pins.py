@@ -702,3 +702,103 @@ def test_load_state_continues_the_trajectory_exactly():
         assert np.array_equal(ta, tb) and np.array_equal(aa, ab)
         sa, sb = a.stats(), b.stats()
         assert all(sa[k] == sb[k] for k in sa if k != "time")     # b's clock started at its set_state
+
+
+# ---------------------------------------------------------------- Lanczos propagator (App. C.3)
+def _lanczos_tb_basis(mutant=None):
+    """Lanczos vectors of one step from psi' = (|n-1> + |n> + |n+1>)/sqrt(3) on an
+    open tight-binding chain (g = 0, eps = 0, J = 1), rows n-4..n+4."""
+    N, n = 21, 10
+    o = Oracle(N, W.CHAIN, J=1.0, g=0.0, omega=1.0, cap=0, m=2, m_init=-1, propagator=1, kmax=30,
+               mutant=mutant)
+    o.set_state([n - 1, n, n + 1], np.zeros((3, N), dtype=np.int32), np.ones(3) / math.sqrt(3.0))
+    o.step(0.05, 0.0)
+    V = o.krylov_basis()
+    t, _ = o.rows()
+    sites = list(t[:, 0])
+    g = gold("lanczos_V4_appC3.json")
+    idx = [sites.index(n + d) for d in g["rows_offset"]]
+    outside = [i for i in range(len(sites)) if i not in idx]
+    return V, idx, outside, g
+
+
+def test_lanczos_basis_matches_the_paper_V4():
+    """App. C.3 prints V_4 for this state: the first four Lanczos vectors of the
+    oracle equal it entry by entry (24 non-zeros) and vanish off rows n-4..n+4."""
+    V, idx, outside, g = _lanczos_tb_basis()
+    ref = np.array([[a * math.sqrt(b) for a, b in row] for row in g["entries_as_a_sqrt_b"]]) / g["scale"]
+    assert V.shape[1] >= 4
+    assert np.max(np.abs(V[idx, :4] - ref)) <= 1e-14
+    assert np.count_nonzero(np.abs(ref) > 0) == g["nonzeros"]
+    assert np.max(np.abs(V[outside, :4])) == 0.0
+    # orthonormal basis
+    G = V.conj().T @ V
+    assert np.max(np.abs(G - np.eye(V.shape[1]))) <= 1e-13
+
+
+def test_lanczos_pin_fails_without_the_beta_term():
+    V, idx, _, g = _lanczos_tb_basis(mutant="LANCZOS_NO_BETA")
+    ref = np.array([[a * math.sqrt(b) for a, b in row] for row in g["entries_as_a_sqrt_b"]]) / g["scale"]
+    assert np.max(np.abs(V[idx, :4] - ref)) > 1e-2
+
+
+@pytest.mark.parametrize("dt,nsteps", [(0.05, 40), (0.5, 6), (3.0, 4)])
+def test_lanczos_full_space_matches_dense_expm(dt, nsteps):
+    """ring4 with its whole 2500-state space every step (theta = 0): the Lanczos
+    step exp(-i h H) v ~ beta_0 V_n exp(-i h T_n) e_1 equals exp(-iHt) psi0 to
+    1e-12; at dt = 3 the step splits into the same substeps as the series."""
+    eps, H, D, strides = _ring4_dense()
+    U = propagator(H)
+    o = Oracle(4, W.RING, J=1.0, eps=eps, omega=1.0, g=1.0, cap=4, m=2, m_init=-1, propagator=1, kmax=40)
+    o.set_state([0], [[0] * 4], [1.0])
+    psi0 = state_vector(o, D, strides, H.shape[0])
+    for _ in range(nsteps):
+        o.step(dt, 0.0)
+    st = o.stats()
+    assert st["substeps"] == max(1, math.ceil(st["hbound"] * dt / 8.0))
+    assert st["terms"] <= 40 * st["substeps"]
+    v = state_vector(o, D, strides, H.shape[0])
+    assert np.linalg.norm(v - U(nsteps * dt, psi0)) <= 1e-12
+    assert abs(st["energy"] - np.vdot(v, H @ v).real) <= 1e-10     # E of c', conserved by the step
+
+
+def test_lanczos_two_site_breakdown_is_exact():
+    """N = 2, g = 0: the Krylov space of |0> is two-dimensional, so the
+    recurrence ends (beta_2 = 0) after two vectors and the step is exact:
+    P_1 = sin^2(J t)."""
+    o = Oracle(2, W.RING, J=1.0, omega=1.0, g=0.0, cap=1, m=2, m_init=-1, propagator=1, kmax=10)
+    o.set_state([0], [[0, 0]], [1.0])
+    for k in range(1, 61):
+        o.step(0.1, 0.0)
+        assert o.stats()["terms"] <= 2
+        P, _ = o.populations()
+        assert abs(P[1] - math.sin(0.1 * k) ** 2) < 1e-13
+
+
+def test_lanczos_agrees_with_the_series_on_a_truncated_trajectory():
+    """Both propagators approximate the same exp(-i P H P dt) to 1e-15 per step;
+    on a truncated ring16 prefix the rows stay identical and the amplitudes
+    within 1e-12 normwise."""
+    cfg = W.WORKLOADS["ring16"]
+    kw = W.model_kwargs(cfg, m_init=4)
+    a, b = Oracle(**kw), Oracle(**kw, propagator=1, kmax=30)
+    for o in (a, b):
+        o.set_state(*W.start_state(cfg))
+    for _ in range(12):
+        a.step(0.02, 1e-5)
+        b.step(0.02, 1e-5)
+        ta, aa = a.rows()
+        tb, ab = b.rows()
+        assert np.array_equal(ta, tb)
+        assert np.max(np.abs(aa - ab)) <= 1e-12 * np.linalg.norm(aa)
+    assert b.stats()["terms"] < a.stats()["terms"]
+
+
+def test_lanczos_rejects_recording_and_bad_dimensions():
+    with pytest.raises(OracleError):
+        Oracle(2, W.RING, J=1.0, g=0.0, cap=1, propagator=1, kmax=0)
+    o = Oracle(2, W.RING, J=1.0, g=0.0, cap=1, propagator=1, kmax=8)
+    o.record(True)
+    o.set_state([0], [[0, 0]], [1.0])
+    with pytest.raises(OracleError):
+        o.step(0.05, 0.0)
