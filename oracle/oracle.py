@@ -65,6 +65,7 @@ def _load(mutant=None):
         lib.or_set_xmax.argtypes = [P, C.c_double]
         lib.or_set_propagator.argtypes = [P, C.c_int, C.c_int]
         lib.or_last_krylov.argtypes = [P, dp, C.c_int]
+        lib.or_set_coefficients.argtypes = [P, C.c_double, dp, dp, dp]
         lib.or_get_hopping.argtypes = [P, dp]
         lib.or_set_state.argtypes = [P, C.c_int, ip, ip, dp]
         lib.or_load_state.argtypes = [P, C.c_int, ip, ip, dp]
@@ -147,6 +148,16 @@ class Oracle:
         if h:
             self._lib.or_destroy(h)
             self._h = None
+
+    def set_coefficients(self, J, eps=None, omega=None, g=None):
+        """Replace H's values between steps (piecewise-constant time dependence);
+        the move graph is fixed (zeros of J and g stay zeros)."""
+        f = lambda v: None if v is None else np.ascontiguousarray(
+            np.broadcast_to(np.asarray(v, dtype=np.float64), (self.N,)))
+        e, w, gg = f(eps), f(omega), f(g)
+        rc = self._lib.or_set_coefficients(self._h, float(J), _dp(e), _dp(w), _dp(gg))
+        if rc:
+            raise OracleError(rc, "or_set_coefficients")
 
     def krylov_basis(self):
         """Lanczos vectors v_1..v_n of the last series of the last Lanczos step, [q, n]."""

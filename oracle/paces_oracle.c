@@ -285,6 +285,34 @@ int or_set_xmax(oracle_t* o, double xmax)
     return OR_OK;
 }
 
+/* Piecewise-constant time dependence (Sec. 6's extension to time-dependent H:
+ * the Hamiltonian is replaced between steps).  New values of J (the hopping
+ * scale of the fixed pattern), eps, omega and g (NULL keeps an array); the
+ * graph of moves may not change, so J and every g_s must stay zero exactly
+ * where they were zero. */
+int or_set_coefficients(oracle_t* o, double J, const double* eps, const double* omega, const double* g)
+{
+    if (!o || !isfinite(J)) return OR_INVALID;
+    if (o->recording) return OR_INVALID;      /* the adjoint assumes one H for all steps */
+    int N = o->N;
+    int jz_old = 1;
+    for (int i = 0; i < N * N; ++i)
+        if (o->Jm[i] != 0.0) jz_old = 0;
+    if ((J == 0.0) != jz_old) return OR_INVALID;
+    for (int s = 0; s < N; ++s) {
+        if (eps && !isfinite(eps[s])) return OR_INVALID;
+        if (omega && !isfinite(omega[s])) return OR_INVALID;
+        if (g && (!isfinite(g[s]) || ((g[s] == 0.0) != (o->g[s] == 0.0)))) return OR_INVALID;
+    }
+    for (int i = 0; i < N * N; ++i) o->Jm[i] = J * o->Mm[i];
+    for (int s = 0; s < N; ++s) {
+        if (eps) o->eps[s] = eps[s];
+        if (omega) o->omega[s] = omega[s];
+        if (g) o->g[s] = g[s];
+    }
+    return OR_OK;
+}
+
 int or_set_propagator(oracle_t* o, int kind, int kmax)
 {
     if (!o || kind < 0 || kind > 1 || (kind == 1 && (kmax < 1 || kmax > OR_MAX_KRYLOV))) return OR_INVALID;

@@ -52,6 +52,11 @@ int or_set_propagator(oracle_t* o, int kind, int kmax);
  * max_vectors and returns n. */
 int or_last_krylov(const oracle_t* o, double* V, int max_vectors);
 
+/* Time-dependent H, piecewise constant (replaced between steps): new hopping
+ * scale J and site arrays eps, omega, g (NULL keeps one).  The move graph is
+ * fixed: J and each g_s must stay zero exactly where they were (OR_INVALID). */
+int or_set_coefficients(oracle_t* o, double J, const double* eps, const double* omega, const double* g);
+
 /* hopping matrix J_ab the oracle built (N*N, row-major) */
 void or_get_hopping(const oracle_t* o, double* out);
 

@@ -802,3 +802,68 @@ def test_lanczos_rejects_recording_and_bad_dimensions():
     o.set_state([0], [[0, 0]], [1.0])
     with pytest.raises(OracleError):
         o.step(0.05, 0.0)
+
+
+# ---------------------------------------------------------------- piecewise-constant time dependence (Sec. 6)
+def _drive(t):
+    """Coefficients of a driven ring4 at time t: J, eps, omega, g."""
+    return (1.0 + 0.3 * math.sin(1.3 * t), np.array([0.1, -0.2, 0.3, 0.0]) * math.cos(0.7 * t),
+            np.full(4, 1.0 + 0.1 * math.sin(t)), np.full(4, 1.0 + 0.2 * math.cos(t)))
+
+
+def test_piecewise_constant_H_matches_the_product_of_dense_exponentials():
+    """H replaced before every step (the paper's extension to Hamiltonians that
+    are piecewise constant in time): over ring4's full space (theta = 0) the
+    state is U_K ... U_1 psi0 (phonon cap 3: 1024 states), U_k = exp(-i H(t_k) dt) from the dense Kronecker
+    H of that step's coefficients."""
+    dt, K = 0.05, 30
+    J, eps, omega, g = _drive(0.0)
+    o = Oracle(4, W.RING, J=J, eps=eps, omega=omega, g=g, cap=3, m=2, m_init=-1)
+    o.set_state([0], [[0] * 4], [1.0])
+    H0, D, strides = dense_holstein(ring_hop(4, J), eps, omega, g, [3] * 4)
+    psi = state_vector(o, D, strides, H0.shape[0])
+    for k in range(K):
+        J, eps, omega, g = _drive(k * dt)
+        o.set_coefficients(J, eps, omega, g)
+        o.step(dt, 0.0)
+        H, _, _ = dense_holstein(ring_hop(4, J), eps, omega, g, [3] * 4)
+        psi = propagator(H)(dt, psi)
+    assert np.linalg.norm(state_vector(o, D, strides, H0.shape[0]) - psi) <= 1e-12
+
+
+def test_uniform_site_energy_drive_is_a_global_phase():
+    """eps_s(t) = f(t) on every site adds f(t) times the identity: the truncated
+    trajectory keeps its rows, populations and phonon numbers, and C(t) picks up
+    exp(-i sum_k f(t_k) dt)."""
+    cfg = W.WORKLOADS["ring16"]
+    kw = W.model_kwargs(cfg, m_init=4)
+    a, b = Oracle(**kw), Oracle(**kw)
+    for o in (a, b):
+        o.set_state(*W.start_state(cfg))
+    phase = 0.0
+    for k in range(15):
+        f = 0.5 * math.cos(2.0 * k * 0.02)
+        b.set_coefficients(cfg["J"], eps=np.full(16, f))
+        phase += f * 0.02
+        a.step(0.02, 1e-5)
+        b.step(0.02, 1e-5)
+        ta, _ = a.rows()
+        tb, _ = b.rows()
+        assert np.array_equal(ta, tb)
+        Pa, na = a.populations()
+        Pb, nb = b.populations()
+        assert np.max(np.abs(Pa - Pb)) <= 1e-12 and np.max(np.abs(na - nb)) <= 1e-11
+        sa, sb = a.stats(), b.stats()
+        Ca, Cb = sa["C_re"] + 1j * sa["C_im"], sb["C_re"] + 1j * sb["C_im"]
+        assert abs(Cb - Ca * np.exp(-1j * phase)) <= 1e-12
+
+
+def test_coefficient_updates_keep_the_move_graph():
+    o = Oracle(4, W.RING, J=1.0, omega=1.0, g=1.0, cap=4, m=2, m_init=2)
+    for bad in (dict(J=0.0), dict(J=1.0, g=[1.0, 0.0, 1.0, 1.0]), dict(J=float("nan"))):
+        with pytest.raises(OracleError):
+            o.set_coefficients(**bad)
+    o.set_coefficients(0.5, g=[2.0] * 4)
+    o.record(True)
+    with pytest.raises(OracleError):
+        o.set_coefficients(1.0)
