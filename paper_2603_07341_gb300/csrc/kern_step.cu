@@ -251,6 +251,87 @@ __device__ __forceinline__ void cand_parent(const DevModel* __restrict__ M, uint
     p = lo + pl;
 }
 
+// One-word keys: the kCPT candidates of a thread are inserted in lockstep.
+// Every round first claims, with one 16-byte compare-and-swap each, all the
+// empty slots its candidates stand on, then compares every occupied slot's key
+// with its candidate's (a one-word slot holds the key next to the tag): the
+// same key as another candidate's joins it (atomicMin on the tag, the lowest
+// candidate index wins), the same key as an existing row resolves to that row,
+// and a different key moves to the next slot, whose load is issued with the
+// others of the round.  All lanes run the same instructions (predicated), so a
+// warp keeps its 32 kCPT claims or probe loads in flight together instead of
+// resolving one candidate's chain (load, compare, claim) after another's.
+constexpr int kCPT1 = 4;                    // one-word keys: candidates per thread
+__device__ __forceinline__ void insert_lockstep(uint64_t* table, uint64_t slots, const Key<1> (&child)[kCPT1],
+                                                uint32_t c0, uint32_t stride, const bool (&ok)[kCPT1],
+                                                const Probe (&pb)[kCPT1], Counters* ctr, int step,
+                                                const uint32_t (&pp)[kCPT1], const int (&mvv)[kCPT1], int D,
+                                                uint32_t nc, uint32_t* __restrict__ cand_slot)
+{
+    constexpr int kCPT = kCPT1;
+    uint32_t pos[kCPT], res[kCPT];
+    uint64_t tag[kCPT], kw[kCPT];
+    unsigned act = 0;                               // bit k: candidate k unresolved
+#pragma unroll
+    for (int k = 0; k < kCPT; ++k) {
+        pos[k] = (uint32_t)pb[k].pos;               // slots < 2^32
+        tag[k] = pb[k].tag;
+        kw[k] = pb[k].kw;
+        res[k] = kNone;
+        act |= ok[k] ? (1u << k) : 0u;
+    }
+    for (uint32_t round = 0; round <= kMaxProbe; ++round) {
+        if (!__any_sync(0xffffffffu, act != 0)) break;
+        unsigned tried = 0;
+#pragma unroll
+        for (int k = 0; k < kCPT; ++k)              // claims of empty slots, all in flight
+            if (((act >> k) & 1u) && tag[k] == kEmpty) {
+                const uint64_t mine = (pb[k].fp << 32) | (uint64_t)(kCand | (c0 + (uint32_t)k * stride));
+                cas128(table + (uint64_t)pos[k] * 2, kEmpty, kEmpty, mine, child[k].w[0], tag[k], kw[k]);
+                tried |= 1u << k;
+            }
+        unsigned adv = 0;
+#pragma unroll
+        for (int k = 0; k < kCPT; ++k) {
+            if (!((act >> k) & 1u)) continue;
+            if (((tried >> k) & 1u) && tag[k] == kEmpty) {   // claimed (the old tag was empty)
+                res[k] = pos[k];
+                act &= ~(1u << k);
+                continue;
+            }
+            // occupied, or lost the race: tag and kw hold the slot's entry
+            if (kw[k] == child[k].w[0]) {
+                const uint32_t v = (uint32_t)tag[k];
+                if (v & kCand) {                    // another candidate of this key
+                    const uint64_t mine = (pb[k].fp << 32) | (uint64_t)(kCand | (c0 + (uint32_t)k * stride));
+                    atomicMin((unsigned long long*)(table + (uint64_t)pos[k] * 2), (unsigned long long)mine);
+                    res[k] = pos[k];
+                } else {
+                    res[k] = kCand | v;             // an existing row
+                }
+                act &= ~(1u << k);
+            } else {
+                pos[k] = (uint32_t)slot_next(pos[k], slots);
+                adv |= 1u << k;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kCPT; ++k)              // next slots, all in flight
+            if ((adv >> k) & 1u) {
+                const ulonglong2 s2 = __ldcg(reinterpret_cast<const ulonglong2*>(table + (uint64_t)pos[k] * 2));
+                tag[k] = s2.x;
+                kw[k] = s2.y;
+            }
+    }
+#pragma unroll
+    for (int k = 0; k < kCPT; ++k) {
+        const uint32_t c = c0 + (uint32_t)k * stride;
+        if (c >= nc) continue;
+        if ((act >> k) & 1u) set_err(ctr, kErrProbe, step, 2);
+        cand_slot[(uint64_t)pp[k] * D + mvv[k]] = res[k];
+    }
+}
+
 template <int W>
 __global__ void __launch_bounds__(kBlock) k_level_insert(const DevModel* __restrict__ M, Counters* ctr, int f,
                                                          const uint64_t* __restrict__ keys,
@@ -266,11 +347,11 @@ __global__ void __launch_bounds__(kBlock) k_level_insert(const DevModel* __restr
         if (blockIdx.x == 0 && threadIdx.x == 0) set_err(ctr, kErrCand, step, f);
         return;
     }
-    constexpr int kCPT = W == 1 ? 4 : 2;
+    constexpr int kCPT = W == 1 ? kCPT1 : 2;
     const uint32_t nc = (uint32_t)ncand, stride = gridDim.x * blockDim.x;
     for (uint32_t c0 = blockIdx.x * blockDim.x + threadIdx.x; c0 < nc; c0 += stride * kCPT) {
         Key<W> child[kCPT];
-        Probe pb[kCPT];
+        Probe pb[kCPT] = {};
         uint32_t pp[kCPT];
         int mvv[kCPT];
         bool ok[kCPT];
@@ -291,14 +372,18 @@ __global__ void __launch_bounds__(kBlock) k_level_insert(const DevModel* __restr
 #pragma unroll
         for (int k = 0; k < kCPT; ++k)          // every home slot in flight at once
             if (ok[k]) probe_start<W>(table, slots, child[k], pb[k]);
+        if constexpr (W == 1) {
+            insert_lockstep(table, slots, child, c0, stride, ok, pb, ctr, step, pp, mvv, D, nc, cand_slot);
+        } else {
 #pragma unroll
-        for (int k = 0; k < kCPT; ++k) {
-            const uint32_t c = c0 + (uint32_t)k * stride;
-            if (c >= nc) continue;
-            uint32_t r = kNone;
-            bool res = false;
-            if (ok[k]) r = insert_candidate<W>(M, table, slots, child[k], c, keys, meta, lo, ctr, step, pb[k], res);
-            cand_slot[(uint64_t)pp[k] * D + mvv[k]] = res ? (kCand | r) : r;
+            for (int k = 0; k < kCPT; ++k) {
+                const uint32_t c = c0 + (uint32_t)k * stride;
+                if (c >= nc) continue;
+                uint32_t r = kNone;
+                bool res = false;
+                if (ok[k]) r = insert_candidate<W>(M, table, slots, child[k], c, keys, meta, lo, ctr, step, pb[k], res);
+                cand_slot[(uint64_t)pp[k] * D + mvv[k]] = res ? (kCand | r) : r;
+            }
         }
     }
 }
