@@ -120,7 +120,27 @@ typedef struct {
                                 /* rho = the largest absolute row sum of H over H_eff   */
                                 /* (each term rounded up to 2^-20); 0 = 8; < 0 = always */
                                 /* one series.  More than 1024 series: NOCONVERGE.      */
+    int32_t propagator;         /* PACES_TAYLOR (0, default) or PACES_LANCZOS           */
+    int32_t krylov_max;         /* PACES_LANCZOS: most Krylov vectors per series,       */
+                                /* 1..PACES_MAX_KRYLOV; 0 = 30                          */
 } paces_params;
+
+/* Propagator of a6.  PACES_TAYLOR is the series of App. C.1.  PACES_LANCZOS is
+ * the Lanczos decomposition App. C.3 compares it with:
+ *   exp(-i h H) v ~ V_n exp(-i h T_n) V_n^dag v = ||v|| V_n exp(-i h T_n) e_1,
+ * V_n the orthonormal Krylov basis of the three-term recurrence and T_n its
+ * tridiagonal matrix, run over the same substeps h = dt / s.  A series stops at
+ * the first n with h beta_n |(exp(-i h T_n) e_1)_n| <= taylor_tol (the norm of
+ * the residual of the Krylov solution relative to ||v||, times h) and fails
+ * with NOCONVERGE past krylov_max vectors.  It holds krylov_max vectors of 16
+ * bytes per row of capacity on the device (the memory cost App. C.3 weighs
+ * against the series) and applies H twice per vector's worth of streaming.
+ * Requires PACES_C128 and batch <= 1, and cannot be recorded for the reverse
+ * pass (paces_record: UNSUPPORTED).  The observables records' term count is the
+ * number of Krylov vectors used. */
+#define PACES_TAYLOR 0
+#define PACES_LANCZOS 1
+#define PACES_MAX_KRYLOV 32
 
 /* Ensembles (batch = R > 1).  The R realisations share every parameter except
  * the site energies.  They are evolved together as one block-diagonal problem:
@@ -233,6 +253,21 @@ paces_status paces_step(paces_t h, double dt, int64_t nsteps, double theta);
  * and UNSUPPORTED for ensembles (batch > 1). */
 paces_status paces_step_nom(paces_t h, double dt, int64_t nsteps, int64_t q_nom, uint64_t seed);
 
+/* Time-dependent Hamiltonians that are piecewise constant in time (the
+ * extension Sec. 6 describes: the Hamiltonian is adjusted at every time step,
+ * with its coupling magnitudes changing and its graph fixed).  Replaces, for
+ * the steps that follow, the hopping scale J (J_ab = J M_ab with the pattern M
+ * of paces_create), and, where the pointer is not NULL, eps[N] (or eps[R*N]
+ * for an ensemble), omega[N] and g[N] (copied).  The move graph may not
+ * change: J must be zero exactly when it was, and each g_s zero exactly where
+ * it was (INVALID otherwise).  Stream-ordered before the next step; the steps
+ * already taken are unaffected.  UNSUPPORTED while paces_record is on (the
+ * reverse pass assumes one Hamiltonian for all recorded steps); CAPACITY if
+ * the new values have more distinct off-diagonal elements than
+ * PACES_MAX_COEFS. */
+paces_status paces_set_coefficients(paces_t h, double J, const double* eps, const double* omega,
+                                    const double* g);
+
 /* Number of rows q = dim H_eff of the current state. */
 paces_status paces_num_rows(paces_t h, int64_t* rows);
 
@@ -272,7 +307,7 @@ paces_status paces_get_hamiltonian(paces_t h, int32_t* cnt, int32_t* cols, doubl
 #define PACES_OBS_ROWS 6         /* q = dim H_eff                               */
 #define PACES_OBS_KEPT 7         /* |M| after truncation                        */
 #define PACES_OBS_NNZ 8          /* stored entries of P H P incl. the diagonal  */
-#define PACES_OBS_TERMS 9        /* Taylor terms used                           */
+#define PACES_OBS_TERMS 9        /* Taylor terms (Lanczos: Krylov vectors) used  */
 #define PACES_OBS_NORM_BEFORE 10 /* ||c||^2 before truncation                   */
 #define PACES_OBS_SUBSTEPS 11    /* Taylor series the step ran (substeps)       */
 #define PACES_OBS_HBOUND 12      /* rho, the bound on ||P H P|| that set them    */

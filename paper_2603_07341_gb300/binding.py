@@ -18,6 +18,8 @@ OK, ERR_INVALID, ERR_KEY_WIDTH, ERR_CAPACITY, ERR_NOCONVERGE, ERR_CUDA, ERR_STAT
 RING, CHAIN, OPEN2D, OPEN3D, EXPLICIT = 0, 1, 2, 3, 4
 NEAREST, DIPOLAR = 0, 1
 C128, DW, C64_SPMV = 0, 1, 2
+TAYLOR, LANCZOS = 0, 1
+MAX_KRYLOV = 32
 MAX_SITES, MAX_WORDS = 128, 4
 OBS_FIELDS = ("time", "norm", "norm_phi0", "energy", "C_re", "C_im", "rows", "kept", "nnz", "terms",
               "norm_before", "substeps", "hbound")
@@ -30,7 +32,7 @@ EXPORTED = (
     "paces_get_levels", "paces_get_keep", "paces_get_hamiltonian", "paces_record_len",
     "paces_num_records", "paces_observables", "paces_profile", "paces_stage_stats",
     "paces_expand_noalloc", "paces_get_tuning", "paces_set_tuning", "paces_record", "paces_backward",
-    "paces_step_nom", "paces_selftest_barrier",
+    "paces_step_nom", "paces_selftest_barrier", "paces_set_coefficients",
 )
 
 
@@ -41,7 +43,8 @@ class Params(C.Structure):
                 ("g", C.POINTER(C.c_double)), ("phonon_cap", C.POINTER(C.c_int32)), ("m", C.c_int32),
                 ("m_init", C.c_int32), ("precision", C.c_int32), ("fixed_terms", C.c_int32),
                 ("taylor_tol", C.c_double), ("taylor_nmax", C.c_int32), ("max_rows", C.c_uint64),
-                ("batch", C.c_int32), ("reserved0", C.c_int32), ("taylor_xmax", C.c_double)]
+                ("batch", C.c_int32), ("reserved0", C.c_int32), ("taylor_xmax", C.c_double),
+                ("propagator", C.c_int32), ("krylov_max", C.c_int32)]
 
 
 class Layout(C.Structure):
@@ -139,6 +142,8 @@ def load():
     lib.paces_backward.argtypes = [P, C.c_int64, dp, dp, dp, dp]
     lib.paces_expand_noalloc.restype = S
     lib.paces_expand_noalloc.argtypes = [C.POINTER(Params), P, C.c_int64, P, C.c_int64, i64p, P]
+    lib.paces_set_coefficients.restype = S
+    lib.paces_set_coefficients.argtypes = [P, C.c_double, dp, dp, dp]
     lib.paces_selftest_barrier.restype = S
     lib.paces_selftest_barrier.argtypes = [C.c_int32, C.c_double, C.POINTER(C.c_int32)]
     _lib = lib
@@ -155,10 +160,11 @@ def _ip(a):
 
 def make_params(n_sites, lattice_kind=RING, dims=(0, 0, 0), coupling_kind=NEAREST, J=1.0, eps=None,
                 omega=None, g=None, cap=None, m=2, m_init=10, precision=C128, fixed_terms=0, tol=0.0,
-                nmax=0, max_rows=0, J_explicit=None, batch=1, xmax=0.0):
+                nmax=0, max_rows=0, J_explicit=None, batch=1, xmax=0.0, propagator=0, kmax=0):
     """Build a Params struct; returns (struct, keepalive arrays).  For an
     ensemble (batch R > 1) eps is [R, N] (or broadcastable to it).  xmax: the
-    substep bound (0: the library's 8; < 0: one Taylor series per step)."""
+    substep bound (0: the library's 8; < 0: one Taylor series per step).
+    propagator: TAYLOR or LANCZOS (kmax Krylov vectors at most; 0: 30)."""
     N = int(n_sites)
     R = max(1, int(batch))
     vec = lambda v: np.ascontiguousarray(np.broadcast_to(np.asarray(0.0 if v is None else v,
@@ -185,6 +191,7 @@ def make_params(n_sites, lattice_kind=RING, dims=(0, 0, 0), coupling_kind=NEARES
     p.taylor_tol, p.taylor_nmax, p.max_rows = float(tol), int(nmax), int(max_rows)
     p.batch = R
     p.taylor_xmax = float(xmax)
+    p.propagator, p.krylov_max = int(propagator), int(kmax)
     return p, keep
 
 
@@ -328,6 +335,22 @@ class Solver:
         """Steps with top-q_nom truncation (the paper's scheme; seeded tie-break)."""
         self._check(self._lib.paces_step_nom(self._h, float(dt), int(nsteps), int(q_nom),
                                              int(seed) & ((1 << 64) - 1)), "step_nom")
+
+    def set_coefficients(self, J, eps=None, omega=None, g=None):
+        """Replace H's values for the following steps (a Hamiltonian piecewise
+        constant in time); None keeps an array.  The move graph is fixed: J and
+        every g_s stay zero exactly where they were."""
+        n = self.N * self.batch
+
+        def f(v, k):
+            if v is None:
+                return None
+            a = np.asarray(v, dtype=np.float64)
+            a = a.reshape(-1) if a.size == k else a      # [R, N] site energies of an ensemble
+            return np.ascontiguousarray(np.broadcast_to(a, (k,)))
+        e, w, gg = f(eps, n), f(omega, self.N), f(g, self.N)
+        self._check(self._lib.paces_set_coefficients(self._h, float(J), _dp(e), _dp(w), _dp(gg)),
+                    "set_coefficients")
 
     def num_rows(self):
         n = C.c_int64()

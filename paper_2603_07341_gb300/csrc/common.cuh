@@ -25,6 +25,7 @@ constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr uint64_t kEmpty = ~0ull;
 constexpr uint32_t kMaxProbe = 1u << 16;
 constexpr int kMaxSub = 1024;         // Taylor series per time step (substeps)
+constexpr int kMaxKrylov = 32;        // Lanczos vectors per series (one warp lane each)
 
 // device error codes (Counters::err)
 enum DevErr : int {

@@ -36,6 +36,8 @@ struct TaylorArgs {
     double* totals;          // [2][4]
     void* terms;             // adjoint re-runs: phi_n stored at [(n - 1) * q + row]
     int term_max;
+    double2* kry;            // Lanczos: s_2 .. s_{kmax+1}, kry_stride rows apart
+    uint64_t kry_stride;
     TaylorParams p;
 };
 
@@ -168,9 +170,11 @@ __device__ __forceinline__ int series_count(const Counters* ctr, const TaylorPar
 // Rows of every 256-row window ordered by their entry count, largest first
 // (stable: equal counts keep row order): rperm[w + k] = offset in window w of
 // its k-th row.  The FP64 propagator gives each warp 32 consecutive ranks, so
-// the rows of a warp have (nearly) equal counts and no warp issues FP64
-// products for entries that only some of its rows have.  Deterministic, so
-// that replays repeat the reduction order bit for bit.
+// the rows of a warp have (nearly) equal counts and few warps issue FP64
+// products for entries that only some of their rows have.  A window is one
+// block's rows of one round, so the rows' own data stay within 256 rows (2048-
+// row windows were measured: 1.5x the DRAM traffic, no fewer idle FP64 lanes).
+// Deterministic, so that replays repeat the reduction order bit for bit.
 __global__ void __launch_bounds__(kBlock) k_row_order(const Counters* __restrict__ ctr, const uint8_t* __restrict__ cnt,
                                                       int pmax, uint8_t* __restrict__ rperm)
 {
@@ -293,22 +297,29 @@ __global__ void __launch_bounds__(kBlock) k_taylor_f64(TaylorArgs a)
             const bool first = (j == 0 && n == 1);
             float phi2 = 0.f;
             double acc_e = 0.0, acc_n = 0.0;
-            auto finish_row = [&](uint32_t row, double2 yv) {
-                double2 xi = x[row];
-                double d;
+            const bool odd = (n & 1) != 0;
+            // the row's own amplitude, B's diagonal and the accumulator
+            auto load_row = [&](uint32_t row, double2& xi, double& d, double2& rr) {
+                xi = x[row];
+                d = first ? a.diag[row] : a.diag_h[row];
+                rr = (n == 1) ? xi : a.r[row];
+            };
+            auto finish_row = [&](uint32_t row, double2 yv, double2 xi, double d, double2 rr) {
                 if (first) {
-                    d = h * a.diag[row];
+                    d = h * d;
                     a.diag_h[row] = d;
-                } else {
-                    d = a.diag_h[row];
                 }
                 yv.x = fma(d, xi.x, yv.x);
                 yv.y = fma(d, xi.y, yv.y);                // psi_n = B x
                 y[row] = yv;
-                double2 rr = (n == 1) ? xi : a.r[row];
-                // r += (sr + i si) psi_n
-                rr.x = fma(sr, yv.x, fma(-si, yv.y, rr.x));
-                rr.y = fma(sr, yv.y, fma(si, yv.x, rr.y));
+                // r += (sr + i si) psi_n: one of sr, si is zero (n odd: sr)
+                if (odd) {
+                    rr.x = fma(-si, yv.y, rr.x);
+                    rr.y = fma(si, yv.x, rr.y);
+                } else {
+                    rr.x = fma(sr, yv.x, rr.x);
+                    rr.y = fma(sr, yv.y, rr.y);
+                }
                 a.r[row] = rr;
                 if (store && slot < a.term_max)
                     store[(size_t)slot * q + row] = make_double2(sr * yv.x - si * yv.y, sr * yv.y + si * yv.x);
@@ -320,47 +331,53 @@ __global__ void __launch_bounds__(kBlock) k_taylor_f64(TaylorArgs a)
                 }
             };
             if constexpr (LPR == 1) {
-                // one 256-row window per block and round, rows by entry count
+                // one 256-row window per block and round, rows by entry count;
+                // every load of a row (its entries, their amplitudes, its own
+                // amplitude, diagonal and accumulator) is issued before its
+                // first FP64 operation
                 for (uint32_t wb = blockIdx.x * kBlock; wb < q; wb += G * kBlock) {
                     const uint32_t sl = wb + threadIdx.x;
                     const uint32_t row = sl < q ? wb + a.rperm[sl] : q;
                     const bool valid = row < q;
                     const uint32_t c = valid ? a.cnt[row] : 0u;
+                    const uint64_t base = (uint64_t)row * P;
+                    uint4 cc = make_uint4(0, 0, 0, 0);
+                    uint32_t ii = 0;
+                    if (c > 0) {
+                        cc = *reinterpret_cast<const uint4*>(a.col + base);
+                        ii = *reinterpret_cast<const uint32_t*>(a.cid + base);
+                    }
+                    const uint32_t cs[4] = {cc.x, cc.y, cc.z, cc.w};
+                    double2 xv[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) xv[k] = c > (uint32_t)k ? x[cs[k]] : make_double2(0.0, 0.0);
+                    double2 xi = make_double2(0.0, 0.0), rr = xi;
+                    double d = 0.0;
+                    if (valid) load_row(row, xi, d, rr);
                     double yr = 0.0, yi = 0.0;
-                    if (__any_sync(0xffffffffu, c > 0)) {
-                        const uint64_t base = (uint64_t)row * P;
-                        uint4 cc = make_uint4(0, 0, 0, 0);
-                        uint32_t ii = 0;
-                        if (valid) {
-                            cc = *reinterpret_cast<const uint4*>(a.col + base);
-                            ii = *reinterpret_cast<const uint32_t*>(a.cid + base);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        if (__any_sync(0xffffffffu, c > (uint32_t)k)) {
+                            const double av = c > (uint32_t)k ? coef[(ii >> (8 * k)) & 0xFFu] : 0.0;
+                            yr = fma(av, xv[k].x, yr);
+                            yi = fma(av, xv[k].y, yi);
                         }
-                        const uint32_t cs[4] = {cc.x, cc.y, cc.z, cc.w};
+                    }
+                    for (uint32_t e = 4; e < c; e += 4) {      // pitches above 4 (P <= 8)
+                        const uint4 c2 = *reinterpret_cast<const uint4*>(a.col + base + e);
+                        const uint32_t i2 = *reinterpret_cast<const uint32_t*>(a.cid + base + e);
+                        const uint32_t cs2[4] = {c2.x, c2.y, c2.z, c2.w};
 #pragma unroll
                         for (int k = 0; k < 4; ++k) {
-                            if (__any_sync(0xffffffffu, c > (uint32_t)k) && c > (uint32_t)k) {
-                                const double av = coef[(ii >> (8 * k)) & 0xFFu];
-                                const double2 xv = x[cs[k]];
-                                yr = fma(av, xv.x, yr);
-                                yi = fma(av, xv.y, yi);
-                            }
-                        }
-                        for (uint32_t e = 4; e < c; e += 4) {      // pitches above 4 (P <= 8)
-                            const uint4 c2 = *reinterpret_cast<const uint4*>(a.col + base + e);
-                            const uint32_t i2 = *reinterpret_cast<const uint32_t*>(a.cid + base + e);
-                            const uint32_t cs2[4] = {c2.x, c2.y, c2.z, c2.w};
-#pragma unroll
-                            for (int k = 0; k < 4; ++k) {
-                                if (e + k < c) {
-                                    const double av = coef[(i2 >> (8 * k)) & 0xFFu];
-                                    const double2 xv = x[cs2[k]];
-                                    yr = fma(av, xv.x, yr);
-                                    yi = fma(av, xv.y, yi);
-                                }
+                            if (e + k < c) {
+                                const double av = coef[(i2 >> (8 * k)) & 0xFFu];
+                                const double2 xw = x[cs2[k]];
+                                yr = fma(av, xw.x, yr);
+                                yi = fma(av, xw.y, yi);
                             }
                         }
                     }
-                    if (valid) finish_row(row, make_double2(yr, yi));
+                    if (valid) finish_row(row, make_double2(yr, yi), xi, d, rr);
                 }
             } else {
                 for (uint32_t rb = warp * RPW; rb < q; rb += nwarps * RPW) {
@@ -369,7 +386,12 @@ __global__ void __launch_bounds__(kBlock) k_taylor_f64(TaylorArgs a)
                     uint32_t c = valid ? a.cnt[row] : 0u;
                     uint64_t base = (uint64_t)row * P;
                     double2 yv = row_apply<LPR, double2>(a.col, a.cid, c, base, coef, x, lane);
-                    if (valid && lane == 0) finish_row(row, yv);
+                    if (valid && lane == 0) {
+                        double2 xi, rr;
+                        double d;
+                        load_row(row, xi, d, rr);
+                        finish_row(row, yv, xi, d, rr);
+                    }
                 }
             }
             ++slot;
@@ -875,13 +897,223 @@ __global__ void __launch_bounds__(kBlock) k_taylor_c64(TaylorArgs a)
     }
 }
 
+// ---------------------------------------------------------------- Lanczos (App. C.3)
+// y = exp(-i h T) e_1 for the j x j symmetric tridiagonal T (diagonal al[0..j-1],
+// off-diagonal be[0..j-2]), one lane per component (j <= 32): the Taylor series
+// u_n = (-i h / n) T u_{n-1}, y = sum_n u_n, until ||u_n||^2 <= 1e-34 ||y||^2.
+// Warp sums by an xor butterfly give every lane the same bits, so every lane
+// (and every block, from the same al, be) takes the same decisions.
+__device__ __forceinline__ double warp_allsum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ void tri_exp_e1(const double* al, const double* be, int j, double h, int lane, double& yr, double& yi)
+{
+    const double a = lane < j ? al[lane] : 0.0;
+    const double bl = (lane >= 1 && lane < j) ? be[lane - 1] : 0.0;
+    const double bu = (lane + 1 < j) ? be[lane] : 0.0;
+    double ur = lane == 0 ? 1.0 : 0.0, ui = 0.0;
+    yr = ur;
+    yi = 0.0;
+    for (int n = 1; n <= 400; ++n) {
+        const double upr = __shfl_up_sync(0xffffffffu, ur, 1), upi = __shfl_up_sync(0xffffffffu, ui, 1);
+        const double dnr = __shfl_down_sync(0xffffffffu, ur, 1), dni = __shfl_down_sync(0xffffffffu, ui, 1);
+        const double vr = fma(a, ur, fma(bl, upr, bu * dnr));
+        const double vi = fma(a, ui, fma(bl, upi, bu * dni));
+        const double f = h / (double)n;
+        ur = f * vi;                       // (-i f) (vr + i vi)
+        ui = -f * vr;
+        yr += ur;
+        yi += ui;
+        const double t2 = warp_allsum(fma(ur, ur, ui * ui)), y2 = warp_allsum(fma(yr, yr, yi * yi));
+        if (t2 <= 1e-34 * y2) break;
+    }
+}
+
+// exp(-i P H P dt) c' by the Lanczos decomposition of App. C.3,
+// exp(-i h H) v ~ beta_0 V_n exp(-i h T_n) e_1, as the same s = ceil(rho dt /
+// xmax) series of h = dt / s as the Taylor propagator.  The basis is kept
+// unnormalised, s_1 = v and s_{j+1} = beta_j v_{j+1}, with v_k = sigma_k s_k,
+// sigma_k = 1 / ||s_k||: per Krylov vector, pass A writes t = H s_j into the
+// slot of s_{j+1} (SpMV with the table of H's entries, unscaled) and sums
+// Re<s_j|t>, so alpha_j = sigma_j^2 Re<s_j|t>; pass B turns t in place into
+// s_{j+1} = sigma_j t - alpha_j sigma_j s_j - beta_{j-1} sigma_{j-1} s_{j-1}
+// and sums its norm, beta_j.  Each pass ends at the reducing grid barrier.
+// Then every block computes y = exp(-i h T_j) e_1 (one warp) and stops at the
+// first j with h beta_j |y_j| <= tol (the residual estimate); past kmax
+// vectors the step does not converge.  The series' result
+// r = ||v|| sum_k y_k sigma_k s_k is one more streaming pass.  FP64 throughout;
+// one Krylov vector costs two passes and the basis kmax vectors of storage,
+// against one pass and no storage per Taylor term.
+template <int LPR>
+__global__ void __launch_bounds__(kBlock) k_lanczos_f64(TaylorArgs a)
+{
+    __shared__ double coef[kMaxCoefs];
+    __shared__ double al[kMaxKrylov], be[kMaxKrylov + 1], sg[kMaxKrylov + 2];
+    __shared__ double yre[32], yim[32];
+    __shared__ double tsh[4];
+    __shared__ int sstop;
+    Counters* ctr = a.ctr;
+    if (ctr->err) return;
+    const DevModel* M = a.M;
+    const uint32_t q = ctr->q;
+    const uint64_t P = (uint64_t)M->P;
+    const unsigned G = gridDim.x;
+    constexpr uint32_t RPW = 32 / LPR;
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (G * blockDim.x) >> 5;
+    const int lane = (threadIdx.x & 31) % LPR;
+    const uint32_t sub = (threadIdx.x & 31) / LPR;
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = G * blockDim.x;
+    const int K = a.p.kmax;
+    const double tol = sqrt(a.p.tol2);
+
+    const int nsub = series_count(ctr, a.p);
+    if (nsub < 1) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_err(ctr, kErrNoConverge, a.p.step, -1);
+        return;
+    }
+    const double h = a.p.dt / (double)nsub;
+    for (int t = threadIdx.x; t < M->ncoef; t += blockDim.x) coef[t] = M->coef[t];
+    __syncthreads();
+    int bar = 0;
+    auto reduce = [&](double (&acc)[4]) -> bool {
+        double* part = a.partials + (size_t)(bar & 1) * G * 4;
+        double* tot = a.totals + (bar & 1) * 4;
+        ++bar;
+        block_sum<kBlock, 4>(acc, part + 4 * blockIdx.x);
+        if (!barrier_reduce(ctr, part, tot, G)) return false;
+        if (threadIdx.x < 4) tsh[threadIdx.x] = __ldcg(tot + threadIdx.x);
+        __syncthreads();
+        return true;
+    };
+    double E = 0.0, n0 = 0.0;
+    int total = 0;
+    bool conv = true;
+    for (int js = 0; js < nsub && conv; ++js) {
+        const double2* s1 = js == 0 ? a.c_in : a.r;
+        auto S = [&](int k) -> const double2* { return k == 1 ? s1 : a.kry + (uint64_t)(k - 2) * a.kry_stride; };
+        double b0 = 0.0;
+        int n = 0;
+        bool done = false;
+        for (int j = 1; j <= K; ++j) {
+            const double2* sj = S(j);
+            double2* out = a.kry + (uint64_t)(j - 1) * a.kry_stride;
+            // pass A: t = H s_j
+            double acc[4] = {0.0, 0.0, 0.0, 0.0};
+            for (uint32_t rb = warp * RPW; rb < q; rb += nwarps * RPW) {
+                const uint32_t row = rb + sub;
+                const bool valid = row < q;
+                const uint32_t c = valid ? a.cnt[row] : 0u;
+                double2 yv = row_apply<LPR, double2>(a.col, a.cid, c, (uint64_t)row * P, coef, sj, lane);
+                if (valid && lane == 0) {
+                    const double2 xi = sj[row];
+                    const double d = a.diag[row];
+                    yv.x = fma(d, xi.x, yv.x);
+                    yv.y = fma(d, xi.y, yv.y);
+                    out[row] = yv;
+                    acc[0] = fma(xi.x, yv.x, fma(xi.y, yv.y, acc[0]));
+                    if (j == 1) acc[1] = fma(xi.x, xi.x, fma(xi.y, xi.y, acc[1]));
+                }
+            }
+            if (!reduce(acc)) return;
+            if (j == 1) {
+                b0 = sqrt(tsh[1]);
+                if (js == 0) {
+                    E = tsh[0];
+                    n0 = tsh[1];
+                }
+                if (b0 == 0.0) {            // exp(..) 0 = 0
+                    done = true;
+                    n = 0;
+                    break;
+                }
+                if (threadIdx.x == 0) sg[1] = 1.0 / b0;
+                __syncthreads();
+            }
+            if (threadIdx.x == 0) al[j - 1] = sg[j] * sg[j] * tsh[0];
+            __syncthreads();
+            // pass B: s_{j+1} = sigma_j t - alpha_j sigma_j s_j - beta_{j-1} sigma_{j-1} s_{j-1}
+            const double cs = sg[j], ca = -al[j - 1] * sg[j];
+            const double cb = j > 1 ? -be[j - 1] * sg[j - 1] : 0.0;
+            const double2* sm = j > 1 ? S(j - 1) : sj;
+            double acc2[4] = {0.0, 0.0, 0.0, 0.0};
+            for (uint32_t row = tid; row < q; row += nthr) {
+                const double2 t = out[row], x = sj[row], xm = sm[row];
+                double2 w;
+                w.x = fma(cs, t.x, fma(ca, x.x, cb * xm.x));
+                w.y = fma(cs, t.y, fma(ca, x.y, cb * xm.y));
+                out[row] = w;
+                acc2[0] = fma(w.x, w.x, fma(w.y, w.y, acc2[0]));
+            }
+            if (!reduce(acc2)) return;
+            if (threadIdx.x == 0) be[j] = sqrt(tsh[0]);
+            __syncthreads();
+            if (threadIdx.x < 32) {
+                double yr, yi;
+                tri_exp_e1(al, be + 1, j, h, threadIdx.x, yr, yi);
+                yre[threadIdx.x] = yr;
+                yim[threadIdx.x] = yi;
+                const double lr = __shfl_sync(0xffffffffu, yr, j - 1), li = __shfl_sync(0xffffffffu, yi, j - 1);
+                if (threadIdx.x == 0) {
+                    sstop = h * be[j] * sqrt(fma(lr, lr, li * li)) <= tol;
+                    sg[j + 1] = 1.0 / be[j];
+                }
+            }
+            __syncthreads();
+            n = j;
+            if (sstop) {
+                done = true;
+                break;
+            }
+        }
+        total += n;
+        if (blockIdx.x == 0 && threadIdx.x == 0) ctr->sub_terms[js] = n;
+        if (!done) {
+            conv = false;
+            break;
+        }
+        // r = ||v|| sum_k y_k sigma_k s_k (in place over s_1 when s_1 = r)
+        for (uint32_t row = tid; row < q; row += nthr) {
+            double rr = 0.0, ri = 0.0;
+            for (int k = 1; k <= n; ++k) {
+                const double2 x = S(k)[row];
+                const double f = b0 * sg[k];
+                const double cr = f * yre[k - 1], ci = f * yim[k - 1];
+                rr = fma(cr, x.x, fma(-ci, x.y, rr));
+                ri = fma(cr, x.y, fma(ci, x.x, ri));
+            }
+            a.r[row] = make_double2(rr, ri);
+        }
+        if (js + 1 < nsub) {                // the next series gathers r
+            double z[4] = {0.0, 0.0, 0.0, 0.0};
+            if (!reduce(z)) return;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctr->nterms = total;
+        ctr->nsub = nsub;
+        ctr->norm_r = 0.0;
+        ctr->norm_phi0 = n0;
+        ctr->energy = E;
+        if (!conv && atomicCAS(&ctr->err, 0, (int)kErrNoConverge) == 0) {
+            ctr->err_step = a.p.step;
+            ctr->err_info = total;
+        }
+    }
+}
+
 // Co-resident blocks per SM of the propagator variant that the precision
 // selects (PACES_C128, PACES_DW or PACES_C64_SPMV).
 template <int LPR>
 static int occupancy(int precision)
 {
     int n = 0;
-    const void* fn = precision == PACES_C128 ? (const void*)k_taylor_f64<LPR>
+    const void* fn = precision == kPrecLanczos ? (const void*)k_lanczos_f64<LPR>
+                   : precision == PACES_C128 ? (const void*)k_taylor_f64<LPR>
                    : precision == PACES_C64_SPMV ? (const void*)k_taylor_c64<LPR> : (const void*)k_taylor_dw<LPR>;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, kBlock, 0);
     return n;
@@ -915,10 +1147,15 @@ int launch_taylor(const Bufs& b, const TaylorParams& p, cudaStream_t st)
     a.totals = b.partials + 2 * 4 * (size_t)b.taylor_grid;
     a.terms = b.terms;
     a.term_max = b.term_max;
+    a.kry = b.kry;
+    a.kry_stride = b.cap_rows;
     a.p = p;
     void* args[] = {&a};
     const void* fn;
-    if (p.fmt == 1)
+    if (p.lanczos)
+        fn = p.lpr == 1 ? (const void*)k_lanczos_f64<1> : p.lpr == 4 ? (const void*)k_lanczos_f64<4>
+                                                                     : (const void*)k_lanczos_f64<8>;
+    else if (p.fmt == 1)
         fn = p.lpr == 1 ? (const void*)k_taylor_f64<1> : p.lpr == 4 ? (const void*)k_taylor_f64<4>
                                                                     : (const void*)k_taylor_f64<8>;
     else if (p.c64)
@@ -940,7 +1177,7 @@ int launch_taylor(const Bufs& b, const TaylorParams& p, cudaStream_t st)
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int n = 0;
-    if (p.fmt == 1 && p.lpr == 1) {          // rows of every window by entry count
+    if (p.fmt == 1 && p.lpr == 1 && !p.lanczos) {   // rows of every window by entry count
         k_row_order<<<b.grid, kBlock, 0, st>>>(b.ctr, b.cnt, b.P, b.rperm);
         ++n;
     }

@@ -220,6 +220,12 @@ paces_status check_params(const paces_params* p, std::string& why)
     if (p->taylor_tol < 0 || p->taylor_nmax < 0 || p->fixed_terms < 0) { why = "series limits"; return PACES_ERR_INVALID; }
     if (p->batch < 0 || p->batch > PACES_MAX_BATCH) { why = "batch out of range"; return PACES_ERR_INVALID; }
     if (!std::isfinite(p->taylor_xmax)) { why = "taylor_xmax"; return PACES_ERR_INVALID; }
+    if (p->propagator != PACES_TAYLOR && p->propagator != PACES_LANCZOS) { why = "propagator"; return PACES_ERR_INVALID; }
+    if (p->krylov_max < 0 || p->krylov_max > PACES_MAX_KRYLOV) { why = "krylov_max"; return PACES_ERR_INVALID; }
+    if (p->propagator == PACES_LANCZOS && (p->precision != PACES_C128 || p->batch > 1)) {
+        why = "the Lanczos propagator needs PACES_C128 and batch <= 1";
+        return PACES_ERR_INVALID;
+    }
     return PACES_OK;
 }
 
@@ -298,6 +304,12 @@ void free_rows(paces_t h)
 }
 
 // Allocate every row-sized buffer for cap rows; on failure frees what it got.
+// Krylov vectors the Lanczos propagator may hold per series.
+int krylov_dim(paces_t h) { return h->prm.krylov_max > 0 ? h->prm.krylov_max : 30; }
+
+// Key of the propagator kernel for occupancy queries.
+int prop_key(paces_t h) { return h->prm.propagator == PACES_LANCZOS ? kPrecLanczos : h->prm.precision; }
+
 paces_status alloc_rows(paces_t h, uint32_t cap, std::vector<DevAlloc>& out, Bufs& b)
 {
     std::vector<DevAlloc> saved;
@@ -329,6 +341,10 @@ paces_status alloc_rows(paces_t h, uint32_t cap, std::vector<DevAlloc>& out, Buf
         b.rperm = nullptr;
     }
     chk(b.cand_slot = alloc_track<uint32_t>(h, h->row_allocs, (size_t)cap * h->D));
+    if (h->prm.propagator == PACES_LANCZOS)
+        chk(b.kry = alloc_track<double2>(h, h->row_allocs, (size_t)cap * krylov_dim(h)));
+    else
+        b.kry = nullptr;
     // sort of the kept set: indices in the winner-mask buffer (free during
     // truncation); keys in the two term buffers when a key fits in 16 bytes
     if (h->W <= 2) {
@@ -491,6 +507,8 @@ TaylorParams taylor_params(paces_t h, double dt, int step)
     p.lpr = h->lpr;
     p.c64 = h->prm.precision == PACES_C64_SPMV;
     p.fmt = h->b.fmt;
+    p.lanczos = h->prm.propagator == PACES_LANCZOS;
+    p.kmax = krylov_dim(h);
     return p;
 }
 
@@ -695,7 +713,15 @@ void step_bytes(paces_t h, const double* r, double q_in, bool truncated, double*
         bytes[1] += q * (2.0 * W8 + 8.0 * h->D + 16.0) + newrows * (W8 + slot + 32.0 + 16.0);
     }
     bytes[2] += q * (W8 + 9.0) + nnz_off * 5.0 + q * h->D * 32.0;
-    if (terms >= 1) bytes[3] += q * 57.0 + nnz_off * 5.0 + (terms - 1) * (q * 73.0 + nnz_off * 5.0);
+    if (h->prm.propagator == PACES_LANCZOS) {
+        // per Krylov vector: pass A 1 + 8 + 16 (s_j) + 16 (t) per row and 5 per
+        // entry, pass B 3 x 16 read + 16 written; per series the combination
+        // reads its n vectors and writes r
+        double nsub = r[PACES_OBS_SUBSTEPS];
+        bytes[3] += terms * (q * 105.0 + nnz_off * 5.0) + q * 16.0 * (terms + nsub);
+    } else if (terms >= 1) {
+        bytes[3] += q * 57.0 + nnz_off * 5.0 + (terms - 1) * (q * 73.0 + nnz_off * 5.0);
+    }
     bytes[4] += q * (W8 + 16.0);
 }
 
@@ -882,7 +908,7 @@ paces_status paces_create(const paces_params* params, const paces_allocator* all
     b.batch = h->R;
     b.G = std::min(kMaxChunkBlocks, h->sms * 4);
     b.grid = h->sms * 8;
-    const int prec = h->prm.precision;
+    const int prec = prop_key(h);
     int bps = taylor_blocks_per_sm(h->lpr, prec);
     if (bps < 1) bps = 1;
     b.taylor_grid = h->sms * bps;
@@ -1280,7 +1306,8 @@ static paces_status step_impl(paces_t h, double dt, int64_t nsteps, double th2, 
             s = set_counters(h);
             if (s) return s;
             return fail(h, PACES_ERR_NOCONVERGE,
-                        "Taylor series not converged after " + std::to_string(nterm) + " terms at step " +
+                        std::string(h->prm.propagator == PACES_LANCZOS ? "Lanczos decomposition" : "Taylor series") +
+                            " not converged after " + std::to_string(nterm) + " terms at step " +
                             std::to_string(h->step_index));
         }
         h->has_state = false;
@@ -1304,6 +1331,64 @@ paces_status paces_step_nom(paces_t h, double dt, int64_t nsteps, int64_t q_nom,
     if (h->R > 1) return fail(h, PACES_ERR_UNSUPPORTED, "top-q_nom truncation covers batch 1 only");
     if (!h->has_state) return fail(h, PACES_ERR_STATE, "no state: call paces_set_state first");
     return step_impl(h, dt, nsteps, 0.0, q_nom, seed);
+}
+
+paces_status paces_set_coefficients(paces_t h, double J, const double* eps, const double* omega, const double* g)
+{
+    if (!h) return PACES_ERR_INVALID;
+    if (h->rec_every > 0)
+        return fail(h, PACES_ERR_UNSUPPORTED, "the reverse pass assumes one Hamiltonian for all recorded steps");
+    const int N = h->N;
+    std::vector<double> ne = h->eps, no = h->omega, ng = h->g;
+    if (eps) ne.assign(eps, eps + (size_t)N * h->R);
+    if (omega) no.assign(omega, omega + N);
+    if (g) ng.assign(g, g + N);
+    if (!std::isfinite(J)) return fail(h, PACES_ERR_INVALID, "J is not finite");
+    for (double v : ne)
+        if (!std::isfinite(v)) return fail(h, PACES_ERR_INVALID, "eps is not finite");
+    for (int j = 0; j < N; ++j) {
+        if (!std::isfinite(no[j]) || !std::isfinite(ng[j])) return fail(h, PACES_ERR_INVALID, "omega or g");
+        if ((ng[j] == 0.0) != (h->g[j] == 0.0))
+            return fail(h, PACES_ERR_INVALID, "g_s must stay zero exactly where it was (fixed move graph)");
+    }
+    if ((J == 0.0) != (h->prm.J == 0.0))
+        return fail(h, PACES_ERR_INVALID, "J must stay zero exactly when it was (fixed move graph)");
+    paces_params p = h->prm;
+    p.J = J;
+    p.eps = ne.data();
+    p.omega = no.data();
+    p.g = ng.data();
+    p.phonon_cap = h->cap.data();
+    p.J_explicit = h->Jx.empty() ? nullptr : h->Jx.data();
+    DevModel* M = new DevModel();
+    paces_status s = paces::fill_model(&p, h->lay, M);
+    if (s) {
+        delete M;
+        return fail(h, s, "the new coefficients do not fit the model tables");
+    }
+    if (M->D != h->D || M->P != h->P) {
+        delete M;
+        return fail(h, PACES_ERR_INVALID, "the move graph changed");
+    }
+    M->eps_b64 = h->hmodel->eps_b64;        // ensembles: the device site-energy arrays stay
+    M->eps_bdw = h->hmodel->eps_bdw;
+    std::vector<dwf> hd;
+    if (h->R > 1) {
+        hd.resize(ne.size());
+        for (size_t j = 0; j < hd.size(); ++j) hd[j] = dw_from_double(ne[j]);
+        CUDA_TRY(h, cudaMemcpyAsync((void*)M->eps_b64, ne.data(), ne.size() * 8, cudaMemcpyHostToDevice, h->st));
+        CUDA_TRY(h, cudaMemcpyAsync((void*)M->eps_bdw, hd.data(), hd.size() * sizeof(dwf), cudaMemcpyHostToDevice,
+                                    h->st));
+    }
+    CUDA_TRY(h, cudaMemcpyAsync((void*)h->b.model, M, sizeof(DevModel), cudaMemcpyHostToDevice, h->st));
+    CUDA_TRY(h, cudaStreamSynchronize(h->st));
+    delete h->hmodel;
+    h->hmodel = M;
+    h->prm.J = J;
+    h->eps.swap(ne);
+    h->omega.swap(no);
+    h->g.swap(ng);
+    return PACES_OK;
 }
 
 paces_status paces_num_rows(paces_t h, int64_t* rows)
@@ -1443,7 +1528,7 @@ paces_status paces_get_tuning(paces_t h, paces_tuning* out)
     out->grid_blocks_per_sm = h->b.grid / h->sms;
     out->chunk_blocks_per_sm = h->b.G / h->sms;
     out->use_graphs = h->use_graphs ? 1 : 0;
-    out->max_taylor_blocks_per_sm = taylor_blocks_per_sm(h->lpr, h->prm.precision);
+    out->max_taylor_blocks_per_sm = taylor_blocks_per_sm(h->lpr, prop_key(h));
     return PACES_OK;
 }
 
@@ -1454,7 +1539,7 @@ paces_status paces_set_tuning(paces_t h, const paces_tuning* in)
         return fail(h, PACES_ERR_STATE, "recorded steps must be replayed with the tuning they ran with");
     int lpr = in->taylor_lanes_per_row;
     if (lpr != 1 && lpr != 4 && lpr != 8) return fail(h, PACES_ERR_INVALID, "lanes per row must be 1, 4 or 8");
-    int maxb = taylor_blocks_per_sm(lpr, h->prm.precision);
+    int maxb = taylor_blocks_per_sm(lpr, prop_key(h));
     if (in->taylor_blocks_per_sm < 1 || in->taylor_blocks_per_sm > maxb)
         return fail(h, PACES_ERR_INVALID, "propagator blocks per SM must be 1.." + std::to_string(maxb));
     if (in->grid_blocks_per_sm < 1 || in->grid_blocks_per_sm > 32) return fail(h, PACES_ERR_INVALID, "grid blocks");
@@ -1549,6 +1634,8 @@ paces_status paces_record(paces_t h, int32_t ckpt_every)
     if (ckpt_every > 0 && h->R > 1) return fail(h, PACES_ERR_UNSUPPORTED, "the reverse pass covers batch 1 only");
     if (ckpt_every > 0 && h->prm.precision == PACES_C64_SPMV)
         return fail(h, PACES_ERR_UNSUPPORTED, "the reverse pass needs double-word or FP64 amplitudes");
+    if (ckpt_every > 0 && h->prm.propagator == PACES_LANCZOS)
+        return fail(h, PACES_ERR_UNSUPPORTED, "the reverse pass differentiates the Taylor propagator only");
     h->rec_every = ckpt_every;
     drop_recording(h);
     return PACES_OK;

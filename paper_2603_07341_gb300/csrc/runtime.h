@@ -60,6 +60,7 @@ struct Bufs {
     uint32_t* sorti[2];            // and their source rows
     uint32_t* rs_hist;             // digit counts per block [256][G]
     int key_bits[kMaxWords];       // bits used by each key word (radix passes)
+    double2* kry;                  // Lanczos basis: kmax vectors of cap_rows rows
     void* terms;                   // adjoint re-runs: Taylor terms phi_1.. [n][row], 16 bytes each
     int term_max;                  // terms storable
     uint64_t* masks;               // winner bits per frontier row
@@ -94,6 +95,8 @@ struct TaylorParams {
     int lpr;                        // lanes per row (1, 4 or 8)
     int c64;                        // complex64 SpMV terms
     int fmt;                        // amplitude storage: 0 double-word, 1 FP64
+    int lanczos;                    // Lanczos decomposition (App. C.3) instead of the series
+    int kmax;                       // Lanczos: most Krylov vectors per series
 };
 
 // Stage launchers; each returns the number of kernels it launched (or -1 on a
@@ -119,6 +122,8 @@ int launch_meta_from_keys(const Bufs& b, int gen, uint32_t n, cudaStream_t st);
 int launch_export_csr(const Bufs& b, uint32_t q, const uint64_t* off, int32_t* cols,
                       double* vals, cudaStream_t st);
 
+// Occupancy query key of the Lanczos propagator (precision values are 0..2).
+constexpr int kPrecLanczos = 16;
 int taylor_blocks_per_sm(int lpr, int precision);
 // Cooperative self-test of the bounded grid barrier (kern_taylor.cu).
 int launch_barrier_selftest(Counters* ctr, double* part, int grid, unsigned expect, unsigned long long timeout_ns,
