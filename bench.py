@@ -327,8 +327,8 @@ def run_trajectory(B, model, cfg, start_state, end, first_timed, K, barrier, clk
     sol.profile(False)
     stage_ms, launches, stage_bytes = sol.stage_stats(reset=True)
     return {"solver": sol, "ms": e0.elapsed_time(e1), "t_host": t_host, "all_units": all_units,
-            "rec": sol.observables(first_timed + 1, K), "stage_ms": stage_ms, "launches": launches,
-            "stage_bytes": stage_bytes}
+            "rec": sol.observables(first_timed + 1, K), "rec_all": sol.observables(0, sol.num_records()),
+            "stage_ms": stage_ms, "launches": launches, "stage_bytes": stage_bytes}
 
 
 def observable_errors(B, rec, ref, N, R_rec=1, R_ref=1, r_rec=0, r_ref=0):
@@ -348,25 +348,45 @@ def observable_errors(B, rec, ref, N, R_rec=1, R_ref=1, r_rec=0, r_ref=0):
     return out
 
 
+def spectrum_error(B, rec_all, ref_all, cfg):
+    """Largest |A(w) - A_ref(w)| over the spectrum grid (1024 points on [-6, 6]),
+    relative to max |A_ref|, of the absorption spectra of two whole
+    trajectories (records from step 0)."""
+    from paper_2603_07341_gb300.analysis import absorption_spectrum
+    w = np.linspace(-6.0, 6.0, 1024)
+    C = lambda r: r[:, B.OBS_FIELDS.index("C_re")] + 1j * r[:, B.OBS_FIELDS.index("C_im")]
+    A, Ar = absorption_spectrum(C(rec_all), cfg["dt"], w), absorption_spectrum(C(ref_all), cfg["dt"], w)
+    return float(np.max(np.abs(A - Ar)) / np.max(np.abs(Ar)))
+
+
 def compare_variants(B, args, cfg, model, start_state, end, first_timed, K, barrier, main):
     """The plain FP64 single-instance form next to the measured one: throughput
-    over the same timed window and the largest observable differences."""
+    over the same timed window, the largest observable differences over those
+    steps and the spectrum difference over the whole trajectory."""
     N = cfg["n_sites"]
     units = lambda rec: float(np.sum(rec[:, 9] * rec[:, 6]))
     out = {}
     R = int(model.get("batch", 1))
     if R == 1:
-        recs = {}
-        for name, p in (("c128", B.C128), ("c64", B.C64_SPMV), ("dw", B.DW)):
+        recs, alls = {}, {}
+        forms = [f for f in ("c128", "c64", "dw") if f == "c128" or f in args.compare_forms.split(",")]
+        prec = {"c128": B.C128, "c64": B.C64_SPMV, "dw": B.DW}
+        for name in forms:
+            p = prec[name]
             if p == model["precision"]:
-                recs[name] = main["rec"]
+                recs[name], alls[name] = main["rec"], main["rec_all"]
                 continue
             run = run_trajectory(B, dict(model, precision=p), cfg, start_state, end, first_timed, K, barrier)
             run["solver"].close()
-            recs[name] = run["rec"]
+            recs[name], alls[name] = run["rec"], run["rec_all"]
             out[name] = {"value": units(run["rec"]) / (run["ms"] / 1e3), "ms_per_step": run["ms"] / K}
-        for name in ("dw", "c64"):
-            out.setdefault(name, {})["max_abs_err_vs_c128"] = observable_errors(B, recs[name], recs["c128"], N)
+        for name in forms:
+            if name == "c128":
+                continue
+            d = out.setdefault(name, {})
+            d["max_abs_err_vs_c128"] = observable_errors(B, recs[name], recs["c128"], N)
+            d["max_abs_err_vs_c128_whole_run"] = observable_errors(B, alls[name][1:], alls["c128"][1:], N)
+            d["spectrum_rel_err_vs_c128"] = spectrum_error(B, alls[name], alls["c128"], cfg)
         out["reference_form"] = "c128: plain FP64 single instance, same steps"
         return out
     # ensemble: single-instance FP64 runs of a sample of realisations
@@ -384,6 +404,37 @@ def compare_variants(B, args, cfg, model, start_state, end, first_timed, K, barr
     out["max_abs_err_vs_single_c128"] = {k: max(e[k] for e in errs) for k in errs[0]}
     out["reference_form"] = "c128: plain FP64 single instance per realisation"
     return out
+
+
+def gradient_run(B, cfg, model, nsteps):
+    """Forward (recorded, checkpoints every ckpt_every steps) and reverse pass of
+    the whole trajectory for the loss L = P_0(T) + mean_w (A(w) - A_target(w))^2,
+    A_target the spectrum at seeded perturbed parameters; host-clock times of
+    both passes and the gradient dL/d[J, g, omega, eps_0 ..]."""
+    import torch
+    from paper_2603_07341_gb300 import autograd as AG
+    N = cfg["n_sites"]
+    base = dict(model)
+    p0 = np.concatenate([[cfg["J"], cfg["g"], cfg["omega"]], np.full(N, float(cfg["eps"]))])
+    start = W.start_state(cfg)
+    w = np.linspace(-6.0, 6.0, 1024)
+    ck = int(cfg.get("ckpt_every", 20))
+    A_t = AG.seeded_target(base, start, cfg["dt"], nsteps, cfg["theta"], w, p0)
+    p = torch.tensor(p0, dtype=torch.float64, requires_grad=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    L = AG.population_spectrum_loss(p, base, start, cfg["dt"], nsteps, cfg["theta"], w, A_t, ckpt_every=ck)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    L.backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    g = p.grad.numpy()
+    return {"steps": nsteps, "ckpt_every": ck, "loss": float(L.detach()), "forward_s": t1 - t0,
+            "backward_s": t2 - t1, "dL_dJ_g_omega": [float(x) for x in g[:3]],
+            "dL_deps_norm": float(np.linalg.norm(g[3:])),
+            "loss_form": "P_0(T) + mean over 1024 points on [-6, 6] of (A - A_target)^2, A_target at "
+                         "p0 (1 + 0.05 z), z seeded normal (seed 12345)"}
 
 
 def run_reference(args, cfg):
@@ -430,6 +481,11 @@ def main():
     ap.add_argument("--compare", action="store_true",
                     help="also time the plain FP64 single-instance form and report observable errors")
     ap.add_argument("--compare-sample", type=int, default=4)
+    ap.add_argument("--compare-forms", default="c64,dw", help="forms --compare runs next to c128")
+    ap.add_argument("--gradient", action="store_true",
+                    help="also time the reverse pass of the whole trajectory (workloads with ckpt_every): "
+                         "the site-0 population at T plus the spectrum mean squared error against a seeded "
+                         "target, through autograd.population_spectrum_loss")
     ap.add_argument("--replicas", action="store_true",
                     help="ensembles under several ranks: every rank runs all realisations instead of a block")
     args = ap.parse_args()
@@ -540,6 +596,9 @@ def main():
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.workload, args.cpu_budget)
 
+    grad = None
+    if args.gradient and rank == 0:
+        grad = gradient_run(B, cfg, model, end)
     variants = None
     if args.compare:
         sol.close()
@@ -580,6 +639,8 @@ def main():
             line["config"]["units"] = "rows of all realisations x Taylor terms"
         if variants is not None:
             line["variants"] = variants
+        if grad is not None:
+            line["gradient"] = grad
         if ens is not None:
             line["ensemble"] = ens
         print(json.dumps(line))

@@ -344,7 +344,13 @@ typedef struct {
     int32_t use_graphs;               /* 1: every step is captured once as a CUDA graph and   */
                                       /* replayed (not while stage timing is on)              */
     int32_t max_taylor_blocks_per_sm; /* read only: co-residency limit of the propagator      */
-    int32_t reserved[2];
+    int32_t table_load_pct;           /* largest load of the hash tables in percent, 20..80   */
+                                      /* (slots = rows of capacity x 100 / pct + 1; default   */
+                                      /* 50); 0 keeps it.  Takes effect when the tables are   */
+                                      /* next allocated: the next paces_set_state or          */
+                                      /* paces_load_state, or capacity growth.  CAPACITY when */
+                                      /* a table would need 2^31 slots or more.               */
+    int32_t reserved;
 } paces_tuning;
 paces_status paces_get_tuning(paces_t h, paces_tuning* out);
 paces_status paces_set_tuning(paces_t h, const paces_tuning* in);

@@ -2,7 +2,8 @@
 
 It times a few steps for each candidate setting of the knobs exposed by
 paces_set_tuning (lanes per row and blocks per SM of the propagator, blocks per
-SM of the grid-stride and scan-based kernels, graph replay of whole steps),
+SM of the grid-stride and scan-based kernels, graph replay of whole steps, the
+largest load of the hash tables, which sets their size and probe lengths),
 always from the same exported state (reloaded with paces_load_state before
 every trial), and keeps the fastest setting by coordinate descent.  Choices are
 cached in a JSON file keyed by the device name and the model's shape, so later
@@ -77,7 +78,8 @@ def autotune(solver, model, dt, theta, steps=3, cache_path=DEFAULT_CACHE, use_ca
         return _time_steps(solver, state, dt, theta, steps)
 
     for knob, values in (("taylor_lanes_per_row", lanes), ("grid_blocks_per_sm", [4, 8, 16]),
-                         ("chunk_blocks_per_sm", [2, 4, 6]), ("use_graphs", [0, 1])):
+                         ("chunk_blocks_per_sm", [2, 4, 6]), ("use_graphs", [0, 1]),
+                         ("table_load_pct", [35, 50, 65])):
         for v in values:
             if best.get(knob) == v:
                 continue

@@ -59,7 +59,7 @@ class Tuning(C.Structure):
     _fields_ = [("taylor_lanes_per_row", C.c_int32), ("taylor_blocks_per_sm", C.c_int32),
                 ("grid_blocks_per_sm", C.c_int32), ("chunk_blocks_per_sm", C.c_int32),
                 ("use_graphs", C.c_int32), ("max_taylor_blocks_per_sm", C.c_int32),
-                ("reserved", C.c_int32 * 2)]
+                ("table_load_pct", C.c_int32), ("reserved", C.c_int32)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)

@@ -455,7 +455,40 @@ __device__ __forceinline__ void cas128(uint64_t* p, uint64_t cmp_lo, uint64_t cm
         : "memory");
 }
 
-// Read-only lookup: row of key or -1.
+// A slot's tag and key words, read with independent 16-byte loads (a slot of
+// kWords 64-bit words is 16-byte aligned), so that a probe is one round trip.
+template <int W>
+struct SlotVal {
+    uint64_t w[Slot<W>::kWords];
+};
+
+// RO: the table does not change while the kernel runs (the read-only path
+// may then keep a probed line in L1 for the next slot of the probe).
+template <int W, bool RO>
+__device__ __forceinline__ SlotVal<W> read_slot(const uint64_t* __restrict__ sl)
+{
+    SlotVal<W> v;
+#pragma unroll
+    for (int i = 0; i < Slot<W>::kWords / 2; ++i) {
+        const ulonglong2* a = reinterpret_cast<const ulonglong2*>(sl) + i;
+        const ulonglong2 p = RO ? __ldg(a) : __ldcg(a);
+        v.w[2 * i] = p.x;
+        v.w[2 * i + 1] = p.y;
+    }
+    return v;
+}
+
+template <int W>
+__device__ __forceinline__ bool slot_has_key(const SlotVal<W>& v, const Key<W>& key)
+{
+    bool eq = true;
+#pragma unroll
+    for (int i = 0; i < W; ++i) eq &= (v.w[1 + i] == key.w[i]);
+    return eq;
+}
+
+// Read-only lookup in a table whose entries are final (every slot holds a
+// row's tag and key): row of key or -1.
 template <int W>
 __device__ __forceinline__ int64_t table_lookup(const uint64_t* __restrict__ table, uint64_t slots,
                                                 const Key<W>& key)
@@ -464,15 +497,9 @@ __device__ __forceinline__ int64_t table_lookup(const uint64_t* __restrict__ tab
     uint64_t fp = fingerprint<W>(h);
     uint64_t pos = slot_home(h, slots);
     for (uint32_t probe = 0; probe < kMaxProbe; ++probe) {
-        const uint64_t* sl = table + pos * Slot<W>::kWords;
-        uint64_t tag = __ldg(sl);
-        if (tag == kEmpty) return -1;
-        if ((tag >> 32) == fp) {
-            bool eq = true;
-#pragma unroll
-            for (int i = 0; i < W; ++i) eq &= (__ldg(sl + 1 + i) == key.w[i]);
-            if (eq) return (int64_t)(uint32_t)tag;
-        }
+        const SlotVal<W> v = read_slot<W, true>(table + pos * Slot<W>::kWords);
+        if (v.w[0] == kEmpty) return -1;
+        if ((v.w[0] >> 32) == fp && slot_has_key<W>(v, key)) return (int64_t)(uint32_t)v.w[0];
         pos = slot_next(pos, slots);
     }
     return -1;

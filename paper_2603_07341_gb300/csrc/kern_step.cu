@@ -208,7 +208,8 @@ __device__ __forceinline__ uint32_t insert_candidate(const DevModel* __restrict_
     return kNone;
 }
 
-// Read-only lookup continuing from a loaded home slot: row of key or -1.
+// Lookup continuing from a loaded home slot in a table that does not change
+// while the kernel runs (the previous step's): row of key or -1.
 template <int W>
 __device__ __forceinline__ int64_t lookup_from(const uint64_t* __restrict__ table, uint64_t slots, const Key<W>& key,
                                                const Probe& pr)
@@ -218,11 +219,11 @@ __device__ __forceinline__ int64_t lookup_from(const uint64_t* __restrict__ tabl
         const uint64_t* sl = table + pos * Slot<W>::kWords;
         uint64_t tag, kw;
         if constexpr (W == 1) {
-            ulonglong2 s2 = probe == 0 ? make_ulonglong2(pr.tag, pr.kw) : __ldcg(reinterpret_cast<const ulonglong2*>(sl));
+            ulonglong2 s2 = probe == 0 ? make_ulonglong2(pr.tag, pr.kw) : __ldg(reinterpret_cast<const ulonglong2*>(sl));
             tag = s2.x;
             kw = s2.y;
         } else {
-            tag = probe == 0 ? pr.tag : __ldcg(sl);
+            tag = probe == 0 ? pr.tag : __ldg(sl);
             kw = kEmpty;
         }
         if (tag == kEmpty) return -1;
@@ -233,7 +234,7 @@ __device__ __forceinline__ int64_t lookup_from(const uint64_t* __restrict__ tabl
             } else {
                 eq = true;
 #pragma unroll
-                for (int i = 0; i < W; ++i) eq &= (__ldcg(sl + 1 + i) == key.w[i]);
+                for (int i = 0; i < W; ++i) eq &= (__ldg(sl + 1 + i) == key.w[i]);
             }
             if (eq) return (int64_t)(uint32_t)tag;
         }

@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(kBlock) k_row_order(const Counters* __restrict
 // phi_1.. of the first series, then for each later series its input and its
 // terms (16 bytes per row each).
 template <int LPR>
-__global__ void __launch_bounds__(kBlock) k_taylor_f64(TaylorArgs a)
+__global__ void __launch_bounds__(kBlock, LPR == 1 ? 4 : 1) k_taylor_f64(TaylorArgs a)
 {
     __shared__ double coef[kMaxCoefs];
     __shared__ double tsh[4];
@@ -264,12 +264,22 @@ __global__ void __launch_bounds__(kBlock) k_taylor_f64(TaylorArgs a)
     double E = 0.0, n0 = 0.0;
     int total = 0, slot = 0, bar = 0;
     bool conv = true;
+    // r is updated at even n with both terms of the pair (n - 1, n); a series
+    // that stops at an odd n leaves r += i pend_s psi_n (pend_y) to be added
+    const double2* pend_y = nullptr;
+    const double2* pend_b = nullptr;                // r, or v when the series stopped at n = 1
+    double pend_s = 0.0;
     for (int j = 0; j < nsub && conv; ++j) {
         const double2* x = a.c_in;
         double2* y = a.ta;
         if (j > 0) {
             for (uint32_t row = blockIdx.x * blockDim.x + threadIdx.x; row < q; row += G * blockDim.x) {
-                double2 v = a.r[row];
+                double2 v = pend_y ? pend_b[row] : a.r[row];
+                if (pend_y) {
+                    const double2 pv = pend_y[row];
+                    v.x = fma(-pend_s, pv.y, v.x);
+                    v.y = fma(pend_s, pv.x, v.y);
+                }
                 a.ta[row] = v;
                 if (store && slot < a.term_max) store[(size_t)slot * q + row] = v;
             }
@@ -283,10 +293,14 @@ __global__ void __launch_bounds__(kBlock) k_taylor_f64(TaylorArgs a)
             x = a.ta;
             y = a.tb;
         }
+        pend_y = nullptr;
+        const double2* vin = x;                     // the series' input v
+        const double2* last = nullptr;              // buffer holding psi_nd
         double nin = 0.0, cn = 1.0;                 // cn = 1 / n!
         int nd = 0;
         bool cj = fixed > 0;
         for (int n = 1; n <= nlimit; ++n) {
+            const double cprev = cn;                 // 1 / (n - 1)!
             cn = cn / (double)n;
             const int L = -ilogb(cn);                // 2^(L-1) < n! <= 2^L
             const double corr = ldexp(cn, L);        // 2^L / n!, in [1, 2)
@@ -294,6 +308,8 @@ __global__ void __launch_bounds__(kBlock) k_taylor_f64(TaylorArgs a)
             const int ph = n & 3;
             const double sr = ph == 0 ? cn : (ph == 2 ? -cn : 0.0);
             const double si = ph == 1 ? -cn : (ph == 3 ? cn : 0.0);
+            // n even: (-i)^(n-1) = i sip
+            const double sip = ph == 2 ? -cprev : cprev;
             const bool first = (j == 0 && n == 1);
             float phi2 = 0.f;
             double acc_e = 0.0, acc_n = 0.0;
@@ -302,7 +318,7 @@ __global__ void __launch_bounds__(kBlock) k_taylor_f64(TaylorArgs a)
             auto load_row = [&](uint32_t row, double2& xi, double& d, double2& rr) {
                 xi = x[row];
                 d = first ? a.diag[row] : a.diag_h[row];
-                rr = (n == 1) ? xi : a.r[row];
+                if (!odd) rr = (n == 2) ? vin[row] : a.r[row];
             };
             auto finish_row = [&](uint32_t row, double2 yv, double2 xi, double d, double2 rr) {
                 if (first) {
@@ -312,15 +328,13 @@ __global__ void __launch_bounds__(kBlock) k_taylor_f64(TaylorArgs a)
                 yv.x = fma(d, xi.x, yv.x);
                 yv.y = fma(d, xi.y, yv.y);                // psi_n = B x
                 y[row] = yv;
-                // r += (sr + i si) psi_n: one of sr, si is zero (n odd: sr)
-                if (odd) {
-                    rr.x = fma(-si, yv.y, rr.x);
-                    rr.y = fma(si, yv.x, rr.y);
-                } else {
-                    rr.x = fma(sr, yv.x, rr.x);
-                    rr.y = fma(sr, yv.y, rr.y);
+                // n even: r += i sip psi_{n-1} + sr psi_n (x holds psi_{n-1});
+                // r is neither read nor written at odd n
+                if (!odd) {
+                    rr.x = fma(sr, yv.x, fma(-sip, xi.y, rr.x));
+                    rr.y = fma(sr, yv.y, fma(sip, xi.x, rr.y));
+                    a.r[row] = rr;
                 }
-                a.r[row] = rr;
                 if (store && slot < a.term_max)
                     store[(size_t)slot * q + row] = make_double2(sr * yv.x - si * yv.y, sr * yv.y + si * yv.x);
                 float p0 = mag_scaled_f32(yv.x, L), p1 = mag_scaled_f32(yv.y, L);
@@ -404,6 +418,7 @@ __global__ void __launch_bounds__(kBlock) k_taylor_f64(TaylorArgs a)
             if (threadIdx.x < 4) tsh[threadIdx.x] = __ldcg(tot + threadIdx.x);
             __syncthreads();
             nd = n;
+            last = y;
             if (n == 1) {
                 nin = tsh[2];
                 if (j == 0) {
@@ -422,6 +437,20 @@ __global__ void __launch_bounds__(kBlock) k_taylor_f64(TaylorArgs a)
         total += nd;
         if (blockIdx.x == 0 && threadIdx.x == 0) ctr->sub_terms[j] = nd;
         conv = cj;
+        if (nd & 1) {                               // (-i)^nd / nd! = i pend_s
+            pend_y = last;
+            pend_b = nd == 1 ? vin : a.r;
+            pend_s = (nd & 3) == 1 ? -cn : cn;
+        }
+    }
+    if (pend_y && conv) {                           // the last series stopped at an odd n
+        for (uint32_t row = blockIdx.x * blockDim.x + threadIdx.x; row < q; row += G * blockDim.x) {
+            double2 v = pend_b[row];
+            const double2 pv = pend_y[row];
+            v.x = fma(-pend_s, pv.y, v.x);
+            v.y = fma(pend_s, pv.x, v.y);
+            a.r[row] = v;
+        }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         ctr->nterms = total;

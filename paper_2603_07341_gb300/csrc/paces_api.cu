@@ -62,6 +62,7 @@ struct paces_handle {
     paces_layout lay;
     DevModel* hmodel = nullptr;   // host copy
     int W = 1, D = 4, P = 4, N = 1, lpr = 1, R = 1;
+    int table_pct = 50;                    // largest hash-table load, percent
     paces_allocator alloc{};
     bool has_alloc = false;
     cudaStream_t st = nullptr;
@@ -303,18 +304,22 @@ void free_rows(paces_t h)
     h->row_allocs.clear();
 }
 
-// Allocate every row-sized buffer for cap rows; on failure frees what it got.
 // Krylov vectors the Lanczos propagator may hold per series.
 int krylov_dim(paces_t h) { return h->prm.krylov_max > 0 ? h->prm.krylov_max : 30; }
 
 // Key of the propagator kernel for occupancy queries.
 int prop_key(paces_t h) { return h->prm.propagator == PACES_LANCZOS ? kPrecLanczos : h->prm.precision; }
 
+// Allocate every row-sized buffer for cap rows; on failure frees what it got.
+
 paces_status alloc_rows(paces_t h, uint32_t cap, std::vector<DevAlloc>& out, Bufs& b)
 {
     std::vector<DevAlloc> saved;
     saved.swap(h->row_allocs);
-    uint64_t slots = 2ull * cap + 1;           // load factor <= 0.5, any size below 2^32
+    // load factor <= table_pct / 100; slot indices must stay below 2^31 (a
+    // candidate slot shares its 32-bit word with the kCand flag)
+    uint64_t slots = (uint64_t)cap * 100 / (uint64_t)h->table_pct + 1;
+    if (slots >= (1ull << 31)) return PACES_ERR_CAPACITY;
     size_t sw = slot_words(h->W);
     bool ok = true;
     auto chk = [&](void* p) { ok = ok && p; };
@@ -1067,6 +1072,22 @@ static paces_status upload_rows(paces_t h, int64_t n, const std::vector<uint64_t
     if ((uint64_t)n * 2 > h->cap_rows) {
         paces_status s = grow(h, (uint64_t)n * 2, 0, 0);
         if (s) return s;
+    } else if (h->b.table_slots != (uint64_t)h->cap_rows * 100 / (uint64_t)h->table_pct + 1) {
+        // a new table load: the same capacity with tables of the new size (the
+        // state is replaced below, so nothing is kept)
+        free_rows(h);
+        Bufs nb = h->b;
+        std::vector<DevAlloc> na;
+        if (alloc_rows(h, h->cap_rows, na, nb) != PACES_OK) {
+            h->has_state = false;
+            h->cap_rows = 0;
+            paces_status s = grow(h, (uint64_t)n * 2, 0, 0);
+            if (s) return s;
+        } else {
+            h->row_allocs.swap(na);
+            h->b = nb;
+            invalidate_graphs(h);
+        }
     }
     h->gen = 0;
     paces_status s = clear_table(h, 0);
@@ -1529,6 +1550,7 @@ paces_status paces_get_tuning(paces_t h, paces_tuning* out)
     out->chunk_blocks_per_sm = h->b.G / h->sms;
     out->use_graphs = h->use_graphs ? 1 : 0;
     out->max_taylor_blocks_per_sm = taylor_blocks_per_sm(h->lpr, prop_key(h));
+    out->table_load_pct = h->table_pct;
     return PACES_OK;
 }
 
@@ -1545,6 +1567,9 @@ paces_status paces_set_tuning(paces_t h, const paces_tuning* in)
     if (in->grid_blocks_per_sm < 1 || in->grid_blocks_per_sm > 32) return fail(h, PACES_ERR_INVALID, "grid blocks");
     if (in->chunk_blocks_per_sm < 1 || in->chunk_blocks_per_sm * h->sms > kMaxChunkBlocks)
         return fail(h, PACES_ERR_INVALID, "chunk blocks");
+    if (in->table_load_pct != 0 && (in->table_load_pct < 20 || in->table_load_pct > 80))
+        return fail(h, PACES_ERR_INVALID, "table load must be 20..80 percent");
+    if (in->table_load_pct != 0) h->table_pct = in->table_load_pct;
     h->lpr = lpr;
     h->b.taylor_grid = h->sms * in->taylor_blocks_per_sm;
     h->b.grid = h->sms * in->grid_blocks_per_sm;

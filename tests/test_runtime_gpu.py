@@ -52,6 +52,26 @@ def test_tuning_knobs_keep_results(libpaces):
     assert np.max(np.abs(aa - ab)) <= 1e-13 * np.linalg.norm(aa)
 
 
+@pytest.mark.parametrize("pct", [25, 70])
+def test_table_load_keeps_results_bitwise(libpaces, pct):
+    """The hash tables' size (their largest load) changes slot positions only:
+    rows, their order and the amplitudes stay bit for bit, through capacity
+    growth from a small start."""
+    cfg = W.WORKLOADS["ring16"]
+    a = solver(cfg, max_rows=64)
+    b = B.Solver(**W.model_kwargs(cfg), max_rows=64)
+    b.set_tuning(table_load_pct=pct)
+    b.set_state(*W.start_state(cfg))
+    assert b.tuning()["table_load_pct"] == pct
+    with pytest.raises(B.PacesError):
+        b.set_tuning(table_load_pct=10)
+    for s in (a, b):
+        s.step(cfg["dt"], 40, cfg["theta"])
+    ta, aa = a.tuples()
+    tb, ab = b.tuples()
+    assert np.array_equal(ta, tb) and np.array_equal(aa, ab)
+
+
 def test_autotuner_picks_valid_settings(libpaces, tmp_path):
     cfg = W.WORKLOADS["ring16"]
     model = W.model_kwargs(cfg)
@@ -62,6 +82,7 @@ def test_autotuner_picks_valid_settings(libpaces, tmp_path):
     best, ms = autotune.autotune(s, model, cfg["dt"], cfg["theta"], steps=2,
                                  cache_path=str(tmp_path / "tune.json"))
     assert ms > 0 and best["taylor_lanes_per_row"] in (1, 4, 8)
+    assert best["table_load_pct"] in (35, 50, 65)
     assert (tmp_path / "tune.json").exists()
     s.step(cfg["dt"], 5, cfg["theta"])
     ref.step(cfg["dt"], 5, cfg["theta"])
