@@ -379,7 +379,7 @@ __device__ __forceinline__ bool apply_move(const DevModel* M, const Key<W>& k,
         return true;
     }
     if (!M->gnz[s]) return false;
-    int w = M->site_word[s];
+    const int w = W == 1 ? 0 : M->site_word[s];
     if (mv == deg) {
         if (ns >= M->cap[s]) return false;
         child.w[w] = k.w[w] + M->stride[s];

@@ -350,7 +350,10 @@ __global__ void __launch_bounds__(kBlock) k_level_insert(const DevModel* __restr
     }
     constexpr int kCPT = W == 1 ? kCPT1 : 2;
     const uint32_t nc = (uint32_t)ncand, stride = gridDim.x * blockDim.x;
-    for (uint32_t c0 = blockIdx.x * blockDim.x + threadIdx.x; c0 < nc; c0 += stride * kCPT) {
+    // every lane of a warp runs the same number of rounds (the lockstep
+    // insertion votes over the whole warp); lanes past nc have no candidates
+    for (uint32_t cw = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); cw < nc; cw += stride * kCPT) {
+        const uint32_t c0 = cw + (threadIdx.x & 31u);
         Key<W> child[kCPT];
         Probe pb[kCPT] = {};
         uint32_t pp[kCPT];
@@ -423,6 +426,10 @@ __global__ void __launch_bounds__(kBlock) k_level_flags(const DevModel* __restri
 }
 
 // New rows in candidate order: key, descriptor, table slot (key words + row).
+// The winners of each round of kBlock candidates (a minority: most candidates
+// meet a row or another candidate of their key) are queued in shared memory in
+// candidate order and written out once kBlock of them are pending, so that
+// every lane of a warp builds a row instead of the few that won their round.
 template <int W>
 __global__ void __launch_bounds__(kBlock) k_level_scatter(const DevModel* __restrict__ M, Counters* ctr, int f,
                                                           uint64_t* keys, uint32_t* meta, uint64_t* table,
@@ -430,29 +437,26 @@ __global__ void __launch_bounds__(kBlock) k_level_scatter(const DevModel* __rest
                                                           const uint32_t* __restrict__ wmask,
                                                           const uint32_t* __restrict__ blk_off)
 {
+    __shared__ uint32_t qc[2 * kBlock];
     if (ctr->err) return;
     uint32_t lo0 = ctr->level_off[f], base_row = ctr->level_off[f + 1];
     const int D = M->D;
     uint32_t NC = (base_row - lo0) * (uint32_t)D, lo, hi;
     chunk_of(NC, gridDim.x, blockIdx.x, lo, hi);
     uint32_t run = blk_off[blockIdx.x];
-    for (uint32_t base = lo; base < hi; base += kBlock) {
-        uint32_t c = base + threadIdx.x;
-        uint32_t w0 = base + (threadIdx.x & ~31u);
-        uint32_t bal = (w0 < hi) ? wmask[w0 >> 5] : 0u;
-        bool win = (c < hi) && ((bal >> (threadIdx.x & 31)) & 1u);
-        uint32_t tot;
-        uint32_t r = block_excl_scan<kBlock>(win ? 1u : 0u, &tot);
-        if (win) {
+    uint32_t pending = 0;
+    auto write_rows = [&](uint32_t n) {
+        for (uint32_t i = threadIdx.x; i < n; i += kBlock) {
+            const uint32_t c = qc[i];
             uint32_t p;
             int mv;
             cand_parent(M, c, lo0, p, mv);
-            Key<W> k = load_key<W>(keys, p);
-            uint32_t pm = meta[p];
+            const Key<W> k = load_key<W>(keys, p);
+            const uint32_t pm = meta[p];
             Key<W> child;
             int cid;
             apply_move<W>(M, k, meta_s(pm), meta_ns(pm), mv, child, cid);
-            uint32_t row = base_row + run + r;
+            const uint32_t row = base_row + run + i;
             store_key<W>(keys, row, child);
             meta[row] = child_meta<W>(M, k, pm, mv);
             uint64_t* sl = table + (uint64_t)cand_slot[(uint64_t)p * D + mv] * Slot<W>::kWords;
@@ -466,7 +470,27 @@ __global__ void __launch_bounds__(kBlock) k_level_scatter(const DevModel* __rest
                 sl[0] = tag;
             }
         }
-        run += tot;
+    };
+    for (uint32_t base = lo; base < hi; base += kBlock) {
+        uint32_t c = base + threadIdx.x;
+        uint32_t w0 = base + (threadIdx.x & ~31u);
+        uint32_t bal = (w0 < hi) ? wmask[w0 >> 5] : 0u;
+        bool win = (c < hi) && ((bal >> (threadIdx.x & 31)) & 1u);
+        uint32_t tot;
+        uint32_t r = block_excl_scan<kBlock>(win ? 1u : 0u, &tot);
+        if (win) qc[pending + r] = c;
+        pending += tot;
+        if (pending >= kBlock) {
+            __syncthreads();
+            write_rows(pending);
+            run += pending;
+            pending = 0;
+            __syncthreads();
+        }
+    }
+    if (pending) {
+        __syncthreads();
+        write_rows(pending);
     }
 }
 
@@ -688,6 +712,149 @@ __global__ void __launch_bounds__(kBlock) k_csr_grp(const DevModel* __restrict__
             hb = b > hb ? b : hb;
             nnz += e;
         }
+    }
+    hbound_publish(ctr, hb);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nnz += __shfl_xor_sync(0xffffffffu, nnz, o);
+    if ((threadIdx.x & 31) == 0 && nnz) atomicAdd(&ctr->nnz, nnz);
+}
+
+// One thread per row for models of at most DM (4 or 8) moves per state: every
+// lane runs the same instructions for its own row.  Rows of the expanded
+// levels read their D recorded slots (one vector load) and then, all together,
+// the tags of the slots they name; rows of the last level look their D images
+// up in lockstep rounds (every unresolved image's slot read in the same round,
+// one 16-byte-aligned read per slot), so a warp keeps 32 D probes in flight.
+template <int W, int DM>
+__global__ void __launch_bounds__(kBlock) k_csr_row(const DevModel* __restrict__ M, Counters* ctr,
+                                                    const uint64_t* __restrict__ keys,
+                                                    const uint32_t* __restrict__ meta,
+                                                    const uint64_t* __restrict__ table, uint64_t slots,
+                                                    const uint32_t* __restrict__ cand_slot,
+                                                    uint32_t* __restrict__ col, uint8_t* __restrict__ cidv,
+                                                    uint8_t* __restrict__ cnt, double* __restrict__ diag)
+{
+    if (ctr->err) return;
+    const uint32_t q = ctr->q, lim = ctr->level_off[ctr->nlevels - 1];
+    const int D = M->D, P = M->P;
+    unsigned long long nnz = 0, hb = 0;
+    const uint32_t nthr = gridDim.x * blockDim.x;
+    for (uint32_t rb = blockIdx.x * blockDim.x; rb < q; rb += nthr) {
+        const uint32_t row = rb + threadIdx.x;
+        const bool valid = row < q;
+        Key<W> k;
+#pragma unroll
+        for (int i = 0; i < W; ++i) k.w[i] = 0;
+        uint32_t m = 0;
+        if (valid) {
+            k = load_key<W>(keys, row);
+            m = meta[row];
+        }
+        const int s = meta_s(m), ns = meta_ns(m);
+        Key<W> child[DM];
+        int cid[DM];
+        unsigned ok = 0, found = 0;
+        uint32_t colv[DM];
+#pragma unroll
+        for (int mv = 0; mv < DM; ++mv) {
+            cid[mv] = 0;
+            colv[mv] = 0;
+            if (valid && mv < D && apply_move<W>(M, k, s, ns, mv, child[mv], cid[mv])) ok |= 1u << mv;
+        }
+        // expanded levels: the slot (or kCand | row) every move recorded; the
+        // rows of one warp may lie on both sides of lim, so both parts run as
+        // predicated code and the lockstep loop below is entered by every lane
+        const bool expanded = row < lim;
+        {
+            uint32_t sl[DM];
+            const uint64_t cb = (uint64_t)row * D;
+            if (DM == 4 && D == 4 && valid && expanded) {
+                const uint4 v = *reinterpret_cast<const uint4*>(cand_slot + cb);
+                sl[0] = v.x; sl[1] = v.y; sl[2] = v.z; sl[3] = v.w;
+            } else {
+#pragma unroll
+                for (int mv = 0; mv < DM; ++mv)
+                    sl[mv] = (expanded && ((ok >> mv) & 1u)) ? cand_slot[cb + mv] : kNone;
+            }
+            uint64_t tg[DM];
+#pragma unroll
+            for (int mv = 0; mv < DM; ++mv) {       // every slot's tag in flight at once
+                tg[mv] = 0;
+                if (expanded && ((ok >> mv) & 1u) && sl[mv] != kNone && !(sl[mv] & kCand))
+                    tg[mv] = __ldg(table + (uint64_t)sl[mv] * Slot<W>::kWords);
+            }
+#pragma unroll
+            for (int mv = 0; mv < DM; ++mv) {
+                if (!expanded || !((ok >> mv) & 1u) || sl[mv] == kNone) continue;
+                colv[mv] = (sl[mv] & kCand) ? (sl[mv] & ~kCand) : (uint32_t)tg[mv];
+                found |= 1u << mv;
+            }
+        }
+        {
+            // last level: lockstep lookups of the images
+            uint64_t pos[DM], fp[DM];
+            unsigned act = expanded ? 0u : ok;
+#pragma unroll
+            for (int mv = 0; mv < DM; ++mv) {
+                pos[mv] = 0;
+                fp[mv] = 0;
+                if ((act >> mv) & 1u) {
+                    const uint64_t hsh = key_hash<W>(child[mv]);
+                    fp[mv] = fingerprint<W>(hsh);
+                    pos[mv] = slot_home(hsh, slots);
+                }
+            }
+            for (uint32_t round = 0; round < kMaxProbe && __any_sync(0xffffffffu, act != 0); ++round) {
+                SlotVal<W> v[DM];
+#pragma unroll
+                for (int mv = 0; mv < DM; ++mv)     // every unresolved image's slot in flight at once
+                    if ((act >> mv) & 1u) v[mv] = read_slot<W, true>(table + pos[mv] * Slot<W>::kWords);
+#pragma unroll
+                for (int mv = 0; mv < DM; ++mv) {
+                    if (!((act >> mv) & 1u)) continue;
+                    if (v[mv].w[0] == kEmpty) {
+                        act &= ~(1u << mv);          // not in H_eff
+                    } else if ((v[mv].w[0] >> 32) == fp[mv] && slot_has_key<W>(v[mv], child[mv])) {
+                        colv[mv] = (uint32_t)v[mv].w[0];
+                        found |= 1u << mv;
+                        act &= ~(1u << mv);
+                    } else {
+                        pos[mv] = slot_next(pos[mv], slots);
+                    }
+                }
+            }
+        }
+        if (!valid) continue;
+        // entries in move order, compacted
+        const uint64_t rbase = (uint64_t)row * P;
+        int e = 0;
+        if (P == 4 && DM == 4) {
+            uint32_t cc[4] = {0, 0, 0, 0}, ii = 0;
+#pragma unroll
+            for (int mv = 0; mv < DM; ++mv)
+                if ((found >> mv) & 1u) {
+#pragma unroll
+                    for (int t = 0; t < 4; ++t)
+                        if (t == e) cc[t] = colv[mv];
+                    ii |= (uint32_t)cid[mv] << (8 * e);
+                    ++e;
+                }
+            *reinterpret_cast<uint4*>(col + rbase) = make_uint4(cc[0], cc[1], cc[2], cc[3]);
+            *reinterpret_cast<uint32_t*>(cidv + rbase) = ii;
+        } else {
+#pragma unroll
+            for (int mv = 0; mv < DM; ++mv)
+                if ((found >> mv) & 1u) {
+                    col[rbase + e] = colv[mv];
+                    cidv[rbase + e] = (uint8_t)cid[mv];
+                    ++e;
+                }
+        }
+        cnt[row] = (uint8_t)e;
+        store_diag(M, diag, row, row_diag<W>(M, k, s, meta_nph(m)));
+        const unsigned long long b = row_hbound<W>(M, k, s, ns, meta_nph(m));
+        hb = b > hb ? b : hb;
+        nnz += e;
     }
     hbound_publish(ctr, hb);
 #pragma unroll
@@ -1176,7 +1343,10 @@ static int csr_w(const Bufs& b, int gen, cudaStream_t st)
         b.diag
     // the row bound is a maximum over this build's rows only
     cudaMemsetAsync(reinterpret_cast<char*>(b.ctr) + offsetof(Counters, hbound), 0, sizeof(unsigned long long), st);
-    if (b.D <= 4) k_csr_grp<W, 4><<<b.grid, kBlock, 0, st>>>(PACES_CSR_ARGS);
+    // one-word keys: one thread per row (the per-row key images fit in registers)
+    if (W == 1 && b.D <= 4) k_csr_row<1, 4><<<b.grid, kBlock, 0, st>>>(PACES_CSR_ARGS);
+    else if (W == 1 && b.D <= 8) k_csr_row<1, 8><<<b.grid, kBlock, 0, st>>>(PACES_CSR_ARGS);
+    else if (b.D <= 4) k_csr_grp<W, 4><<<b.grid, kBlock, 0, st>>>(PACES_CSR_ARGS);
     else if (b.D <= 8) k_csr_grp<W, 8><<<b.grid, kBlock, 0, st>>>(PACES_CSR_ARGS);
     else if (b.D <= 16) k_csr_grp<W, 16><<<b.grid, kBlock, 0, st>>>(PACES_CSR_ARGS);
     else if (b.D <= 32) k_csr_grp<W, 32><<<b.grid, kBlock, 0, st>>>(PACES_CSR_ARGS);
