@@ -1041,6 +1041,118 @@ __global__ void __launch_bounds__(kBlock) k_obs_accum(const DevModel* __restrict
     }
 }
 
+// floor(w 2^84) = hi 2^32 + lo for 0 <= w < 2^32, from the bits of w with
+// integer operations only (the same values as split_weight, whose FP64
+// floor and conversions cost the FP64 pipe about four operations per row).
+__device__ __forceinline__ void split_weight_int(double w, unsigned long long& hi, unsigned long long& lo)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(w);
+    const int e = (int)((b >> 52) & 0x7FF);
+    hi = lo = 0;
+    if (e == 0) return;                                  // zero or below 2^-1022
+    const unsigned long long m = (b & ((1ull << 52) - 1ull)) | (1ull << 52);
+    const int sh = e - 991;                              // w 2^84 = m 2^sh
+    unsigned __int128 v;
+    if (sh >= 0) v = (unsigned __int128)m << sh;
+    else if (sh > -64) v = (unsigned __int128)(m >> -sh);
+    else return;
+    hi = (unsigned long long)(v >> 32);
+    lo = (unsigned long long)(v & 0xFFFFFFFFull);
+}
+
+// k_obs_accum for at most 16 sites and one model: the same integer sums, with
+// each thread keeping its own <n_j> limbs in registers over all its rows (one
+// warp reduction per site at the end instead of one per site and round of 32
+// rows).  Per-thread sums cannot overflow: the hi limbs of all rows sum to at
+// most 2^52 ||c||^2 K.
+template <int W>
+__global__ void __launch_bounds__(kBlock) k_obs_accum16(const DevModel* __restrict__ M, Counters* ctr,
+                                                        const uint64_t* __restrict__ keys,
+                                                        const double2* __restrict__ vec,
+                                                        unsigned long long* __restrict__ part)
+{
+    constexpr int NS = 16;
+    __shared__ unsigned long long sh[kBlock / 32][kObsStride][2];
+    if (ctr->err) return;
+    const int N = M->N, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int t = lane; t < 2 * N + 1; t += 32) sh[warp][t][0] = sh[warp][t][1] = 0ull;
+    __syncwarp();
+    const int fmt = M->fmt;
+    const uint32_t q = ctr->q;
+    const bool uni = M->uniform_radix != 0;
+    const UDiv rd0 = M->div_radix[0];
+    const UDiv dexc = M->div_exc;
+    int wf[W + 1];
+#pragma unroll
+    for (int i = 0; i <= W; ++i) wf[i] = M->word_first[i];
+    unsigned long long ah[NS], al[NS];
+#pragma unroll
+    for (int j = 0; j < NS; ++j) ah[j] = al[j] = 0ull;
+    unsigned long long nh = 0, nl = 0;
+    for (uint32_t row = blockIdx.x * blockDim.x + threadIdx.x; row < q; row += gridDim.x * blockDim.x) {
+        unsigned long long hi = 0, lo = 0;
+        if (fmt == 1) {
+            const double2 v = vec[row];
+            split_weight_int(v.x * v.x + v.y * v.y, hi, lo);
+        } else {
+            const dwf w = dw_norm2(reinterpret_cast<const float4*>(vec)[row]);
+            if (w.hi != 0.0f) {
+                __int128 F = fix84(w.hi) + fix84(w.lo);
+                if (F < 0) F = 0;
+                hi = (unsigned long long)(F >> 32);
+                lo = (unsigned long long)(F & 0xFFFFFFFF);
+            }
+        }
+        if (!(hi | lo)) continue;
+        const Key<W> k = load_key<W>(keys, row);
+        const uint64_t q0 = udiv(k.w[0], dexc);
+        const int s = (int)(k.w[0] - q0 * dexc.d);
+        atomicAdd(&sh[warp][s][0], hi);
+        atomicAdd(&sh[warp][s][1], lo);
+        nh += hi;
+        nl += lo;
+#pragma unroll
+        for (int wd = 0; wd < W; ++wd) {
+            uint64_t x = (wd == 0) ? q0 : k.w[wd];
+#pragma unroll
+            for (int j = 0; j < NS; ++j) {
+                if (j < wf[wd] || j >= wf[wd + 1]) continue;
+                const UDiv dv = uni ? rd0 : M->div_radix[j];
+                const uint64_t xq = udiv(x, dv);
+                const uint32_t nj = (uint32_t)(x - xq * dv.d);
+                x = xq;
+                ah[j] += hi * nj;
+                al[j] += lo * nj;
+            }
+        }
+    }
+    nh = warp_sum_u64(nh);
+    nl = warp_sum_u64(nl);
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+        if (j >= N) break;                   // uniform
+        const unsigned long long a = warp_sum_u64(ah[j]), c = warp_sum_u64(al[j]);
+        if (lane == 0) {
+            sh[warp][N + j][0] += a;
+            sh[warp][N + j][1] += c;
+        }
+    }
+    if (lane == 0) {
+        sh[warp][2 * N][0] += nh;
+        sh[warp][2 * N][1] += nl;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < 2 * N + 1; t += blockDim.x) {
+        unsigned long long ah2 = 0, al2 = 0;
+        for (int wp = 0; wp < kBlock / 32; ++wp) {
+            ah2 += sh[wp][t][0];
+            al2 += sh[wp][t][1];
+        }
+        if (ah2) atomicAdd(&part[2 * t], ah2);
+        if (al2) atomicAdd(&part[2 * t + 1], al2);
+    }
+}
+
 // Ensembles: the same integer sums per (realisation, site), accumulated in
 // shared memory when the R x 2N table fits there, else in global memory.
 template <int W>
@@ -1367,7 +1479,8 @@ static int observe_w(const Bufs& b, int gen, const double2* vec, double dt, int 
                                                     b.psi0_amp, b.n0, vec, dt, mode, b.obs_part, b.obs, b.rec_len);
         return 2;
     }
-    k_obs_accum<W><<<b.G, kBlock, 0, st>>>(b.model, b.ctr, b.keys[gen], vec, b.obs_part);
+    if (b.N <= 16) k_obs_accum16<W><<<b.G, kBlock, 0, st>>>(b.model, b.ctr, b.keys[gen], vec, b.obs_part);
+    else k_obs_accum<W><<<b.G, kBlock, 0, st>>>(b.model, b.ctr, b.keys[gen], vec, b.obs_part);
     k_obs_finish<W><<<1, kBlock, 0, st>>>(b.model, b.ctr, b.table[gen], b.table_slots, b.psi0_keys, b.psi0_amp,
                                           b.n0, vec, dt, mode, b.obs_part, b.obs, b.rec_len);
     return 2;
