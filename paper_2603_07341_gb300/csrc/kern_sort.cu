@@ -199,14 +199,70 @@ __global__ void __launch_bounds__(kBlock) k_trunc_place(Counters* ctr, const uin
 {
     if (ctr->err) return;
     const uint32_t n = ctr->kept;
-    for (uint32_t dst = blockIdx.x * blockDim.x + threadIdx.x; dst < n; dst += gridDim.x * blockDim.x) {
-        const uint32_t src = si[dst];
-        Key<W> k = load_key<W>(sk, dst);
-        store_key<W>(keys_out, dst, k);
-        c_out[dst] = c_in[src];
-        meta_out[dst] = meta_in[src];
-        if (from) from[dst] = src;
-        if (!table_insert_unique<W>(table_out, slots, k, dst)) set_err(ctr, kErrProbe, step, 1);
+    if constexpr (W == 1) {
+        // one-word keys: kRPT rows per thread, their gathers issued together
+        // and their (unique) keys inserted in warp-wide lockstep rounds: every
+        // round claims, with one 16-byte compare-and-swap each, the empty
+        // slots the unplaced keys stand on and loads the next slot of the
+        // others.  Every lane of a warp runs the same number of rounds.
+        constexpr int kRPT = 4;
+        const uint32_t stride = gridDim.x * blockDim.x;
+        for (uint32_t dw = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); dw < n; dw += stride * kRPT) {
+            const uint32_t d0 = dw + (threadIdx.x & 31u);
+            uint64_t key[kRPT], tag[kRPT];
+            uint32_t pos[kRPT];
+            unsigned act = 0;
+#pragma unroll
+            for (int k = 0; k < kRPT; ++k) {
+                const uint32_t dst = d0 + (uint32_t)k * stride;
+                key[k] = 0;
+                tag[k] = 0;
+                pos[k] = 0;
+                if (dst < n) {
+                    const uint32_t src = si[dst];
+                    key[k] = sk[dst];
+                    keys_out[dst] = key[k];
+                    c_out[dst] = c_in[src];
+                    meta_out[dst] = meta_in[src];
+                    if (from) from[dst] = src;
+                    const uint64_t h = key_hash<1>(Key<1>{{key[k]}});
+                    tag[k] = ((uint64_t)fingerprint<1>(h) << 32) | dst;
+                    pos[k] = (uint32_t)slot_home(h, slots);
+                    act |= 1u << k;
+                }
+            }
+            uint64_t cur[kRPT];
+#pragma unroll
+            for (int k = 0; k < kRPT; ++k)
+                cur[k] = ((act >> k) & 1u) ? __ldcg(table_out + (uint64_t)pos[k] * 2) : 0ull;
+            for (uint32_t round = 0; round <= kMaxProbe && __any_sync(0xffffffffu, act != 0); ++round) {
+#pragma unroll
+                for (int k = 0; k < kRPT; ++k)      // claims, all in flight
+                    if (((act >> k) & 1u) && cur[k] == kEmpty) {
+                        uint64_t olo, ohi;
+                        cas128(table_out + (uint64_t)pos[k] * 2, kEmpty, kEmpty, tag[k], key[k], olo, ohi);
+                        if (olo == kEmpty) act &= ~(1u << k);
+                        cur[k] = olo;
+                    }
+#pragma unroll
+                for (int k = 0; k < kRPT; ++k)      // occupied: the next slots, all in flight
+                    if (((act >> k) & 1u) && cur[k] != kEmpty) {
+                        pos[k] = (uint32_t)slot_next(pos[k], slots);
+                        cur[k] = __ldcg(table_out + (uint64_t)pos[k] * 2);
+                    }
+            }
+            if (act) set_err(ctr, kErrProbe, step, 1);
+        }
+    } else {
+        for (uint32_t dst = blockIdx.x * blockDim.x + threadIdx.x; dst < n; dst += gridDim.x * blockDim.x) {
+            const uint32_t src = si[dst];
+            Key<W> k = load_key<W>(sk, dst);
+            store_key<W>(keys_out, dst, k);
+            c_out[dst] = c_in[src];
+            meta_out[dst] = meta_in[src];
+            if (from) from[dst] = src;
+            if (!table_insert_unique<W>(table_out, slots, k, dst)) set_err(ctr, kErrProbe, step, 1);
+        }
     }
 }
 
