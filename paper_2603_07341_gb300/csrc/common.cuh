@@ -205,6 +205,13 @@ struct DevModel {
     dwf omega_dw[kMaxSites];
     int uniform_omega;         // all omega_j equal (diagonal = eps_s + omega sum_j n_j)
     int uniform_radix;         // all site radices equal (one divisor decodes every digit)
+    // one-word keys with a uniform radix R and at most 16 sites, when
+    // R^8 (R - 1) < 2^32: the phonon digits split into two 32-bit halves of at
+    // most 8 digits (q0 = h R^8 + l), each decoded with 32-bit multiplies by
+    // r_magic = ceil(2^32 / R), exact for every half below 2^32 / (R - 1)
+    int r8_ok;
+    uint32_t r_magic;
+    UDiv div_r8;
     int batch;                 // realisations R of an ensemble (1: one model)
     int batch_word;            // realisation digit: word, place value, radix
     UDiv div_batch_stride;

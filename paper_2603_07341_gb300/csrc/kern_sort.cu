@@ -236,19 +236,24 @@ __global__ void __launch_bounds__(kBlock) k_trunc_place(Counters* ctr, const uin
             for (int k = 0; k < kRPT; ++k)
                 cur[k] = ((act >> k) & 1u) ? __ldcg(table_out + (uint64_t)pos[k] * 2) : 0ull;
             for (uint32_t round = 0; round <= kMaxProbe && __any_sync(0xffffffffu, act != 0); ++round) {
+                unsigned emp = 0;
+#pragma unroll
+                for (int k = 0; k < kRPT; ++k) {    // occupied: the next slots, in flight with the claims
+                    if (!((act >> k) & 1u)) continue;
+                    if (cur[k] == kEmpty) {
+                        emp |= 1u << k;
+                    } else {
+                        pos[k] = (uint32_t)slot_next(pos[k], slots);
+                        cur[k] = __ldcg(table_out + (uint64_t)pos[k] * 2);
+                    }
+                }
 #pragma unroll
                 for (int k = 0; k < kRPT; ++k)      // claims, all in flight
-                    if (((act >> k) & 1u) && cur[k] == kEmpty) {
+                    if ((emp >> k) & 1u) {
                         uint64_t olo, ohi;
                         cas128(table_out + (uint64_t)pos[k] * 2, kEmpty, kEmpty, tag[k], key[k], olo, ohi);
                         if (olo == kEmpty) act &= ~(1u << k);
-                        cur[k] = olo;
-                    }
-#pragma unroll
-                for (int k = 0; k < kRPT; ++k)      // occupied: the next slots, all in flight
-                    if (((act >> k) & 1u) && cur[k] != kEmpty) {
-                        pos[k] = (uint32_t)slot_next(pos[k], slots);
-                        cur[k] = __ldcg(table_out + (uint64_t)pos[k] * 2);
+                        cur[k] = olo;               // lost: moves on in the next round
                     }
             }
             if (act) set_err(ctr, kErrProbe, step, 1);

@@ -437,7 +437,9 @@ __global__ void __launch_bounds__(kBlock) k_level_scatter(const DevModel* __rest
                                                           const uint32_t* __restrict__ wmask,
                                                           const uint32_t* __restrict__ blk_off)
 {
-    __shared__ uint32_t qc[2 * kBlock];
+    constexpr int kCPT = 4;                     // consecutive candidates per thread and round
+    constexpr uint32_t kRound = kBlock * kCPT;
+    __shared__ uint32_t qc[kRound + kBlock];
     if (ctr->err) return;
     uint32_t lo0 = ctr->level_off[f], base_row = ctr->level_off[f + 1];
     const int D = M->D;
@@ -471,14 +473,21 @@ __global__ void __launch_bounds__(kBlock) k_level_scatter(const DevModel* __rest
             }
         }
     };
-    for (uint32_t base = lo; base < hi; base += kBlock) {
-        uint32_t c = base + threadIdx.x;
-        uint32_t w0 = base + (threadIdx.x & ~31u);
-        uint32_t bal = (w0 < hi) ? wmask[w0 >> 5] : 0u;
-        bool win = (c < hi) && ((bal >> (threadIdx.x & 31)) & 1u);
+    // chunks are multiples of kBlock candidates (chunk_of), so a thread's four
+    // consecutive candidates share one 32-bit mask word
+    for (uint32_t base = lo; base < hi; base += kRound) {
+        const uint32_t c = base + kCPT * threadIdx.x;
+        unsigned bits = 0;
+        if (c < hi) {
+            bits = (wmask[c >> 5] >> (c & 31u)) & 0xFu;
+            if (hi - c < (uint32_t)kCPT) bits &= (1u << (hi - c)) - 1u;
+        }
         uint32_t tot;
-        uint32_t r = block_excl_scan<kBlock>(win ? 1u : 0u, &tot);
-        if (win) qc[pending + r] = c;
+        const uint32_t r = block_excl_scan<kBlock>((uint32_t)__popc(bits), &tot);
+        uint32_t o = pending + r;
+#pragma unroll
+        for (int k = 0; k < kCPT; ++k)
+            if ((bits >> k) & 1u) qc[o++] = c + (uint32_t)k;
         pending += tot;
         if (pending >= kBlock) {
             __syncthreads();
@@ -1082,6 +1091,8 @@ __global__ void __launch_bounds__(kBlock) k_obs_accum16(const DevModel* __restri
     const bool uni = M->uniform_radix != 0;
     const UDiv rd0 = M->div_radix[0];
     const UDiv dexc = M->div_exc;
+    const bool r8 = M->r8_ok != 0;
+    const uint32_t rmag = M->r_magic, rad = (uint32_t)rd0.d;
     int wf[W + 1];
 #pragma unroll
     for (int i = 0; i <= W; ++i) wf[i] = M->word_first[i];
@@ -1111,18 +1122,35 @@ __global__ void __launch_bounds__(kBlock) k_obs_accum16(const DevModel* __restri
         atomicAdd(&sh[warp][s][1], lo);
         nh += hi;
         nl += lo;
+        if (W == 1 && r8) {
+            // two independent chains of 32-bit digit divisions
+            const uint64_t xh = udiv(q0, M->div_r8);
+            uint32_t x0 = (uint32_t)(q0 - xh * M->div_r8.d), x1 = (uint32_t)xh;
 #pragma unroll
-        for (int wd = 0; wd < W; ++wd) {
-            uint64_t x = (wd == 0) ? q0 : k.w[wd];
+            for (int j = 0; j < 8; ++j) {
+                const uint32_t q0j = __umulhi(x0, rmag), q1j = __umulhi(x1, rmag);
+                const uint32_t n0 = x0 - q0j * rad, n1 = x1 - q1j * rad;
+                x0 = q0j;
+                x1 = q1j;
+                ah[j] += hi * n0;
+                al[j] += lo * n0;
+                ah[j + 8] += hi * n1;            // zero past the last site
+                al[j + 8] += lo * n1;
+            }
+        } else {
 #pragma unroll
-            for (int j = 0; j < NS; ++j) {
-                if (j < wf[wd] || j >= wf[wd + 1]) continue;
-                const UDiv dv = uni ? rd0 : M->div_radix[j];
-                const uint64_t xq = udiv(x, dv);
-                const uint32_t nj = (uint32_t)(x - xq * dv.d);
-                x = xq;
-                ah[j] += hi * nj;
-                al[j] += lo * nj;
+            for (int wd = 0; wd < W; ++wd) {
+                uint64_t x = (wd == 0) ? q0 : k.w[wd];
+#pragma unroll
+                for (int j = 0; j < NS; ++j) {
+                    if (j < wf[wd] || j >= wf[wd + 1]) continue;
+                    const UDiv dv = uni ? rd0 : M->div_radix[j];
+                    const uint64_t xq = udiv(x, dv);
+                    const uint32_t nj = (uint32_t)(x - xq * dv.d);
+                    x = xq;
+                    ah[j] += hi * nj;
+                    al[j] += lo * nj;
+                }
             }
         }
     }

@@ -764,6 +764,21 @@ paces_status paces::fill_model(const paces_params* params, const paces_layout& L
     for (int j = 1; j < N; ++j) M->uniform_omega &= (M->omega[j] == M->omega[0]);
     M->uniform_radix = 1;
     for (int j = 1; j < N; ++j) M->uniform_radix &= (L.site_radix[j] == L.site_radix[0]);
+    M->r8_ok = 0;
+    if (M->uniform_radix && L.words == 1 && N <= 16 && L.site_radix[0] >= 2) {
+        const uint64_t R = L.site_radix[0];
+        uint64_t r8 = 1;
+        bool fits = true;
+        for (int i = 0; i < 8 && fits; ++i) {
+            r8 *= R;
+            fits = r8 < (1ull << 32);
+        }
+        if (fits && r8 * (R - 1) < (1ull << 32)) {
+            M->r8_ok = 1;
+            M->r_magic = (uint32_t)(((1ull << 32) + R - 1) / R);
+            M->div_r8 = make_udiv(r8);
+        }
+    }
     M->batch = params->batch > 1 ? params->batch : 1;
     M->batch_word = L.batch_word;
     M->div_batch_stride = make_udiv(L.batch_stride);
