@@ -79,8 +79,10 @@ typedef enum {
 #define PACES_DW 1        /* double-word: every amplitude is a pair of FP32 (48-bit       */
                           /* significand) and all arithmetic on them runs on the FP32     */
                           /* pipe with error-free transformations                         */
-#define PACES_C64_SPMV 2  /* complex64 SpMV for terms n >= 3; terms 1-2, the accumulator, */
-                          /* norms and truncation magnitudes double-word                  */
+#define PACES_C64_SPMV 2  /* complex64 SpMV for the small terms of a series: from two     */
+                          /* terms after the first whose norm is at most 2^-16 of the     */
+                          /* state's (never before term 3); the leading terms, the        */
+                          /* accumulator, norms and truncation magnitudes double-word     */
 
 /* Device memory hook.  alloc returns device memory of `bytes` usable on
  * `stream` (a cudaStream_t) or NULL; free releases it.  Both may be called from

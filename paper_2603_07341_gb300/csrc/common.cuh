@@ -598,6 +598,19 @@ __device__ __forceinline__ void block_sum(double (&v)[K], double* out /* smem or
     __syncthreads();
 }
 
+// |v| 2^(32 - L) as an FP32 number, from the upper 32 bits of the FP64 v (20
+// bits of significand, truncated: relative error below 2^-20), with integer
+// operations only, so that magnitude tests cost the FP64 pipe nothing.
+// Results below 2^-126 give 0 or a subnormal; results at or above 2^128
+// saturate near 2^128.
+__device__ __forceinline__ float mag_scaled_f32(double v, int L)
+{
+    int h = __double2hiint(v) & 0x7FFFFFFF;
+    int e = (h >> 20) - (1023 - 127 - 32) - L;
+    e = min(max(e, 0), 254);
+    return __int_as_float((e << 23) | ((h & 0xFFFFF) << 3));
+}
+
 // ---------------------------------------------------------------- grid barrier
 __device__ __forceinline__ uint64_t global_ns()
 {

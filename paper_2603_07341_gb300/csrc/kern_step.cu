@@ -36,11 +36,54 @@ __global__ void k_insert_rows(const uint64_t* __restrict__ keys, uint32_t n, uin
 // product and sum rounded separately (no FMA contraction), as the oracle does.
 // Double-word storage: |c|^2 in double-word arithmetic (relative error below
 // 2^-46) compared with theta^2 rounded to a double-word.
-__device__ __forceinline__ bool keep_row(const double2* c, uint64_t i, int fmt, double th2, dwf th)
+//
+// FP64 storage: the FP64 pipe of this part retires about two operations per SM
+// and clock, so the three FP64 operations of the test would bound the pass.
+// The decision is first taken from the leading 20 bits of each component
+// (mag_scaled_f32, integer operations, scaled by 2^(32 - L) so that theta^2
+// lands near 1 in FP32): a = |x| 2^(32-L), b = |y| 2^(32-L), each at most
+// 2^-20 below the exact magnitude, so a^2 + b^2 (FP32, three roundings of
+// 2^-24) is within 2^-18 of |c|^2 2^(64-2L), and the FP64 test's own rounding is
+// 2^-52.  Outside a band of 2^-14 around t = theta^2 2^(64-2L) the decision is
+// therefore the FP64 test's; inside it, for infinite or NaN components and
+// for theta^2 outside [2^-400, 2^100] (where t would leave the FP32 range),
+// the FP64 test runs.  The kept set is the same bit for bit.
+struct KeepTest {
+    double th2;
+    int L;          // scale exponent: t = theta^2 2^(64 - 2L) in [1/4, 1)
+    bool filter;    // false: FP64 test only
+    float t_lo, t_hi;
+};
+
+__device__ __forceinline__ KeepTest keep_test(double th2)
+{
+    KeepTest k;
+    k.th2 = th2;
+    k.filter = th2 >= 0x1p-400 && th2 <= 0x1p100;
+    k.L = 32;
+    k.t_lo = k.t_hi = 0.f;
+    if (k.filter) {
+        const int E = ilogb(th2);               // th2 in [2^E, 2^(E+1))
+        k.L = 32 + ((E + 2) >> 1);              // 2 (L - 32) = E + 1 or E + 2 (floor division)
+        const float t = (float)ldexp(th2, 64 - 2 * k.L);
+        k.t_lo = t * (1.0f - 0x1p-14f);
+        k.t_hi = t * (1.0f + 0x1p-14f);
+    }
+    return k;
+}
+
+__device__ __forceinline__ bool keep_row(const double2* c, uint64_t i, int fmt, const KeepTest& kt, dwf th)
 {
     if (fmt == 1) {
         double2 v = c[i];
-        return __dadd_rn(__dmul_rn(v.x, v.x), __dmul_rn(v.y, v.y)) >= th2;
+        const int ex = (__double2hiint(v.x) >> 20) & 0x7FF, ey = (__double2hiint(v.y) >> 20) & 0x7FF;
+        if (kt.filter && ex != 0x7FF && ey != 0x7FF) {
+            const float a = mag_scaled_f32(v.x, kt.L), b = mag_scaled_f32(v.y, kt.L);
+            const float w = __fmaf_rn(a, a, __fmul_rn(b, b));
+            if (w < kt.t_lo) return false;
+            if (w > kt.t_hi) return true;
+        }
+        return __dadd_rn(__dmul_rn(v.x, v.x), __dmul_rn(v.y, v.y)) >= kt.th2;
     }
     dwf w = dw_norm2(reinterpret_cast<const float4*>(c)[i]);
     return w.hi > th.hi || (w.hi == th.hi && w.lo >= th.lo);
@@ -53,10 +96,11 @@ __global__ void __launch_bounds__(kBlock) k_trunc_count(const double2* __restric
     if (ctr->err) return;
     uint32_t q = ctr->q, lo, hi;
     chunk_of(q, gridDim.x, blockIdx.x, lo, hi);
+    const KeepTest kt = keep_test(th2);
     uint32_t cnt = 0;
     for (uint32_t base = lo; base < hi; base += kBlock) {
         uint32_t i = base + threadIdx.x;
-        bool keep = (i < hi) && keep_row(c, i, fmt, th2, th);
+        bool keep = (i < hi) && keep_row(c, i, fmt, kt, th);
         unsigned bal = __ballot_sync(0xffffffffu, keep);
         uint32_t w0 = base + (threadIdx.x & ~31u);
         if ((threadIdx.x & 31) == 0 && w0 < hi) keepw[w0 >> 5] = bal;
@@ -1100,56 +1144,76 @@ __global__ void __launch_bounds__(kBlock) k_obs_accum16(const DevModel* __restri
 #pragma unroll
     for (int j = 0; j < NS; ++j) ah[j] = al[j] = 0ull;
     unsigned long long nh = 0, nl = 0;
-    for (uint32_t row = blockIdx.x * blockDim.x + threadIdx.x; row < q; row += gridDim.x * blockDim.x) {
-        unsigned long long hi = 0, lo = 0;
-        if (fmt == 1) {
-            const double2 v = vec[row];
-            split_weight_int(v.x * v.x + v.y * v.y, hi, lo);
-        } else {
-            const dwf w = dw_norm2(reinterpret_cast<const float4*>(vec)[row]);
-            if (w.hi != 0.0f) {
-                __int128 F = fix84(w.hi) + fix84(w.lo);
-                if (F < 0) F = 0;
-                hi = (unsigned long long)(F >> 32);
-                lo = (unsigned long long)(F & 0xFFFFFFFF);
+    // two rows per thread and round, with the amplitude and key loads of both
+    // issued before any arithmetic (the key no longer waits for the weight)
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t r0 = blockIdx.x * blockDim.x + threadIdx.x; r0 < q; r0 += 2 * stride) {
+        float4 va[2];
+        Key<W> kk[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const uint32_t row = r0 + (uint32_t)u * stride;      // q < 2^31: no wrap
+            va[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int i = 0; i < W; ++i) kk[u].w[i] = 0;
+            if (row < q) {
+                va[u] = reinterpret_cast<const float4*>(vec)[row];
+                kk[u] = load_key<W>(keys, row);
             }
         }
-        if (!(hi | lo)) continue;
-        const Key<W> k = load_key<W>(keys, row);
-        const uint64_t q0 = udiv(k.w[0], dexc);
-        const int s = (int)(k.w[0] - q0 * dexc.d);
-        atomicAdd(&sh[warp][s][0], hi);
-        atomicAdd(&sh[warp][s][1], lo);
-        nh += hi;
-        nl += lo;
-        if (W == 1 && r8) {
-            // two independent chains of 32-bit digit divisions
-            const uint64_t xh = udiv(q0, M->div_r8);
-            uint32_t x0 = (uint32_t)(q0 - xh * M->div_r8.d), x1 = (uint32_t)xh;
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const uint32_t q0j = __umulhi(x0, rmag), q1j = __umulhi(x1, rmag);
-                const uint32_t n0 = x0 - q0j * rad, n1 = x1 - q1j * rad;
-                x0 = q0j;
-                x1 = q1j;
-                ah[j] += hi * n0;
-                al[j] += lo * n0;
-                ah[j + 8] += hi * n1;            // zero past the last site
-                al[j + 8] += lo * n1;
+        for (int u = 0; u < 2; ++u) {
+            unsigned long long hi = 0, lo = 0;
+            if (fmt == 1) {
+                const double vx = __hiloint2double(__float_as_int(va[u].y), __float_as_int(va[u].x));
+                const double vy = __hiloint2double(__float_as_int(va[u].w), __float_as_int(va[u].z));
+                split_weight_int(vx * vx + vy * vy, hi, lo);
+            } else {
+                const dwf w = dw_norm2(va[u]);
+                if (w.hi != 0.0f) {
+                    __int128 F = fix84(w.hi) + fix84(w.lo);
+                    if (F < 0) F = 0;
+                    hi = (unsigned long long)(F >> 32);
+                    lo = (unsigned long long)(F & 0xFFFFFFFF);
+                }
             }
-        } else {
+            if (!(hi | lo)) continue;                // rows past q have zero weight
+            const Key<W>& k = kk[u];
+            const uint64_t q0 = udiv(k.w[0], dexc);
+            const int s = (int)(k.w[0] - q0 * dexc.d);
+            atomicAdd(&sh[warp][s][0], hi);
+            atomicAdd(&sh[warp][s][1], lo);
+            nh += hi;
+            nl += lo;
+            if (W == 1 && r8) {
+                // two independent chains of 32-bit digit divisions
+                const uint64_t xh = udiv(q0, M->div_r8);
+                uint32_t x0 = (uint32_t)(q0 - xh * M->div_r8.d), x1 = (uint32_t)xh;
 #pragma unroll
-            for (int wd = 0; wd < W; ++wd) {
-                uint64_t x = (wd == 0) ? q0 : k.w[wd];
+                for (int j = 0; j < 8; ++j) {
+                    const uint32_t q0j = __umulhi(x0, rmag), q1j = __umulhi(x1, rmag);
+                    const uint32_t n0 = x0 - q0j * rad, n1 = x1 - q1j * rad;
+                    x0 = q0j;
+                    x1 = q1j;
+                    ah[j] += hi * n0;
+                    al[j] += lo * n0;
+                    ah[j + 8] += hi * n1;            // zero past the last site
+                    al[j + 8] += lo * n1;
+                }
+            } else {
 #pragma unroll
-                for (int j = 0; j < NS; ++j) {
-                    if (j < wf[wd] || j >= wf[wd + 1]) continue;
-                    const UDiv dv = uni ? rd0 : M->div_radix[j];
-                    const uint64_t xq = udiv(x, dv);
-                    const uint32_t nj = (uint32_t)(x - xq * dv.d);
-                    x = xq;
-                    ah[j] += hi * nj;
-                    al[j] += lo * nj;
+                for (int wd = 0; wd < W; ++wd) {
+                    uint64_t x = (wd == 0) ? q0 : k.w[wd];
+#pragma unroll
+                    for (int j = 0; j < NS; ++j) {
+                        if (j < wf[wd] || j >= wf[wd + 1]) continue;
+                        const UDiv dv = uni ? rd0 : M->div_radix[j];
+                        const uint64_t xq = udiv(x, dv);
+                        const uint32_t nj = (uint32_t)(x - xq * dv.d);
+                        x = xq;
+                        ah[j] += hi * nj;
+                        al[j] += lo * nj;
+                    }
                 }
             }
         }

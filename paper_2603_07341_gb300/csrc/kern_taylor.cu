@@ -142,18 +142,6 @@ __device__ __forceinline__ double2 row_apply(const uint32_t* __restrict__ col, c
     return make_double2(yr, yi);
 }
 
-// |v| 2^(32 - L) as an FP32 number, from the upper 32 bits of the FP64 v (20
-// bits of significand, relative error below 2^-20), with integer operations
-// only, so that the stop test costs the FP64 pipe nothing.  Results below
-// 2^-126 give 0 or a subnormal; results at or above 2^128 saturate near 2^128.
-__device__ __forceinline__ float mag_scaled_f32(double v, int L)
-{
-    int h = __double2hiint(v) & 0x7FFFFFFF;
-    int e = (h >> 20) - (1023 - 127 - 32) - L;
-    e = min(max(e, 0), 254);
-    return __int_as_float((e << 23) | ((h & 0xFFFFF) << 3));
-}
-
 // Number of Taylor series a step runs as (App. C.1's scaling alternative):
 // s = ceil(rho dt / xmax), rho = the row bound of P H P that the build of the
 // step's Hamiltonian left in the counters (in units of 2^-20); 1 when xmax <= 0;
@@ -731,12 +719,24 @@ __global__ void __launch_bounds__(kBlock) k_taylor_dw(TaylorArgs a)
 }
 
 // ---------------------------------------------------------------- complex64 terms
-// PACES_C64_SPMV: terms n <= kDwTerms as in k_taylor_dw; from term kDwTerms + 1 on,
-// the SpMV runs in plain complex64 (FP32 products and sums, coefficients
-// rounded to FP32), phi_n is stored as float2 and added into the double-word
-// accumulator r with an error-free sum.  The first terms carry most of the
-// weight (||phi_1|| ~ dt ||H||), so keeping them double-word bounds the error.
-constexpr int kDwTerms = 2;
+// PACES_C64_SPMV: the leading terms run as in k_taylor_dw; once a term is small
+// against the state, the later terms of the series run in plain complex64 (FP32
+// products and sums, coefficients rounded to FP32), each phi_n stored as float2
+// and added into the double-word accumulator r with an error-free sum.  The
+// switch is taken from the norms the stop test already reduces: when term m
+// ends with ||phi_m||^2 <= kC64Tau2 ||r||^2, terms from max(m + 2, kDwTerms + 1)
+// on run in complex64 (term m + 1 has started by then with its output format
+// fixed, so it stays double-word and writes its result rounded to float2 for
+// the first complex64 term).  Every block reads the same reduced norms, so the
+// whole grid switches at the same term.  An FP32 term's rounding is about
+// 2^-24 (c + 2) of its own norm, so with tau = 2^-16 what the complex64 terms
+// add to a step's error stays near 2^-38 of ||v|| (||phi_{m+2}|| is at most
+// tau ||v|| (rho h)^2 / ((m + 1)(m + 2))), and a 2048-step run stays far inside
+// a 1e-6 observable tolerance.  With the first terms of a series in
+// double-word and the rest in FP32, the series costs less the faster its
+// terms decay.
+constexpr int kDwTerms = 2;                  // terms that always run double-word
+constexpr float kC64Tau2 = 2.3283064365386963e-10f;   // tau^2 = 2^-32
 
 // double-word + float (Joldes et al., DWPlusFP, Alg. 4)
 __device__ __forceinline__ dwf dw_add_f(dwf x, float y)
@@ -803,6 +803,9 @@ __global__ void __launch_bounds__(kBlock) k_taylor_c64(TaylorArgs a)
     const uint32_t sub = (threadIdx.x & 31) / LPR;
     float4* Y = reinterpret_cast<float4*>(a.ta);
     float4* Y2 = reinterpret_cast<float4*>(a.tb);   // input copy of series after the first
+    // double-word terms alternate between the two buffers: odd terms write Y,
+    // even terms Y2 (after the first series, term 2 overwrites the series
+    // input copy, which only term 1 reads)
     float4* R = reinterpret_cast<float4*>(a.r);
     float2* F[2] = {a.fa, a.fb};
     const float2* DG = reinterpret_cast<const float2*>(a.diag);
@@ -834,19 +837,21 @@ __global__ void __launch_bounds__(kBlock) k_taylor_c64(TaylorArgs a)
         }
         int nd = 0;
         bool cj = fixed > 0;
+        int c64_from = nlimit + 2;                  // first complex64 term (none yet)
         for (int n = 1; n <= nlimit; ++n) {
             const double s = h / (double)n;
             const dwf sdw = dw_from_double(s);
             const float s32 = (float)s;
-            const bool dw_term = n <= kDwTerms;
+            const bool dw_term = n < c64_from;
+            const bool dw_next = n + 1 < c64_from;  // the format term n + 1 reads
             __syncthreads();
             for (int t = threadIdx.x; t < ncoef; t += blockDim.x) {
                 coef[t] = dw_from_double(s * M->coef[t]);
                 coef32[t] = (float)(s * M->coef[t]);
             }
             __syncthreads();
-            const float4* Xd = (n == 1) ? X : (n == 2 ? Y : nullptr);        // double-word input
-            const float2* Xf = F[(n + 1) & 1];                               // complex64 input (n >= 3)
+            const float4* Xd = (n == 1) ? X : ((n & 1) ? Y2 : Y);             // double-word input
+            const float2* Xf = F[(n + 1) & 1];                               // complex64 input
             float2* Yf = F[n & 1];                                           // complex64 output
             Red8 acc{0.f, 0.f, {0.f, 0.f}, {0.f, 0.f}};
             for (uint32_t rb = warp * RPW; rb < q; rb += nwarps * RPW) {
@@ -866,7 +871,7 @@ __global__ void __launch_bounds__(kBlock) k_taylor_c64(TaylorArgs a)
                     dot2_mac(im, ds, xi.z, xi.w);
                     dwf yre = dot2_result(re), yim = dot2_result(im);
                     phi = make_float4(yim.hi, yim.lo, -yre.hi, -yre.lo);
-                    if (n < kDwTerms) Y[row] = phi;
+                    if (dw_next) ((n & 1) ? Y : Y2)[row] = phi;
                     else Yf[row] = make_float2(phi.x + phi.y, phi.z + phi.w);   // next input, rounded
                     if (n == 1 && j == 0) {
                         acc.e = dw_add(acc.e, dw_add(dw_mul(dwf{xi.x, xi.y}, yre), dw_mul(dwf{xi.z, xi.w}, yim)));
@@ -908,6 +913,7 @@ __global__ void __launch_bounds__(kBlock) k_taylor_c64(TaylorArgs a)
                 cj = true;
                 break;
             }
+            if (c64_from > nlimit && tsh[0] <= kC64Tau2 * tsh[1]) c64_from = max(n + 2, kDwTerms + 1);
         }
         total += nd;
         if (blockIdx.x == 0 && threadIdx.x == 0) ctr->sub_terms[j] = nd;

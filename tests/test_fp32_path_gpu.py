@@ -1,7 +1,9 @@
 """The complex64-SpMV propagator (PACES_C64_SPMV) against the plain FP64
 single-instance form (PACES_C128, complex128 as in the paper) on the same GPU,
-and against the FP64 oracle.  Terms n >= 3 run in FP32; the first two terms,
-the accumulator, norms and truncation magnitudes stay double-word.  Stated
+and against the FP64 oracle.  The terms of a series from two after the first
+one below 2^-16 of the state's norm run in FP32 (never before term 3); the
+leading terms, the accumulator, norms and truncation magnitudes stay
+double-word.  Stated
 bound: every observable (site populations P_s, phonon numbers <n_j>, the
 autocorrelation C(t), the norm and the energy) within 1e-6 of the FP64 result
 at every step of the horizon tested."""
