@@ -22,27 +22,40 @@ constexpr int kDigits = 256;
 }
 
 // Kept rows as (key, source row) in row order (the scan of the keep bits).
+// Each thread takes four consecutive rows per block scan (chunks start at
+// multiples of kBlock, so the four keep bits share one 32-bit word) and issues
+// the key loads of its kept rows before the scan.
 template <int W>
 __global__ void __launch_bounds__(kBlock) k_trunc_compact(const uint64_t* __restrict__ keys_in, Counters* ctr,
                                                           const uint32_t* __restrict__ keepw,
                                                           const uint32_t* __restrict__ blk_off,
                                                           uint64_t* __restrict__ sk, uint32_t* __restrict__ si)
 {
+    constexpr int kRPT = 4;
     if (ctr->err) return;
     uint32_t q = ctr->q_in, lo, hi;
     chunk_of(q, gridDim.x, blockIdx.x, lo, hi);
     uint32_t run = blk_off[blockIdx.x];
-    for (uint32_t base = lo; base < hi; base += kBlock) {
-        uint32_t i = base + threadIdx.x;
-        uint32_t w0 = base + (threadIdx.x & ~31u);
-        uint32_t bal = (w0 < hi) ? keepw[w0 >> 5] : 0u;
-        bool keep = (i < hi) && ((bal >> (threadIdx.x & 31)) & 1u);
-        uint32_t tot;
-        uint32_t r = block_excl_scan<kBlock>(keep ? 1u : 0u, &tot);
-        if (keep) {
-            store_key<W>(sk, run + r, load_key<W>(keys_in, i));
-            si[run + r] = i;
+    for (uint32_t base = lo; base < hi; base += kBlock * kRPT) {
+        const uint32_t i0 = base + kRPT * threadIdx.x;
+        unsigned bits = 0;
+        if (i0 < hi) {
+            bits = (keepw[i0 >> 5] >> (i0 & 31u)) & 0xFu;
+            if (hi - i0 < (uint32_t)kRPT) bits &= (1u << (hi - i0)) - 1u;
         }
+        Key<W> k[kRPT];
+#pragma unroll
+        for (int u = 0; u < kRPT; ++u)
+            if ((bits >> u) & 1u) k[u] = load_key<W>(keys_in, i0 + u);
+        uint32_t tot;
+        uint32_t o = run + block_excl_scan<kBlock>((uint32_t)__popc(bits), &tot);
+#pragma unroll
+        for (int u = 0; u < kRPT; ++u)
+            if ((bits >> u) & 1u) {
+                store_key<W>(sk, o, k[u]);
+                si[o] = i0 + u;
+                ++o;
+            }
         run += tot;
     }
 }

@@ -436,33 +436,49 @@ __global__ void __launch_bounds__(kBlock) k_level_insert(const DevModel* __restr
     }
 }
 
-// Winner bits, one per candidate (32 per word, chunks aligned to 256).
+// Winner bits, one per candidate (32 per word, chunks aligned to 256).  A
+// block takes kR rounds of kBlock candidates at once: the candidate-slot reads
+// of all rounds, then the tag reads of all rounds, are issued before any
+// winner is decided, so each thread keeps kR dependent pairs in flight.
 template <int W>
 __global__ void __launch_bounds__(kBlock) k_level_flags(const DevModel* __restrict__ M, Counters* ctr, int f,
                                                         const uint64_t* __restrict__ table,
                                                         const uint32_t* __restrict__ cand_slot,
                                                         uint32_t* __restrict__ wmask, uint32_t* __restrict__ blk_cnt)
 {
+    constexpr int kR = 4;
     if (ctr->err) return;
     uint32_t lo0 = ctr->level_off[f], NC = (ctr->level_off[f + 1] - lo0) * (uint32_t)M->D, lo, hi;
     chunk_of(NC, gridDim.x, blockIdx.x, lo, hi);
     const int D = M->D;
     uint32_t cnt = 0;
-    for (uint32_t base = lo; base < hi; base += kBlock) {
-        uint32_t c = base + threadIdx.x;
-        bool win = false;
-        if (c < hi) {
-            uint32_t p;
-            int mv;
-            cand_parent(M, c, lo0, p, mv);
-            uint32_t sl = cand_slot[(uint64_t)p * D + mv];
-            // a candidate that met an existing row (kCand | row) is no winner: no probe
-            if (!(sl & kCand)) win = (uint32_t)table[(uint64_t)sl * Slot<W>::kWords] == (kCand | c);
+    for (uint32_t base = lo; base < hi; base += kBlock * kR) {
+        uint32_t sl[kR], tg[kR];
+#pragma unroll
+        for (int r = 0; r < kR; ++r) {
+            const uint32_t c = base + (uint32_t)r * kBlock + threadIdx.x;
+            sl[r] = kNone;
+            if (c < hi) {
+                uint32_t p;
+                int mv;
+                cand_parent(M, c, lo0, p, mv);
+                sl[r] = cand_slot[(uint64_t)p * D + mv];
+            }
         }
-        unsigned bal = __ballot_sync(0xffffffffu, win);
-        uint32_t w0 = base + (threadIdx.x & ~31u);
-        if ((threadIdx.x & 31) == 0 && w0 < hi) wmask[w0 >> 5] = bal;
-        cnt += win ? 1u : 0u;
+        // a candidate that met an existing row (kCand | row), or none, is no
+        // winner: no tag read
+#pragma unroll
+        for (int r = 0; r < kR; ++r)
+            tg[r] = (sl[r] & kCand) ? 0u : (uint32_t)table[(uint64_t)sl[r] * Slot<W>::kWords];
+#pragma unroll
+        for (int r = 0; r < kR; ++r) {
+            const uint32_t c = base + (uint32_t)r * kBlock + threadIdx.x;
+            const bool win = c < hi && !(sl[r] & kCand) && tg[r] == (kCand | c);
+            const unsigned bal = __ballot_sync(0xffffffffu, win);
+            const uint32_t w0 = base + (uint32_t)r * kBlock + (threadIdx.x & ~31u);
+            if ((threadIdx.x & 31) == 0 && w0 < hi) wmask[w0 >> 5] = bal;
+            cnt += win ? 1u : 0u;
+        }
     }
     uint32_t tot;
     block_excl_scan<kBlock>(cnt, &tot);
@@ -491,29 +507,48 @@ __global__ void __launch_bounds__(kBlock) k_level_scatter(const DevModel* __rest
     chunk_of(NC, gridDim.x, blockIdx.x, lo, hi);
     uint32_t run = blk_off[blockIdx.x];
     uint32_t pending = 0;
+    // at most kRound + kBlock - 1 rows are pending: every thread loads the
+    // parents (key, descriptor, candidate slot) of kPT of its rows, then builds
+    // them (one-word keys: all its rows at once)
+    constexpr int kPT = W == 1 ? (kRound + kBlock) / kBlock : 2;
     auto write_rows = [&](uint32_t n) {
-        for (uint32_t i = threadIdx.x; i < n; i += kBlock) {
-            const uint32_t c = qc[i];
-            uint32_t p;
-            int mv;
-            cand_parent(M, c, lo0, p, mv);
-            const Key<W> k = load_key<W>(keys, p);
-            const uint32_t pm = meta[p];
-            Key<W> child;
-            int cid;
-            apply_move<W>(M, k, meta_s(pm), meta_ns(pm), mv, child, cid);
-            const uint32_t row = base_row + run + i;
-            store_key<W>(keys, row, child);
-            meta[row] = child_meta<W>(M, k, pm, mv);
-            uint64_t* sl = table + (uint64_t)cand_slot[(uint64_t)p * D + mv] * Slot<W>::kWords;
-            // the tag is rebuilt from the key's hash: a store, no read of the slot
-            const uint64_t tag = ((uint64_t)fingerprint<W>(key_hash<W>(child)) << 32) | (uint64_t)row;
-            if constexpr (W == 1) {
-                *reinterpret_cast<ulonglong2*>(sl) = make_ulonglong2(tag, child.w[0]);
-            } else {
+        for (uint32_t i0 = threadIdx.x; i0 < n; i0 += kPT * kBlock) {
+            Key<W> pk[kPT];
+            uint32_t pm[kPT], sl[kPT];
+            int mvv[kPT];
 #pragma unroll
-                for (int w = 0; w < W; ++w) sl[1 + w] = child.w[w];
-                sl[0] = tag;
+            for (int u = 0; u < kPT; ++u) {
+                const uint32_t i = i0 + (uint32_t)u * kBlock;
+                if (i >= n) continue;
+                uint32_t p;
+                int mv;
+                cand_parent(M, qc[i], lo0, p, mv);
+                mvv[u] = mv;
+                pk[u] = load_key<W>(keys, p);
+                pm[u] = meta[p];
+                sl[u] = cand_slot[(uint64_t)p * D + mv];
+            }
+#pragma unroll
+            for (int u = 0; u < kPT; ++u) {
+                const uint32_t i = i0 + (uint32_t)u * kBlock;
+                if (i >= n) continue;
+                const Key<W> k = pk[u];
+                Key<W> child;
+                int cid;
+                apply_move<W>(M, k, meta_s(pm[u]), meta_ns(pm[u]), mvv[u], child, cid);
+                const uint32_t row = base_row + run + i;
+                store_key<W>(keys, row, child);
+                meta[row] = child_meta<W>(M, k, pm[u], mvv[u]);
+                uint64_t* slp = table + (uint64_t)sl[u] * Slot<W>::kWords;
+                // the tag is rebuilt from the key's hash: a store, no read of the slot
+                const uint64_t tag = ((uint64_t)fingerprint<W>(key_hash<W>(child)) << 32) | (uint64_t)row;
+                if constexpr (W == 1) {
+                    *reinterpret_cast<ulonglong2*>(slp) = make_ulonglong2(tag, child.w[0]);
+                } else {
+#pragma unroll
+                    for (int w = 0; w < W; ++w) slp[1 + w] = child.w[w];
+                    slp[0] = tag;
+                }
             }
         }
     };

@@ -279,3 +279,44 @@ def test_holstein_chain_full_space_nonzeros_at_scale(libpaces):
     rec = B.records_dict(g.observables(), L)
     assert rec["nnz"][-1] == d ** L * (5 * L - 2) - 2 * L * d ** (L - 1) == 76953125
     assert abs(rec["norm"][-1] - 1.0) < 1e-12
+
+
+def test_threshold_band_kept_set_exact(libpaces):
+    """Truncation keeps exactly the rows with re^2 + im^2 >= theta^2 evaluated in
+    FP64 with the products and the sum rounded separately (the oracle's rule),
+    for amplitudes planted on theta^2, within and just outside 2^-14 of it (the
+    band in which the kernel stops trusting its 20-bit magnitudes and runs the
+    FP64 test), far from it, at zero, and at subnormal and large magnitudes.
+    Every state of the 4-site ring is loaded, so no row is missing."""
+    import itertools
+    cfg = W.WORKLOADS["ring4"]
+    N, K = cfg["n_sites"], cfg["cap"]
+    occ1 = np.array(list(itertools.product(range(K + 1), repeat=N)), dtype=np.int32)
+    site = np.repeat(np.arange(N, dtype=np.int32), len(occ1))
+    occ = np.tile(occ1, (N, 1))
+    n = len(site)
+    rng = np.random.default_rng(11)
+    offs = np.array([0.0, 2.0 ** -10, 2.0 ** -13, 2.0 ** -14 * 1.001, 2.0 ** -14, 2.0 ** -14 * 0.999,
+                     2.0 ** -15, 2.0 ** -20, 2.0 ** -30, 1e-12, 1e-15, 2.0 ** -52, 2.0 ** -53])
+    offs = np.concatenate([offs, -offs[1:]])
+    for theta in (1e-7, 3.1e-4, 1e-2):
+        w = theta * theta * (1.0 + np.resize(offs, n))
+        w[::7] = theta * theta * np.exp(rng.normal(0.0, 4.0, len(w[::7])))   # far from the band
+        ang = rng.uniform(0.0, 2.0 * np.pi, n)
+        x, y = np.sqrt(w) * np.cos(ang), np.sqrt(w) * np.sin(ang)
+        x[0], y[0] = theta, 0.0                   # exactly on theta^2
+        x[1], y[1] = 0.0, -theta
+        x[2], y[2] = 0.0, 0.0
+        x[3], y[3] = 5e-324, 0.0                  # subnormal
+        x[4], y[4] = 1e-300, 1e-300
+        x[5], y[5] = 30.0, -40.0                  # large
+        x[6], y[6] = np.nextafter(theta, 0.0), 0.0
+        amps = x + 1j * y
+        g = B.Solver(**W.model_kwargs(cfg))
+        g.load_state(site, occ, amps)
+        g.step(cfg["dt"], 1, theta)
+        keep = g.keep()
+        expect = (x * x + y * y) >= theta * theta
+        assert len(keep) == n
+        assert np.array_equal(keep, expect), (theta, np.flatnonzero(keep != expect)[:10])
+        g.close()
