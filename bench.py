@@ -479,9 +479,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--realisations", type=int, default=0, help="ensemble size (0: the workload's)")
     ap.add_argument("--compare", action="store_true",
-                    help="also time the plain FP64 single-instance form and report observable errors")
+                    help="also time the plain FP64 single-instance form and report observable errors "
+                         "(on by default for a single instance on one GPU)")
+    ap.add_argument("--no-compare", action="store_true", help="skip the comparison run")
     ap.add_argument("--compare-sample", type=int, default=4)
-    ap.add_argument("--compare-forms", default="c64,dw", help="forms --compare runs next to c128")
+    ap.add_argument("--compare-forms", default="c64", help="forms the comparison runs next to c128 (c64, dw)")
     ap.add_argument("--gradient", action="store_true",
                     help="also time the reverse pass of the whole trajectory (workloads with ckpt_every): "
                          "the site-0 population at T plus the spectrum mean squared error against a seeded "
@@ -600,7 +602,10 @@ def main():
     if args.gradient and rank == 0:
         grad = gradient_run(B, cfg, model, end)
     variants = None
-    if args.compare:
+    # by default a single instance on one GPU is also run in complex64 terms over
+    # the same steps: its throughput and observable errors against this run
+    compare = args.compare or (ws == 1 and R == 1 and not args.no_compare and args.propagator == "taylor")
+    if compare:
         sol.close()
         variants = compare_variants(B, args, cfg, model, (site_p, occ_p, amps_p[0::2] + 1j * amps_p[1::2]), end,
                                     first_timed, K, barrier, run)
