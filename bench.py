@@ -579,6 +579,11 @@ def main():
                 "frac": frac_fp64, "traffic": traffic,
                 "peak_kind": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
                 "hbm_achieved_gbs": achieved_gbs, "hbm_frac": frac_hbm, "hbm_peak_gbs": peak_gbs}
+        # the FP64 rate this GPU sustains on independent FMA chains, measured
+        # after the timed steps (paces_fp64_rate), next to the derived peak
+        fp64_meas = B.fp64_rate()
+        roof["fp64_measured_tflops"] = fp64_meas
+        roof["frac_of_measured_fp64"] = achieved_tf / fp64_meas if fp64_meas > 0 else None
     else:
         roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": peak_gbs, "unit": "GB/s",
                 "frac": frac_hbm, "traffic": traffic, "peak_kind": peak_kind + " (copy), sustained",

@@ -410,6 +410,17 @@ paces_status paces_backward(paces_t h, int64_t nsteps, const double* dL_dc_final
  * buffers with cudaMalloc.  Returns INVALID or CUDA. */
 paces_status paces_selftest_barrier(int32_t extra_arrivals, double timeout_ms, int32_t* device_error);
 
+/* ---- FP64 rate probe (no counterpart in the paper) -------------------------
+ * The complex128 propagator is bound by the FP64 pipe, so its roofline needs
+ * the FP64 rate the GPU actually sustains next to the one derived from unit
+ * counts and clocks.  On the current device this runs a kernel whose threads
+ * (as many as fit on every SM) each keep eight independent FP64 FMA chains
+ * going, once untimed and three times timed with CUDA events on a stream of
+ * its own, and stores the best rate in *tflops (TFLOP/s, two flops per FMA).
+ * Synchronises that stream; allocates no device memory.  Returns INVALID
+ * (tflops NULL) or CUDA. */
+paces_status paces_fp64_rate(double* tflops);
+
 /* ---- Expansion without allocation (no counterpart in the paper) -----------
  * Some callers cannot allocate device memory: hosts whose framework has
  * already reserved all of it in its own pool, real-time loops that must never

@@ -32,7 +32,7 @@ EXPORTED = (
     "paces_get_levels", "paces_get_keep", "paces_get_hamiltonian", "paces_record_len",
     "paces_num_records", "paces_observables", "paces_profile", "paces_stage_stats",
     "paces_expand_noalloc", "paces_get_tuning", "paces_set_tuning", "paces_record", "paces_backward",
-    "paces_step_nom", "paces_selftest_barrier", "paces_set_coefficients",
+    "paces_step_nom", "paces_selftest_barrier", "paces_set_coefficients", "paces_fp64_rate",
 )
 
 
@@ -146,6 +146,8 @@ def load():
     lib.paces_set_coefficients.argtypes = [P, C.c_double, dp, dp, dp]
     lib.paces_selftest_barrier.restype = S
     lib.paces_selftest_barrier.argtypes = [C.c_int32, C.c_double, C.POINTER(C.c_int32)]
+    lib.paces_fp64_rate.restype = S
+    lib.paces_fp64_rate.argtypes = [C.POINTER(C.c_double)]
     _lib = lib
     return lib
 
@@ -491,3 +493,13 @@ def selftest_barrier(extra_arrivals, timeout_ms=1.0):
     if rc:
         raise PacesError(rc, "paces_selftest_barrier")
     return int(err.value)
+
+
+def fp64_rate():
+    """FP64 FMA rate the current device sustains, TFLOP/s (paces_fp64_rate)."""
+    lib = load()
+    v = C.c_double()
+    rc = lib.paces_fp64_rate(C.byref(v))
+    if rc:
+        raise PacesError(rc, "paces_fp64_rate")
+    return v.value

@@ -1237,4 +1237,45 @@ int launch_barrier_selftest(Counters* ctr, double* part, int grid, unsigned expe
     return cudaLaunchKernelExC(&cfg, (const void*)k_barrier_selftest, args) == cudaSuccess ? 1 : -1;
 }
 
+// ---------------------------------------------------------------- FP64 rate probe
+// The FP64 FMA rate this GPU sustains, for the propagator's roofline: every
+// thread runs kChains independent FMA chains a <- a m + c for `iters`
+// iterations (with m = 1/2 and c = 1/4 every chain settles at 1/2, so the
+// values stay finite and normal).  A store that only a chain ending at a value
+// it cannot reach would take keeps the work live; g_fp64_sink is a valid
+// device variable, so even that store stays in bounds.
+__device__ double g_fp64_sink;
+
+__global__ void __launch_bounds__(kBlock) k_fp64_rate(int iters, double m, double c)
+{
+    constexpr int kChains = 8;
+    double a[kChains];
+#pragma unroll
+    for (int i = 0; i < kChains; ++i) a[i] = (double)((threadIdx.x + i) & 7);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int i = 0; i < kChains; ++i) a[i] = fma(a[i], m, c);
+    }
+    double sum = 0.0;
+#pragma unroll
+    for (int i = 0; i < kChains; ++i) sum += a[i];
+    if (sum == -1.0) g_fp64_sink = sum;
+}
+
+// Launches the probe on `grid` blocks of kBlock threads and returns the FMAs
+// it issues (kChains per thread and iteration), or -1 on a launch error.
+double launch_fp64_rate(int grid, int iters, cudaStream_t st)
+{
+    k_fp64_rate<<<grid, kBlock, 0, st>>>(iters, 0.5, 0.25);
+    if (cudaGetLastError() != cudaSuccess) return -1.0;
+    return 8.0 * (double)grid * kBlock * (double)iters;
+}
+
+int fp64_rate_blocks_per_sm()
+{
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fp64_rate, kBlock, 0);
+    return n;
+}
+
 }  // namespace paces

@@ -1626,6 +1626,43 @@ paces_status paces_selftest_barrier(int32_t extra_arrivals, double timeout_ms, i
     return s;
 }
 
+paces_status paces_fp64_rate(double* tflops)
+{
+    if (!tflops) return PACES_ERR_INVALID;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+        return PACES_ERR_CUDA;
+    const int bps = fp64_rate_blocks_per_sm();
+    if (bps < 1) return PACES_ERR_CUDA;
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return PACES_ERR_CUDA;
+    paces_status s = PACES_OK;
+    double best = 0.0;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        s = PACES_ERR_CUDA;
+    } else {
+        // one untimed launch, then the best of three timed ones
+        for (int k = 0; k < 4 && s == PACES_OK; ++k) {
+            float ms = 0.f;
+            double fmas = 0.0;
+            if (cudaEventRecord(e0, st) != cudaSuccess || (fmas = launch_fp64_rate(sms * bps, 2048, st)) < 0.0 ||
+                cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess || !(ms > 0.f)) {
+                s = PACES_ERR_CUDA;
+                break;
+            }
+            if (k > 0) best = std::max(best, 2.0 * fmas / (ms * 1e-3) / 1e12);
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaStreamDestroy(st);
+    if (s == PACES_OK) *tflops = best;
+    return s;
+}
+
 paces_status paces_num_records(paces_t h, int64_t* n)
 {
     if (!h || !n) return PACES_ERR_INVALID;

@@ -125,6 +125,8 @@ int launch_export_csr(const Bufs& b, uint32_t q, const uint64_t* off, int32_t* c
 // Occupancy query key of the Lanczos propagator (precision values are 0..2).
 constexpr int kPrecLanczos = 16;
 int taylor_blocks_per_sm(int lpr, int precision);
+double launch_fp64_rate(int grid, int iters, cudaStream_t st);
+int fp64_rate_blocks_per_sm();
 // Cooperative self-test of the bounded grid barrier (kern_taylor.cu).
 int launch_barrier_selftest(Counters* ctr, double* part, int grid, unsigned expect, unsigned long long timeout_ns,
                             cudaStream_t st);

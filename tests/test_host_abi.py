@@ -17,7 +17,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def declared_symbols():
     src = open(os.path.join(ROOT, "include", "paces.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(paces_[a-z_]+)\s*\(", src)) - {"paces_t"})
+    return sorted(set(re.findall(r"\b(paces_[a-z0-9_]+)\s*\(", src)) - {"paces_t"})
 
 
 def test_library_exports_every_declared_symbol(libpaces):

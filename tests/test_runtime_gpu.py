@@ -107,3 +107,14 @@ def test_grid_barrier_time_limit_runs_out_safely(libpaces):
     s.set_state(*W.start_state(cfg))
     s.step(cfg["dt"], 2, cfg["theta"])
     assert s.num_records() == 3
+
+
+def test_fp64_rate_probe(libpaces):
+    """The FP64 rate probe reports a positive rate no higher than the rate
+    derived from the unit counts and the maximum clock (152 SMs x 2 FMA per
+    clock x 2 flops x 2.07 GHz = 1.26 TFLOP/s), with a margin for the clock, and
+    the same order of magnitude on a second call."""
+    a = B.fp64_rate()
+    b = B.fp64_rate()
+    assert 0.05 < a < 1.4 and 0.05 < b < 1.4, (a, b)
+    assert 0.5 < a / b < 2.0
