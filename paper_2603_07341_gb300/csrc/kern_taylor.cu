@@ -725,16 +725,16 @@ __global__ void __launch_bounds__(kBlock) k_taylor_dw(TaylorArgs a)
 // and added into the double-word accumulator r with an error-free sum.  The
 // switch is taken from the norms the stop test already reduces: when term m
 // ends with ||phi_m||^2 <= kC64Tau2 ||r||^2, terms from max(m + 2, kDwTerms + 1)
-// on run in complex64 (term m + 1 has started by then with its output format
-// fixed, so it stays double-word and writes its result rounded to float2 for
-// the first complex64 term).  Every block reads the same reduced norms, so the
-// whole grid switches at the same term.  An FP32 term's rounding is about
-// 2^-24 (c + 2) of its own norm, so with tau = 2^-16 what the complex64 terms
-// add to a step's error stays near 2^-38 of ||v|| (||phi_{m+2}|| is at most
-// tau ||v|| (rho h)^2 / ((m + 1)(m + 2))), and a 2048-step run stays far inside
-// a 1e-6 observable tolerance.  With the first terms of a series in
-// double-word and the rest in FP32, the series costs less the faster its
-// terms decay.
+// on run in complex64 (term m has written its result in double-word, the input
+// format of a double-word term, so term m + 1 stays double-word and writes its
+// own result rounded to float2 for the first complex64 term).  Every block
+// reads the same reduced norms, so the whole grid switches at the same term.
+// An FP32 term's rounding is about 2^-24 (c + 2) of its own norm, so with
+// tau = 2^-16 what the complex64 terms add to a step's error stays near 2^-38
+// of ||v|| (||phi_{m+2}|| is at most tau ||v|| (rho h)^2 / ((m + 1)(m + 2))),
+// and a 2048-step run stays far inside a 1e-6 observable tolerance.  With the
+// first terms of a series in double-word and the rest in FP32, the series
+// costs less the faster its terms decay.
 constexpr int kDwTerms = 2;                  // terms that always run double-word
 constexpr float kC64Tau2 = 2.3283064365386963e-10f;   // tau^2 = 2^-32
 
