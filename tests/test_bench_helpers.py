@@ -1,7 +1,7 @@
 """Host-side helpers of bench.py: the propagator traffic scaled from a stored
 small-case capture is reported only for the library code it was captured on
-(comments ignored); the CPU description; the replica reduction lives in
-test_bench_ranks."""
+(comments ignored); the CPU description; the variant comparison's error
+figures; the replica reduction lives in test_bench_ranks."""
 import os
 import shutil
 
@@ -81,3 +81,30 @@ def test_autograd_parameter_vector_maps_onto_the_model():
     assert np.all(m["g"] == 1.3) and np.all(m["omega"] == 0.9)
     assert np.array_equal(m["eps"], p[3:])
     assert m["n_sites"] == base["n_sites"] and m["cap"] is base["cap"]
+
+
+def test_variant_errors_are_the_largest_differences():
+    """The comparison block of the bench (a variant against the complex128 run)
+    reports, per observable, the largest absolute difference over the records,
+    and the spectrum difference relative to the reference spectrum's peak; an
+    identical run reports zeros."""
+    import numpy as np
+    from paper_2603_07341_gb300 import binding as B
+    N, T = 3, 40
+    rng = np.random.default_rng(5)
+    ref = rng.normal(size=(T, B.OBS_FIXED + 2 * N))
+    ref[:, 0] = 0.05 * np.arange(T)                      # time
+    var = ref.copy()
+    var[7, B.OBS_FIXED + 1] += 3e-9                      # P_1 at one step
+    var[11, B.OBS_FIXED + N + 2] -= 5e-10                # <n_2> at another
+    var[20, 4] += 4e-8                                   # Re C
+    var[21, 5] -= 3e-8                                   # Im C (a different step)
+    var[30, 3] += 1e-7                                   # energy
+    e = bench.observable_errors(B, var, ref, N)
+    assert abs(e["P"] - 3e-9) < 1e-15 and abs(e["nbar"] - 5e-10) < 1e-15
+    assert abs(e["C"] - 4e-8) < 1e-15 and abs(e["energy"] - 1e-7) < 1e-14 and e["norm"] == 0.0
+    z = bench.observable_errors(B, ref, ref, N)
+    assert all(v == 0.0 for v in z.values())
+    cfg = {"dt": 0.05}
+    assert bench.spectrum_error(B, ref, ref, cfg) == 0.0
+    assert 0.0 < bench.spectrum_error(B, var, ref, cfg) < 1e-6
